@@ -1,0 +1,116 @@
+"""Plain definitions the Krylov sampler and the log-det estimator converge to.
+
+* Section 4: x = Q^{-1/2} z, Q^{-1/2} the inverse of the principal square root,
+  is a draw from N(0, Q^{-1}) when z ~ N(0, I).
+* Section 1: the dense baseline Q = L L^T (Cholesky) gives
+  log det Q = 2 sum_i log L_ii.
+* Section 2: block-circulant Q is diagonalised by the FFT; the same holds for
+  the cell-centred Neumann lattice with the DCT-II and for Dirichlet with the
+  DST-I (constant kappa^2 only).
+* Section 6: the Hutchinson terms v^T log(Q) v.
+
+Everything here is FP64.  Pins: tests/test_oracle_exact.py.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.fft as sfft
+import scipy.linalg as sla
+
+from . import stencil
+
+
+# ---------------------------------------------------------------- dense (tiny n)
+def dense_eigh(Q):
+    """Eigen-decomposition of a (sparse or dense) SPD Q, ascending eigenvalues."""
+    Qd = Q.toarray() if hasattr(Q, "toarray") else np.asarray(Q, dtype=np.float64)
+    return np.linalg.eigh(Qd)
+
+
+def matrix_function_dense(Q, Z, f):
+    """f(Q) z for each row z of Z (rows are vectors), via dense eigh."""
+    lam, U = dense_eigh(Q)
+    Z = np.atleast_2d(np.asarray(Z, dtype=np.float64))
+    return ((U * f(lam)) @ (U.T @ Z.T)).T
+
+
+def sample_dense(Q, Z):
+    """x = Q^{-1/2} z (Section 4) for each row z of Z, by dense eigh."""
+    lam, _ = dense_eigh(Q)
+    if lam[0] <= 0:
+        raise ValueError("Q is not positive definite")
+    return matrix_function_dense(Q, Z, lambda l: 1.0 / np.sqrt(l))
+
+
+def logdet_cholesky(Q) -> float:
+    """log det Q = 2 sum log L_ii with Q = L L^T (Section 1's factorisation)."""
+    Qd = Q.toarray() if hasattr(Q, "toarray") else np.asarray(Q, dtype=np.float64)
+    L = sla.cholesky(Qd, lower=True)
+    return float(2.0 * np.sum(np.log(np.diag(L))))
+
+
+def quadform_log_dense(Q, V) -> np.ndarray:
+    """v^T log(Q) v for each row v of V (the Hutchinson summands, Section 6)."""
+    lam, U = dense_eigh(Q)
+    V = np.atleast_2d(np.asarray(V, dtype=np.float64))
+    W = V @ U
+    return (W * W) @ np.log(lam)
+
+
+# ------------------------------------------------------ spectral (constant kappa)
+def _fwd(bc, X):
+    axes = tuple(range(X.ndim))
+    if bc == "periodic":
+        return sfft.fftn(X, axes=axes, norm="ortho")
+    if bc == "neumann":
+        return sfft.dctn(X, type=2, axes=axes, norm="ortho")
+    if bc == "dirichlet":
+        return sfft.dstn(X, type=1, axes=axes, norm="ortho")
+    raise ValueError(bc)
+
+
+def _inv(bc, X):
+    axes = tuple(range(X.ndim))
+    if bc == "periodic":
+        return sfft.ifftn(X, axes=axes, norm="ortho").real
+    if bc == "neumann":
+        return sfft.idctn(X, type=2, axes=axes, norm="ortho")
+    if bc == "dirichlet":
+        return sfft.idstn(X, type=1, axes=axes, norm="ortho")
+    raise ValueError(bc)
+
+
+def spectral_apply(shape, bc, mu, v):
+    """U diag(mu) U^T v where U is the lattice Laplacian's eigenbasis for ``bc``
+    (unitary FFT / DCT-II / DST-I) and ``mu`` is given on the transform grid."""
+    shape = tuple(int(s) for s in shape)
+    X = np.asarray(v, dtype=np.float64).reshape(shape)
+    return _inv(bc, np.asarray(mu) * _fwd(bc, X)).reshape(-1)
+
+
+def spectral_coefficients(shape, bc, v):
+    """Coefficients of v in the unitary eigenbasis (complex for periodic)."""
+    shape = tuple(int(s) for s in shape)
+    return _fwd(bc, np.asarray(v, dtype=np.float64).reshape(shape))
+
+
+def sample_spectral(shape, bc, op, kappa2_const, tau, z):
+    """x = Q^{-1/2} z for constant kappa^2 through the closed-form eigenvalues."""
+    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau)
+    return spectral_apply(shape, bc, 1.0 / np.sqrt(mu), z)
+
+
+def logdet_spectral(shape, bc, op, kappa2_const, tau) -> float:
+    """log det Q = sum of log eigenvalues (constant kappa^2)."""
+    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau)
+    return float(np.sum(np.log(mu)))
+
+
+def quadform_log_spectral(shape, bc, op, kappa2_const, tau, V) -> np.ndarray:
+    """v^T log(Q) v = sum_k |c_k|^2 log mu_k for each row v (constant kappa^2)."""
+    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau)
+    out = []
+    for v in np.atleast_2d(V):
+        c = spectral_coefficients(shape, bc, v)
+        out.append(float(np.sum(np.abs(c) ** 2 * np.log(mu))))
+    return np.array(out)
