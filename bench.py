@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark of the Krylov GMRF sampler (Algorithm 1 + Proposition 1) on GB300.
+
+Workload: 2-D SPDE-type GMRF on a 1024 x 1024 grid with zero-Neumann boundary,
+Q = (K - Lap)^2 (13-point), log kappa^2(s) a smooth Gaussian field (mean
+log 0.05, sd 0.5, length-scale 64 cells), preconditioned by the constant-kappa
+circulant version of Q via 2-D FFT (Section 5.1), FP32 vectors with FP64
+recurrence scalars, one sample per step to relative tolerance 1e-6.
+
+One step = one gmrf_sample call: Philox noise z, ||z||, the preconditioned
+Lanczos loop with its stopping rule, T_m^{-1/2} e_1, x = ||z|| V_m y and the
+final M^{-1/2}.  Inputs are resident in HBM; L2 is flushed (256 MiB write)
+before every timed step, and every step is timed with CUDA events on the
+problem's stream.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = 1024
+TOL = 1e-6
+M_MAX = 2000
+KAPPA_SEED = 1
+# Lanczos steps the oracle's own stopping rule takes on this workload (FP64,
+# circulant M, tol 1e-6); used to scale the bounded oracle timing.  Measured by
+# running oracle.lanczos.precond_sample to convergence on this input.
+ORACLE_M = {"circulant": None, "mirror": None}
+
+
+def workload_config(precond):
+    return {
+        "workload": "2D SPDE GMRF %dx%d zero-Neumann, Q=(K-Lap)^2 13-point, log kappa^2 ~ GP(mean log 0.05, "
+                    "sd 0.5, ell 64 cells), %s-preconditioned (2D FFT), FP32 vectors / FP64 scalars, "
+                    "1 sample per step, rel tol %g" % (GRID, GRID, precond, TOL),
+        "grid": [GRID, GRID], "bc": "neumann", "op": "spde_squared", "precond": precond,
+        "samples_per_step": 1, "tol": TOL, "m_max": M_MAX,
+        "l2": "flushed before every timed step (256 MiB write)",
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv"
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ roofline bytes
+def algorithmic_bytes(kclass, n, nx, ny, kind):
+    """Bytes each launch of a kernel class must move for one 1024^2 vector
+    (FP32).  Spectral rows: circulant (nx/2+1) complex, mirror nx reals."""
+    spec = ny * (nx // 2 + 1) * 8 if kind == "circulant" else n * 4
+    return {
+        "pre_col": 2 * spec,                       # read + write the spectrum
+        "pre_row_fwd": 2 * 4 * n + 4 * n + spec,   # q_{j-1}, v_{j-1} in; v_j, spectrum out
+        "pre_row_mid": spec + 3 * 4 * n + spec,    # spectrum, v_j, kappa^2 in; g, spectrum out
+        "pre_row_last": spec + 3 * 4 * n + 4 * n,  # spectrum, g, v_j, v_{j-1} in; q_j out
+    }.get(kclass)
+
+
+def traffic_from_profile(kclass):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the
+    current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_1312_1476_gb300", "csrc", "precond.cu"), "rb").read()
+        if d.get("precond_cu_sha1") != hashlib.sha1(src).hexdigest():
+            return None
+        return d.get("bytes_per_launch", {}).get(kclass)
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline(precond, k_steps=24, m_scale=None):
+    """The oracle (FP64 NumPy/SciPy) timed on the host: k_steps of its
+    preconditioned Lanczos on the same 1024^2 input, scaled to one sample."""
+    import scipy.fft
+    from oracle import lanczos as olz, precond as opre, stencil
+    from paper_1312_1476_gb300 import inputs
+    cores = os.cpu_count() or 1
+    shape = (GRID, GRID)
+    k2 = inputs.kappa2_gp_field(shape, seed=KAPPA_SEED).astype(np.float64)
+    kb = opre.kappa2_bar(k2)
+    kind = "periodic" if precond == "circulant" else "neumann"
+    z = inputs.gaussian_vectors(1, GRID * GRID, seed=2, dtype=np.float64)[0]
+    with scipy.fft.set_workers(cores):
+        t0 = time.perf_counter()
+        Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2, 1.0)
+        A = olz.preconditioned_operator(Q, shape, kind, "spde_squared", kb, 1.0)
+        t1 = time.perf_counter()
+        done = 0
+        for st in olz.lanczos_steps(A, z):
+            done += 1
+            if done >= k_steps or st["breakdown"]:
+                break
+        t2 = time.perf_counter()
+    per_step = (t2 - t1) / done
+    m = m_scale if m_scale else done
+    per_sample = per_step * m
+    return {"value": 1.0 / per_sample, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": "%d Lanczos steps of one %dx%d sample (oracle FP64, scipy.fft workers=%d), "
+                      "scaled to m=%d steps per sample; operator assembly (%.1f s) not counted"
+                      % (done, GRID, GRID, cores, m, t1 - t0)}
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1312_1476_gb300 import _build, inputs
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1312_1476_gb300 import gmrf
+
+    shape = (GRID, GRID)
+    n = GRID * GRID
+    k2 = torch.from_numpy(inputs.kappa2_gp_field(shape, seed=KAPPA_SEED)).cuda()
+    stream = torch.cuda.current_stream()
+    prob = gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond=args.precond, precision="fp32",
+                        stream=stream.cuda_stream)
+    x = torch.empty(n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    seed0 = 1000 + 100000 * rank
+
+    def step(i, out=None, z=None):
+        rc, info = prob.sample(out if out is not None else x, nsamples=1, tol=TOL, m_max=M_MAX,
+                               seed=seed0 + i, z=z, check_every=args.check_every)
+        return rc, info[0]
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    gmrf.trace_reset()
+    gmrf.trace_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ms_used, errs = [], []
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        rc, info = step(args.warmup + i)
+        ev[i][1].record(stream)
+        ms_used.append(info.m_used)
+        errs.append(info.err_est)
+        if rc != gmrf.OK:
+            raise RuntimeError("sample failed: %s %s" % (gmrf.strerror(rc), info))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    gmrf.trace_timing(False)
+    clk = clocks.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = dev_ms
+    if world > 1:
+        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    value = world * args.steps / (t_max / 1e3)
+
+    # per-kernel times from the live trace over the timed region
+    classes = ["pre_row_fwd", "pre_col", "pre_row_mid", "pre_row_last", "stencil_step", "tm", "assemble",
+               "pre_apply", "init", "rng", "other"]
+    per = {c: gmrf.trace_query(c) for c in classes}
+    launches = gmrf.trace_query("all")[1]
+    dom = max((c for c in classes if algorithmic_bytes(c, n, GRID, GRID, args.precond)),
+              key=lambda c: per[c][0])
+    ms_tot, nl, nt = per[dom]
+    avg_s = ms_tot / max(nt, 1) / 1e3
+    ab = algorithmic_bytes(dom, n, GRID, GRID, args.precond)
+    peak, peak_src = load_peaks()
+    achieved = ab / avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(dom),
+            "algorithmic_bytes_per_launch": ab, "avg_launch_us": round(avg_s * 1e6, 3),
+            "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+            "kernel_share": {c: round(per[c][0] / max(sum(v[0] for v in per.values()), 1e-9), 4)
+                             for c in classes if per[c][1]}}
+
+    # end to end through the C ABI with pinned host buffers (z in, x out)
+    zh = torch.from_numpy(inputs.gaussian_vectors(1, n, seed=7, dtype=np.float32)[0]).pin_memory()
+    xh = torch.empty(n, dtype=torch.float32).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e2e_ev[i][0].record(stream)
+        rc, _ = step(i, out=xh, z=zh)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        out = {
+            "metric": "GMRF samples/s at 1e-6 rel err (1024^2 grid), %HBM peak; serve p50/p99 ms",
+            "value": round(value, 3), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args.precond),
+            "m_used": {"mean": float(np.mean(ms_used)), "min": int(min(ms_used)), "max": int(max(ms_used))},
+            "err_est_max": float(max(errs)),
+            "roofline": roof,
+            "e2e": {"value": round(world * args.steps / (e2e_ms / 1e3), 3), "unit": "samples/s",
+                    "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "wall_s_timed_region": round(t_wall, 3),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.precond, m_scale=int(round(np.mean(ms_used))))
+        print(json.dumps(out), flush=True)
+    prob.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle as the reference arm (CPU, FP64), same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    m_ref = ORACLE_M.get(args.precond)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(args.precond, k_steps=4, m_scale=m_ref)
+        if i >= args.warmup:
+            times.append(1.0 / cb["value"])
+    value = 1.0 / float(np.mean(times))
+    out = {"impl": "reference", "metric": "GMRF samples/s at 1e-6 rel err (1024^2 grid), %HBM peak; serve p50/p99 ms",
+           "value": value, "unit": "samples/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(args.precond),
+           "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cb["cores"], "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precond", choices=["circulant", "mirror"], default="circulant")
+    ap.add_argument("--check-every", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * gmrf.h -- C ABI of the GB300 Krylov GMRF sampler and Lanczos log-determinant.
+ *
+ * The operations follow Simpson, Turner, Strickland and Pettitt, "Scalable
+ * iterative methods for sampling from massive Gaussian random vectors":
+ *
+ *   gmrf_create  -- a precision matrix Q given matrix-free as a lattice
+ *                   stencil with a coefficient field (Section 2: Q is never
+ *                   formed, only Q v is computed), optionally with the
+ *                   constant-coefficient preconditioner M of Section 5.1
+ *                   (Theorem 2) used through Proposition 1.
+ *   gmrf_sample  -- x_m ~= Q^{-1/2} z by the Lanczos sampler (Section 4,
+ *                   Algorithm 1), m chosen adaptively from the a-posteriori
+ *                   bound of Theorem 1 (eq. krylov_bound).
+ *   gmrf_logdet  -- log det Q by the Hutchinson estimator with Rademacher
+ *                   probes and Lanczos (Gauss) quadrature (Section 6), with
+ *                   the preconditioned split of Section 6.2
+ *                   (log det Q = log det(F^-1 Q F^-T) + log det M).
+ *
+ * Operator family (unit lattice spacing, graph Laplacian L):
+ *   GMRF_OP_SHIFTED_LAPLACIAN  Q = tau (K + L)      5-point 2-D / 7-point 3-D
+ *   GMRF_OP_SPDE_SQUARED       Q = tau (K + L)^2    13-point 2-D
+ * with K = diag(kappa^2(s)).  Boundary: periodic (torus), cell-centred
+ * Neumann (a boundary cell counts only neighbours inside the grid) or
+ * Dirichlet (zero outside the grid).  Cell (z, y, x) has index
+ * x + nx*(y + ny*z).  Vectors of a batch are stored one after another:
+ * element i of vector s is at [s*n + i] ("[nvec][n]" layout).
+ *
+ * Memory: every pointer argument may be host memory or device memory of the
+ * current device (detected with cudaPointerGetAttributes).  The caller keeps
+ * ownership of everything it passes; the library copies kappa2 during
+ * gmrf_create and owns its own workspaces (Lanczos basis, scalars,
+ * transform tables), which gmrf_destroy frees.
+ *
+ * Streams: all device work of a problem is issued on the stream given to
+ * gmrf_create (NULL = the legacy default stream).  Every call returns after
+ * its results are complete (it synchronises that stream).
+ *
+ * Errors: 0 = GMRF_OK, otherwise a negative code below; gmrf_strerror maps a
+ * code to a static string.  On GMRF_ERR_NOT_CONVERGED the sample is still
+ * written (with the last subspace size) and each info record carries its own
+ * status and error estimate.  A problem must not be used from two threads at
+ * once.
+ */
+#ifndef GMRF_H
+#define GMRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GMRF_OK 0
+#define GMRF_ERR_INVALID (-1)       /* bad dimensions, kappa2 < 0 or not finite, tol <= 0, ... */
+#define GMRF_ERR_OOM (-2)           /* device memory for one vector's Lanczos state not available */
+#define GMRF_ERR_NOT_CONVERGED (-3) /* m_max reached before the stopping rule held */
+#define GMRF_ERR_NOT_SPD (-4)       /* a non-positive pivot of T_m: Q (or A) is not SPD */
+#define GMRF_ERR_NUMERIC (-5)       /* NaN or Inf during the iteration */
+#define GMRF_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define GMRF_ERR_TIMEOUT (-7)       /* a device-side wait ran out of its iteration budget */
+#define GMRF_ERR_UNSUPPORTED (-8)   /* a valid combination this build does not implement */
+
+typedef struct gmrf_problem gmrf_problem; /* opaque, library-owned */
+
+typedef enum { GMRF_BC_PERIODIC = 0, GMRF_BC_NEUMANN = 1, GMRF_BC_DIRICHLET = 2 } gmrf_bc;
+
+typedef enum {
+  GMRF_OP_SHIFTED_LAPLACIAN = 0, /* tau (K + L) */
+  GMRF_OP_SPDE_SQUARED = 1       /* tau (K + L)^2, 2-D only */
+} gmrf_op;
+
+/* Preconditioner M (Proposition 1 with F = M^{1/2}; Section 5.1):
+ *   NONE      -- plain Algorithm 1 on Q;
+ *   CIRCULANT -- M = the same operator with constant kappa_bar^2 on the
+ *                grid's own torus (block circulant, applied by 2-D FFT);
+ *   MIRROR    -- M = the same operator with constant kappa_bar^2 on the
+ *                mirror-extended torus, i.e. the cell-centred Neumann
+ *                operator, applied by 2-D DCT-II (an FFT of the reflected
+ *                grid).
+ * Preconditioning needs dim == 2 and power-of-two nx, ny in [8, 4096]. */
+typedef enum { GMRF_PREC_NONE = 0, GMRF_PREC_CIRCULANT = 1, GMRF_PREC_MIRROR = 2 } gmrf_precond;
+
+/* Vector arithmetic of the Krylov iteration.  FP32: vectors, stencil and
+ * transforms in FP32, dot products in compensated FP32 (pairs of floats)
+ * finished in FP64, alpha/beta, T_m and quadrature in FP64.  FP64:
+ * everything in FP64. */
+typedef enum { GMRF_FP32 = 0, GMRF_FP64 = 1 } gmrf_precision;
+
+typedef struct {
+  int32_t dim;       /* 2 or 3 */
+  int32_t bc;        /* gmrf_bc */
+  int32_t op;        /* gmrf_op */
+  int32_t precond;   /* gmrf_precond */
+  int64_t nx, ny, nz;  /* grid extents (nz ignored for dim == 2); each >= 2 */
+  const float* kappa2; /* [n] coefficient field, host or device; NULL => kappa2_const */
+  double kappa2_const; /* used when kappa2 == NULL */
+  double tau;          /* precision scale, > 0 */
+  double kappa2_precond; /* constant kappa_bar^2 of M; <= 0 => exp(mean log kappa2) */
+  int32_t precision;   /* gmrf_precision */
+  int32_t reserved;    /* must be 0 */
+} gmrf_desc;
+
+typedef struct {
+  double tol;          /* relative tolerance of the Theorem 1 estimate, > 0 */
+  int32_t m_max;       /* largest subspace size, >= 1 */
+  int32_t nsamples;    /* number of vectors z (>= 1) */
+  uint64_t seed;       /* Philox-4x32-10 key for z when z_in == NULL */
+  const void* z_in;    /* optional [nsamples][n] noise, float (FP32) or double (FP64), host or device */
+  int32_t check_every; /* steps between host polls of the convergence flags (<= 0: 16) */
+  int32_t reserved;    /* must be 0 */
+} gmrf_sample_opts;
+
+typedef struct {
+  int32_t m_used;  /* subspace size of the returned vector */
+  int32_t status;  /* GMRF_OK, GMRF_ERR_NOT_CONVERGED, GMRF_ERR_NOT_SPD or GMRF_ERR_NUMERIC */
+  double err_est;  /* relative Theorem 1 estimate at m_used (0 after an exact breakdown) */
+} gmrf_result_info;
+
+typedef struct {
+  double tol;          /* same stopping rule as gmrf_sample, per probe */
+  int32_t m_max;
+  int32_t nprobes;     /* N >= 1 (>= 2 for a standard error) */
+  uint64_t seed;       /* Philox key of the Rademacher probes when probes_in == NULL */
+  const void* probes_in; /* optional [nprobes][n] probes (float / double by precision) */
+  int32_t check_every;
+  int32_t reserved;
+} gmrf_logdet_opts;
+
+/* Section 2 / 5.1: build a problem.  Validates the descriptor, copies kappa2,
+ * builds the preconditioner's spectral tables.  stream: a cudaStream_t or
+ * NULL.  *out receives the handle. */
+int gmrf_create(const gmrf_desc* desc, void* stream, gmrf_problem** out);
+
+/* Number of cells n of a problem. */
+int gmrf_size(const gmrf_problem* p, int64_t* n);
+
+/* Section 4, Algorithm 1 (+ Proposition 1 when preconditioned): writes
+ * x_out [nsamples][n] (float for FP32, double for FP64; host or device) and
+ * info [nsamples] (host, may be NULL).  Returns the worst per-vector status. */
+int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* opts, void* x_out, gmrf_result_info* info);
+
+/* Section 6 (+ Section 6.2 when preconditioned): *logdet = mean_i q_i +
+ * log det M + n log tau, *std_err = sd(q_i)/sqrt(N) (NaN for N == 1),
+ * q_out [nprobes] (host, may be NULL) = the per-probe terms
+ * ||v_i||^2 e_1^T log(T_m) e_1 of the (preconditioned) operator, info as for
+ * gmrf_sample.  logdet and std_err are host pointers. */
+int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* opts, double* logdet, double* std_err,
+                double* q_out, gmrf_result_info* info);
+
+/* Matrix-free operator applies on nvec vectors of the problem's precision
+ * (Section 2's "routine that computes the matrix-vector product"), for
+ * testing and for callers composing their own solvers:
+ *   which = 0: y = Q v
+ *   which = 1: y = A v, A = M^{-1/2} Q M^{-1/2} (Proposition 1; needs a preconditioner)
+ *   which = 2: y = M^{-1/2} v                  (needs a preconditioner)
+ * v and y are [nvec][n], host or device, must not overlap. */
+int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void* y);
+
+/* Device Philox-4x32-10 streams (the z of Algorithm 1 and the probes of
+ * Section 6), [nvec][n]:
+ *   kind 0 = N(0,1) (float if precision == GMRF_FP32, else double),
+ *   kind 1 = Rademacher +-1 (same types),
+ *   kind 2 = the raw 32-bit words of the Gaussian stream ([nvec][4*ceil(n/4)] uint32).
+ * out: host or device; stream: cudaStream_t or NULL. */
+int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t seed, void* out,
+             void* stream);
+
+/* Tracing (a build facility, not a step of the paper's method): launch counts
+ * and CUDA-event timing of the library's kernels by class, for profiling and
+ * the roofline report.  Classes: 0 fused stencil step, 1 preconditioned
+ * row-forward, 2 column transform, 3 row-mid, 4 row-last, 5 ||z||, 6 Philox,
+ * 7 T_m functions, 8 assembly, 9 plain preconditioner applies, 10 other.
+ *   op 0: reset counters and times;  op 1: enable event timing (events are
+ *   recorded around every launch on its stream);  op 2: disable timing;
+ *   op 3: query class kclass (-1 = all): *total_ms = summed kernel time,
+ *   *launches = kernel launches, *timed = launches that were timed.
+ * Process-wide, not thread-safe; any output pointer may be NULL. */
+int gmrf_trace(int32_t op, int32_t kclass, double* total_ms, int64_t* launches, int64_t* timed);
+
+void gmrf_destroy(gmrf_problem* p);
+const char* gmrf_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMRF_H */

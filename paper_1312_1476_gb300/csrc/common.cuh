@@ -1,0 +1,365 @@
+// common.cuh -- device helpers shared by the Lanczos kernels.
+//
+// * compensated FP32 ("double-float") sums for the dot products of the
+//   Lanczos recurrence: GB300's FP64 rate is a small fraction of its FP32
+//   rate, so every per-element and per-warp reduction of the FP32 path runs
+//   on pairs of floats and only the final per-vector sums are FP64;
+// * the per-vector iteration state and the end-of-step logic shared by the
+//   stencil and the preconditioned step kernels: alpha_j, beta_j
+//   (Algorithm 1), the LDL^T recurrence of T_m, and the stopping rule built
+//   on the a-posteriori bound of Theorem 1 (eq. krylov_bound);
+// * Philox-4x32-10 (Salmon et al., SC'11) for z and the Rademacher probes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gmrf.h"
+
+namespace gmrf {
+
+// ----------------------------------------------------------------- status codes
+enum : int { VS_RUNNING = 1, VS_DONE = 0 };  // other values: negative gmrf error codes
+
+// --------------------------------------------------------- compensated float sums
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, e);
+}
+// exact product a*b as an unevaluated pair
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ df df_shfl_down(df v, int off) {
+  return {__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+}
+__device__ __forceinline__ double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
+
+// Accumulator of the three dot products of one Lanczos step:
+//   s1 = v_j . q, s2 = q . q, s3 = v_j . v_j  (all for one vector).
+template <typename T>
+struct Dots;
+
+template <>
+struct Dots<float> {
+  df s1, s2, s3;
+  __device__ __forceinline__ void zero() { s1 = s2 = s3 = {0.f, 0.f}; }
+  __device__ __forceinline__ void add(float v, float q) {
+    s1 = df_add(s1, two_prod(v, q));
+    s2 = df_add(s2, two_prod(q, q));
+    s3 = df_add(s3, two_prod(v, v));
+  }
+  __device__ __forceinline__ void merge(const Dots& o) {
+    s1 = df_add(s1, o.s1);
+    s2 = df_add(s2, o.s2);
+    s3 = df_add(s3, o.s3);
+  }
+  __device__ __forceinline__ Dots shfl_down(int off) const {
+    Dots r;
+    r.s1 = df_shfl_down(s1, off);
+    r.s2 = df_shfl_down(s2, off);
+    r.s3 = df_shfl_down(s3, off);
+    return r;
+  }
+  __device__ __forceinline__ void get(double& a, double& b, double& c) const {
+    a = df_to_double(s1);
+    b = df_to_double(s2);
+    c = df_to_double(s3);
+  }
+};
+
+template <>
+struct Dots<double> {
+  double s1, s2, s3;
+  __device__ __forceinline__ void zero() { s1 = s2 = s3 = 0.0; }
+  __device__ __forceinline__ void add(double v, double q) {
+    s1 = fma(v, q, s1);
+    s2 = fma(q, q, s2);
+    s3 = fma(v, v, s3);
+  }
+  __device__ __forceinline__ void merge(const Dots& o) {
+    s1 += o.s1;
+    s2 += o.s2;
+    s3 += o.s3;
+  }
+  __device__ __forceinline__ Dots shfl_down(int off) const {
+    Dots r;
+    r.s1 = __shfl_down_sync(0xffffffffu, s1, off);
+    r.s2 = __shfl_down_sync(0xffffffffu, s2, off);
+    r.s3 = __shfl_down_sync(0xffffffffu, s3, off);
+    return r;
+  }
+  __device__ __forceinline__ void get(double& a, double& b, double& c) const {
+    a = s1;
+    b = s2;
+    c = s3;
+  }
+};
+
+// Fixed-order block reduction (result valid in thread 0).  `scratch` must
+// hold blockDim/32 entries.  The tree depends only on the block shape.
+template <typename A>
+__device__ __forceinline__ A block_reduce(A v, A* scratch) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y * blockDim.z) >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v.merge(v.shfl_down(off));
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    A w;
+    if (lane < nwarps) w = scratch[lane];
+    else w.zero();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) w.merge(w.shfl_down(off));
+    v = w;
+  }
+  __syncthreads();
+  return v;
+}
+
+// ------------------------------------------------------------- iteration state
+// One record per vector (sample z or probe v) of a Lanczos batch.
+struct VecState {
+  int status;     // VS_RUNNING, VS_DONE or a negative gmrf error code
+  int m;          // completed steps = number of alpha values
+  double znorm;   // ||z||
+  double d_prev;  // LDL^T pivot d_{m-1} of T_m
+  double u_prev;  // u_{m-1} = (L^{-1} e_1)_{m-1}
+  double energy;  // e_1^T T_m^{-1} e_1 = sum_i u_i^2 / d_i
+  double theta;   // smallest Ritz value theta_min (upper estimate)
+  double err_est; // relative Theorem 1 estimate at m
+  double amax;    // max |alpha_i|
+  double bmax;    // max beta_i
+  double beta_last;  // beta_{m-1}
+  double pad;
+};
+
+struct StepParams {
+  int j;          // index of the basis vector formed in this step (0-based)
+  int m_max;      // largest subspace size
+  int nslots;     // ring size of the stored basis (m_max + 1, or 2 when V_m is not kept)
+  int n_sturm;    // unused padding
+  double tol;     // stopping tolerance on the relative estimate
+  double bd_tol;  // breakdown threshold relative to ||T_m||
+};
+
+// Count of eigenvalues of T_m below sigma (Sturm sequence of the LDL^T pivots
+// of T_m - sigma I), in FP32 on float copies of alpha and beta^2.
+__device__ __forceinline__ int sturm_count(const float* __restrict__ af, const float* __restrict__ b2f, int m,
+                                           float sigma) {
+  int cnt = 0;
+  float d = 1.f;
+  for (int i = 0; i < m; ++i) {
+    float a = af[i] - sigma;
+    d = (i == 0) ? a : a - __fdividef(b2f[i - 1], d);
+    if (fabsf(d) < 1e-30f) d = -1e-30f;
+    cnt += (d < 0.f);
+  }
+  return cnt;
+}
+
+// Smallest eigenvalue of T_m by multisection over the block's threads on a
+// geometric grid below `hi` (an upper bound).  All threads of the block call
+// it; the result is returned to every thread.  Relative resolution after two
+// rounds with 256+ threads is ~1e-4, ample for the bound's lambda_min^{-1/2}.
+__device__ __noinline__ static double smallest_ritz(const float* af, const float* b2f, int m, double hi_in, int* s_int,
+                                float* s_flt) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  float hi = (float)(hi_in * 1.0001) + 1e-30f;
+  float lo = hi * 1e-8f;
+  for (int round = 0; round < 8; ++round) {
+    // points p_t = lo * (hi/lo)^((t+1)/nt), t = 0..nt-1 ; p_{nt-1} = hi
+    float lr = __logf(hi / lo);
+    float p = lo * __expf(lr * (float)(tid + 1) / (float)nt);
+    if (tid == nt - 1) p = hi;
+    int c = sturm_count(af, b2f, m, p);
+    if (tid == 0) s_int[0] = nt;  // first index with count >= 1
+    __syncthreads();
+    if (c >= 1) atomicMin(&s_int[0], tid);
+    int c_lo = (tid == 0) ? sturm_count(af, b2f, m, lo) : 0;
+    __syncthreads();
+    if (tid == 0) {
+      int t = s_int[0];
+      float nlo = lo, nhi = hi;
+      int again = 0;
+      if (c_lo >= 1) {          // theta_min below lo: move the window down
+        nhi = lo;
+        nlo = lo * 1e-8f;
+        again = (nlo > 1e-35f) ? 2 : 3;
+      } else if (t == nt) {     // hi was not an upper bound: widen up
+        nlo = hi;
+        nhi = hi * 1e4f;
+        again = 2;
+      } else {
+        nhi = lo * __expf(lr * (float)(t + 1) / (float)nt);
+        if (t == nt - 1) nhi = hi;
+        nlo = (t == 0) ? lo : lo * __expf(lr * (float)t / (float)nt);
+        again = (round == 0) ? 1 : 0;  // two refinement rounds
+      }
+      s_flt[0] = nlo;
+      s_flt[1] = nhi;
+      s_int[1] = again;
+    }
+    __syncthreads();
+    lo = s_flt[0];
+    hi = s_flt[1];
+    int again = s_int[1];
+    __syncthreads();
+    if (again == 0 || again == 3) break;
+  }
+  return (double)hi;
+}
+
+// End of a Lanczos step for vector s, run by the last block of that vector
+// (every thread of the block calls it).  Sums the per-block partial dot
+// products in a fixed order, forms alpha_j and beta_j, advances the LDL^T
+// recurrence of T_m and applies the stopping rule:
+//   est = theta_min^{-1/2} ||r_m|| / ||x_m||,
+//   ||r_m|| / ||z|| = beta_{m-1} |u_{m-1} / d_{m-1}|,  ||x_m|| / ||z|| = sqrt(e_1^T T_m^{-1} e_1).
+template <typename T>
+__device__ static void finish_step(const StepParams& P, int s, const Dots<T>* __restrict__ partials, int nblk,
+                            VecState* __restrict__ st, double* __restrict__ alpha, double* __restrict__ beta,
+                            float* __restrict__ alpha_f, float* __restrict__ beta2_f, Dots<T>* red_scratch,
+                            int* s_int, float* s_flt) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  Dots<T> acc;
+  acc.zero();
+  for (int b = tid; b < nblk; b += nt) acc.merge(partials[(size_t)s * nblk + b]);
+  acc = block_reduce(acc, red_scratch);
+  __shared__ int s_need_theta;
+  __shared__ double s_theta_hi, s_pfac;
+  const int j = P.j;
+  const size_t mo = (size_t)s * P.m_max;
+  if (tid == 0) {
+    double s1, s2, s3;
+    acc.get(s1, s2, s3);
+    VecState v = st[s];
+    double a = s1;
+    double b2 = s2 - 2.0 * a * s1 + a * a * s3;
+    double b = b2 > 0.0 ? sqrt(b2) : 0.0;
+    alpha[mo + j] = a;
+    beta[mo + j] = b;
+    alpha_f[mo + j] = (float)a;
+    beta2_f[mo + j] = (float)(b * b);
+    // LDL^T of T_m: d_0 = a_0, d_j = a_j - b_{j-1}^2 / d_{j-1}; u_0 = 1, u_j = -(b_{j-1}/d_{j-1}) u_{j-1}
+    double d, u;
+    if (j == 0) {
+      d = a;
+      u = 1.0;
+      v.energy = 0.0;
+      v.amax = 0.0;
+      v.bmax = 0.0;
+      v.theta = a;
+    } else {
+      double bp = v.beta_last;
+      d = a - bp * bp / v.d_prev;
+      u = -(bp / v.d_prev) * v.u_prev;
+    }
+    v.m = j + 1;
+    v.beta_last = b;
+    v.amax = fmax(v.amax, fabs(a));
+    v.bmax = fmax(v.bmax, b);
+    int need = 0;
+    if (!(isfinite(a) && isfinite(b) && isfinite(d))) {
+      v.status = GMRF_ERR_NUMERIC;
+    } else if (d <= 0.0 || a <= 0.0) {
+      v.status = GMRF_ERR_NOT_SPD;
+    } else {
+      v.energy += u * u / d;
+      v.d_prev = d;
+      v.u_prev = u;
+      double pfac = b * fabs(u / d) / sqrt(v.energy);  // ||r_m|| / ||x_m||
+      if (b <= P.bd_tol * (v.amax + v.bmax)) {
+        v.status = VS_DONE;  // invariant Krylov subspace: x_m is exact
+        v.err_est = 0.0;
+        need = 1;            // theta still wanted for the T_m function
+      } else {
+        double est_lb = pfac / sqrt(v.theta);  // theta >= theta_min(T_m): a lower bound of est
+        v.err_est = est_lb;
+        if (est_lb <= P.tol || j + 1 >= P.m_max) need = 1;
+      }
+      s_pfac = pfac;
+    }
+    s_need_theta = need;
+    s_theta_hi = v.theta;
+    st[s] = v;
+  }
+  __syncthreads();
+  if (s_need_theta) {
+    double th = smallest_ritz(alpha_f + mo, beta2_f + mo, j + 1, s_theta_hi, s_int, s_flt);
+    if (tid == 0) {
+      VecState v = st[s];
+      v.theta = th;
+      if (v.status == VS_RUNNING) {
+        double est = s_pfac / sqrt(th);
+        v.err_est = est;
+        if (est <= P.tol) v.status = VS_DONE;
+        else if (j + 1 >= P.m_max) v.status = GMRF_ERR_NOT_CONVERGED;
+      }
+      st[s] = v;
+    }
+  }
+}
+
+// Last-block election: returns true in every thread of the block that is the
+// last of the `nblk` blocks of vector s to finish (counter reset by it).
+__device__ __forceinline__ bool last_block(unsigned* counter, int s, int nblk, int* s_flag) {
+  __threadfence();
+  __syncthreads();
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (tid == 0) {
+    unsigned t = atomicAdd(&counter[s], 1u);
+    int last = (t == (unsigned)(nblk - 1));
+    if (last) counter[s] = 0u;
+    *s_flag = last;
+  }
+  __syncthreads();
+  if (*s_flag) __threadfence();
+  return *s_flag != 0;
+}
+
+// ------------------------------------------------------------------- Philox
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t lo0 = 0xD2511F53u * c[0];
+    uint32_t hi0 = __umulhi(0xD2511F53u, c[0]);
+    uint32_t lo1 = 0xCD9E8D57u * c[2];
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    uint32_t n0 = hi1 ^ c[1] ^ k0;
+    uint32_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+}  // namespace gmrf

@@ -1,0 +1,516 @@
+// gmrf_api.cu -- the C ABI (include/gmrf.h) and the host driver.
+//
+// The driver validates arguments, sizes the device workspaces from free HBM,
+// stages host buffers, and issues the kernels of one call on the problem's
+// stream:
+//   noise (Philox) or caller z  ->  ||z||                   (Algorithm 1, start)
+//   repeat: fused Lanczos steps, c at a time, then one poll of the per-vector
+//           convergence flags                              (Algorithm 1 loop, Theorem 1)
+//   T_m^{-1/2} e_1 (rational approximation)  ->  x = ||z|| V_m y  (last step)
+//   preconditioned problems: x = M^{-1/2} u                 (Proposition 1)
+// Vectors that converge early stop doing work (their kernels exit at entry).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "precond.h"
+#include "trace.h"
+
+using namespace gmrf;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+int ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return GMRF_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRF_ERR_OOM;
+  }
+  b.bytes = bytes;
+  return GMRF_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+#define CK(x)                               \
+  do {                                      \
+    cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) {                \
+      cudaGetLastError();                   \
+      return GMRF_ERR_CUDA;                 \
+    }                                       \
+  } while (0)
+#define CKR(x)                 \
+  do {                         \
+    int r_ = (x);              \
+    if (r_ != GMRF_OK) return r_; \
+  } while (0)
+
+}  // namespace
+
+struct gmrf_problem {
+  Grid g;
+  int precond = GMRF_PREC_NONE;
+  bool fp64 = false;
+  double tau = 1.0;
+  double kappa2_const = 0.0;
+  double kbar2 = 0.0;
+  double logdet_M = 0.0;  // log det of the tau-free preconditioner (B_bar^p)
+  cudaStream_t stream = nullptr;
+  DevBuf kappa2;  // float [n] or empty (constant)
+  PrecondTables pre;
+  // Lanczos workspace (grow-only)
+  DevBuf W0, W1, V, st, alpha, beta, alpha_f, beta2_f, partials, counters, y, scratch, nodes, q, out2, stage,
+      stage2, work;
+  VecState* st_host = nullptr;
+  int st_host_cap = 0;
+};
+
+namespace {
+
+size_t esize(const gmrf_problem* p) { return p->fp64 ? 8 : 4; }
+
+int ensure_host_states(gmrf_problem* p, int nvec) {
+  if (p->st_host_cap >= nvec) return GMRF_OK;
+  if (p->st_host) cudaFreeHost(p->st_host);
+  p->st_host = nullptr;
+  p->st_host_cap = 0;
+  if (cudaMallocHost(&p->st_host, sizeof(VecState) * nvec) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRF_ERR_OOM;
+  }
+  p->st_host_cap = nvec;
+  return GMRF_OK;
+}
+
+// Buffers for a batch of nvec vectors with nslots stored basis vectors each.
+int ensure_lanczos(gmrf_problem* p, int nvec, int nslots, int m_max, bool need_tm, LanczosBufs& b) {
+  const size_t n = p->g.n, es = esize(p);
+  CKR(ensure(p->W0, (size_t)nvec * n * es));
+  CKR(ensure(p->W1, (size_t)nvec * n * es));
+  CKR(ensure(p->V, (size_t)nvec * nslots * n * es));
+  CKR(ensure(p->st, sizeof(VecState) * nvec));
+  CKR(ensure(p->alpha, sizeof(double) * nvec * m_max));
+  CKR(ensure(p->beta, sizeof(double) * nvec * m_max));
+  CKR(ensure(p->alpha_f, sizeof(float) * nvec * m_max));
+  CKR(ensure(p->beta2_f, sizeof(float) * nvec * m_max));
+  int nblk = std::max(stencil_blocks_per_vector(p->g), 256);
+  nblk = std::max(nblk, precond_blocks_per_vector(p->pre));
+  CKR(ensure(p->partials, (size_t)nvec * nblk * sizeof(Dots<double>)));
+  const bool fresh_counters = p->counters.bytes < sizeof(unsigned) * nvec;
+  CKR(ensure(p->counters, sizeof(unsigned) * nvec));
+  if (fresh_counters) CK(cudaMemsetAsync(p->counters.p, 0, sizeof(unsigned) * nvec, p->stream));
+  CKR(ensure(p->nodes, sizeof(TmNodes) * nvec));
+  CKR(ensure(p->y, sizeof(double) * nvec * m_max));
+  CKR(ensure(p->q, sizeof(double) * nvec));
+  if (need_tm) CKR(ensure(p->scratch, sizeof(double) * 2 * (size_t)nvec * m_max * kMaxNodes));
+  CKR(ensure_host_states(p, nvec));
+  b.W[0] = p->W0.p;
+  b.W[1] = p->W1.p;
+  b.V = p->V.p;
+  b.st = (VecState*)p->st.p;
+  b.alpha = (double*)p->alpha.p;
+  b.beta = (double*)p->beta.p;
+  b.alpha_f = (float*)p->alpha_f.p;
+  b.beta2_f = (float*)p->beta2_f.p;
+  b.partials = p->partials.p;
+  b.counters = (unsigned*)p->counters.p;
+  b.nvec = nvec;
+  b.nslots = nslots;
+  b.m_max = m_max;
+  return GMRF_OK;
+}
+
+// Vectors per batch that fit in free device memory.
+int batch_size(gmrf_problem* p, int want, int nslots, int m_max, bool need_tm, size_t extra_per_vec) {
+  size_t freeb = 0, total = 0;
+  if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  // memory already held by this problem's workspace can be reused
+  const size_t held = p->W0.bytes + p->W1.bytes + p->V.bytes + p->scratch.bytes + p->stage.bytes +
+                      p->stage2.bytes + p->work.bytes;
+  const size_t n = p->g.n, es = esize(p);
+  size_t per = (size_t)(nslots + 2) * n * es + extra_per_vec + 64 * (size_t)m_max + 4096;
+  if (need_tm) per += sizeof(double) * 2 * (size_t)m_max * kMaxNodes;
+  const size_t budget = (size_t)((double)(freeb + held) * 0.85);
+  size_t c = budget / per;
+  if (c > (size_t)want) c = want;
+  if (c > 65535) c = 65535;
+  return (int)c;
+}
+
+int worst_status(const VecState* st, int nvec) {
+  int worst = GMRF_OK;
+  for (int s = 0; s < nvec; ++s) {
+    int c = st[s].status;
+    if (c == VS_DONE) continue;
+    if (c == VS_RUNNING) c = GMRF_ERR_NOT_CONVERGED;
+    if (worst == GMRF_OK || (worst == GMRF_ERR_NOT_CONVERGED && c != GMRF_ERR_NOT_CONVERGED)) worst = c;
+  }
+  return worst;
+}
+
+// Runs the Lanczos iteration on the vectors already in W[0].  Returns a
+// gmrf code for launch failures only; per-vector outcomes are in st_host.
+int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, int check_every) {
+  cudaStream_t s = p->stream;
+  CK(traced(KC_INIT, s, 1, [&] { return launch_lanczos_init(p->fp64, p->g.n, b, s); }));
+  StepParams P{};
+  P.m_max = m_max;
+  P.nslots = b.nslots;
+  P.tol = tol;
+  P.bd_tol = p->fp64 ? 1e-13 : 1e-6;
+  const int c = check_every > 0 ? check_every : 16;
+  int j = 0;
+  while (j < m_max) {
+    const int jend = std::min(m_max, j + c);
+    for (; j < jend; ++j) {
+      P.j = j;
+      if (p->precond == GMRF_PREC_NONE)
+        CK(traced(KC_STENCIL_STEP, s, 1,
+                  [&] { return launch_stencil_step(p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s); }));
+      else
+        CK(launch_precond_step(p->pre, p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s));
+    }
+    CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * b.nvec, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    trace_collect();
+    bool running = false;
+    for (int v = 0; v < b.nvec; ++v) running |= (p->st_host[v].status == VS_RUNNING);
+    if (!running) break;
+  }
+  return GMRF_OK;
+}
+
+void fill_info(const VecState* st, int nvec, gmrf_result_info* info) {
+  if (!info) return;
+  for (int s = 0; s < nvec; ++s) {
+    info[s].m_used = st[s].m;
+    int c = st[s].status;
+    if (c == VS_DONE) c = GMRF_OK;
+    if (c == VS_RUNNING) c = GMRF_ERR_NOT_CONVERGED;
+    info[s].status = c;
+    info[s].err_est = st[s].err_est;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gmrf_strerror(int code) {
+  switch (code) {
+    case GMRF_OK: return "ok";
+    case GMRF_ERR_INVALID: return "invalid argument";
+    case GMRF_ERR_OOM: return "out of device memory";
+    case GMRF_ERR_NOT_CONVERGED: return "not converged within m_max";
+    case GMRF_ERR_NOT_SPD: return "operator is not symmetric positive definite";
+    case GMRF_ERR_NUMERIC: return "non-finite value during the iteration";
+    case GMRF_ERR_CUDA: return "CUDA runtime error";
+    case GMRF_ERR_TIMEOUT: return "device wait timed out";
+    case GMRF_ERR_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown error";
+  }
+}
+
+int gmrf_size(const gmrf_problem* p, int64_t* n) {
+  if (!p || !n) return GMRF_ERR_INVALID;
+  *n = (int64_t)p->g.n;
+  return GMRF_OK;
+}
+
+int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
+  if (!d || !out) return GMRF_ERR_INVALID;
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return GMRF_ERR_INVALID;
+  if (d->bc < 0 || d->bc > 2 || d->op < 0 || d->op > 1 || d->precond < 0 || d->precond > 2) return GMRF_ERR_INVALID;
+  if (d->precision != GMRF_FP32 && d->precision != GMRF_FP64) return GMRF_ERR_INVALID;
+  if (d->reserved != 0) return GMRF_ERR_INVALID;
+  if (d->nx < 2 || d->ny < 2 || (d->dim == 3 && d->nz < 2)) return GMRF_ERR_INVALID;
+  if (d->nx > (1 << 30) || d->ny > (1 << 30) || (d->dim == 3 && d->nz > (1 << 30))) return GMRF_ERR_INVALID;
+  if (!(d->tau > 0.0) || !std::isfinite(d->tau)) return GMRF_ERR_INVALID;
+  const int64_t nz = d->dim == 3 ? d->nz : 1;
+  const double nd = (double)d->nx * (double)d->ny * (double)nz;
+  if (nd > 4.0e9) return GMRF_ERR_INVALID;
+  if (!d->kappa2 && (!(d->kappa2_const >= 0.0) || !std::isfinite(d->kappa2_const))) return GMRF_ERR_INVALID;
+  if (d->dim == 3 && d->op == GMRF_OP_SPDE_SQUARED) return GMRF_ERR_UNSUPPORTED;
+  if (d->precond != GMRF_PREC_NONE) {
+    if (d->dim != 2) return GMRF_ERR_UNSUPPORTED;
+    if (!precond_size_ok(d->nx) || !precond_size_ok(d->ny)) return GMRF_ERR_UNSUPPORTED;
+    if (!(d->kappa2_precond <= 0.0 || std::isfinite(d->kappa2_precond))) return GMRF_ERR_INVALID;
+  }
+  gmrf_problem* p = new (std::nothrow) gmrf_problem();
+  if (!p) return GMRF_ERR_OOM;
+  p->g.dim = d->dim;
+  p->g.nx = (int)d->nx;
+  p->g.ny = (int)d->ny;
+  p->g.nz = (int)nz;
+  p->g.n = (size_t)d->nx * d->ny * nz;
+  p->g.bc = d->bc;
+  p->g.op = d->op;
+  p->precond = d->precond;
+  p->fp64 = d->precision == GMRF_FP64;
+  p->tau = d->tau;
+  p->kappa2_const = d->kappa2_const;
+  p->stream = (cudaStream_t)stream;
+  auto fail = [&](int code) {
+    gmrf_destroy(p);
+    return code;
+  };
+  double sum_log = 0.0, nzero = 0.0;
+  if (d->kappa2) {
+    if (ensure(p->kappa2, sizeof(float) * p->g.n) != GMRF_OK) return fail(GMRF_ERR_OOM);
+    const cudaMemcpyKind kind = is_device_ptr(d->kappa2) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(p->kappa2.p, d->kappa2, sizeof(float) * p->g.n, kind, p->stream) != cudaSuccess)
+      return fail(GMRF_ERR_CUDA);
+    DevBuf stats;
+    if (ensure(stats, 4 * sizeof(double)) != GMRF_OK) return fail(GMRF_ERR_OOM);
+    double h[4] = {0, 0, 0, 0};
+    bool ok = launch_field_stats((const float*)p->kappa2.p, p->g.n, (double*)stats.p, p->stream) == cudaSuccess &&
+              cudaMemcpyAsync(h, stats.p, sizeof(h), cudaMemcpyDeviceToHost, p->stream) == cudaSuccess &&
+              cudaStreamSynchronize(p->stream) == cudaSuccess;
+    release(stats);
+    if (!ok) return fail(GMRF_ERR_CUDA);
+    if (h[0] > 0.5) return fail(GMRF_ERR_INVALID);
+    nzero = h[1];
+    sum_log = h[2];
+    if (d->bc != GMRF_BC_DIRICHLET && nzero > (double)p->g.n - 0.5) return fail(GMRF_ERR_INVALID);
+  } else {
+    if (d->bc != GMRF_BC_DIRICHLET && !(d->kappa2_const > 0.0)) return fail(GMRF_ERR_INVALID);
+    sum_log = d->kappa2_const > 0 ? (double)p->g.n * std::log(d->kappa2_const) : 0.0;
+    nzero = d->kappa2_const > 0 ? 0.0 : (double)p->g.n;
+  }
+  if (d->precond != GMRF_PREC_NONE) {
+    double kb = d->kappa2_precond;
+    if (!(kb > 0.0)) {
+      const double npos = (double)p->g.n - nzero;
+      kb = npos > 0.5 ? std::exp(sum_log / npos) : 0.0;
+    }
+    if (!(kb > 0.0) && d->precond != GMRF_PREC_NONE && d->bc != GMRF_BC_DIRICHLET) return fail(GMRF_ERR_INVALID);
+    if (!(kb > 0.0)) return fail(GMRF_ERR_INVALID);
+    p->kbar2 = kb;
+    const int r = precond_build(p->pre, p->g, d->precond, d->op, kb, p->fp64, p->stream, &p->logdet_M);
+    if (r != GMRF_OK) return fail(r);
+  }
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(GMRF_ERR_CUDA);
+  *out = p;
+  return GMRF_OK;
+}
+
+void gmrf_destroy(gmrf_problem* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  else cudaDeviceSynchronize();
+  DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,
+                    &p->partials, &p->counters, &p->y, &p->scratch, &p->nodes, &p->q, &p->out2, &p->stage,
+                    &p->stage2, &p->work};
+  for (DevBuf* b : bufs) release(*b);
+  precond_free(p->pre);
+  if (p->st_host) cudaFreeHost(p->st_host);
+  delete p;
+}
+
+int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_result_info* info) {
+  if (!p || !o || !x_out) return GMRF_ERR_INVALID;
+  if (!(o->tol > 0.0) || !std::isfinite(o->tol) || o->m_max < 1 || o->m_max > 8192 || o->nsamples < 1 ||
+      o->reserved != 0)
+    return GMRF_ERR_INVALID;
+  const size_t n = p->g.n, es = esize(p);
+  const int m_max = o->m_max;
+  const int nslots = m_max + 1;
+  const bool x_dev = is_device_ptr(x_out);
+  const bool z_dev = o->z_in && is_device_ptr(o->z_in);
+  const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) : 0);
+  int chunk = batch_size(p, o->nsamples, nslots, m_max, true, extra);
+  if (chunk < 1) return GMRF_ERR_OOM;
+  cudaStream_t s = p->stream;
+  std::vector<VecState> all((size_t)o->nsamples);
+  for (int s0 = 0; s0 < o->nsamples; s0 += chunk) {
+    const int c = std::min(chunk, o->nsamples - s0);
+    LanczosBufs b;
+    CKR(ensure_lanczos(p, c, nslots, m_max, true, b));
+    if (o->z_in) {
+      const char* src = (const char*)o->z_in + (size_t)s0 * n * es;
+      CK(cudaMemcpyAsync(b.W[0], src, (size_t)c * n * es, z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         s));
+    } else {
+      CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, c, (int64_t)n, o->seed, s0, b.W[0], s); }));
+    }
+    CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
+    CK(traced(KC_TM, s, 3, [&] {
+      return launch_tm_inv_sqrt(b, p->fp64, (TmNodes*)p->nodes.p, (double*)p->scratch.p, (double*)p->y.p, s);
+    }));
+    void* xdst = (char*)x_out + (size_t)s0 * n * es;
+    if (!x_dev) {
+      CKR(ensure(p->stage, (size_t)c * n * es));
+      xdst = p->stage.p;
+    }
+    if (p->precond == GMRF_PREC_NONE) {
+      CK(traced(KC_ASSEMBLE, s, 1, [&] {
+        return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0 / std::sqrt(p->tau), xdst, s);
+      }));
+    } else {
+      // u = ||z|| V_m y, then x = M^{-1/2} u = tau^{-1/2} B_bar^{-p/2} u (Proposition 1)
+      CKR(ensure(p->work, (size_t)c * n * es));
+      CK(traced(KC_ASSEMBLE, s, 1,
+                [&] { return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
+      CK(traced(KC_PRE_APPLY, s, 3,
+                [&] { return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, p->work.p, xdst, c, s); }));
+      CK(traced(KC_OTHER, s, 1,
+                [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / std::sqrt(p->tau), s); }));
+    }
+    if (!x_dev)
+      CK(cudaMemcpyAsync((char*)x_out + (size_t)s0 * n * es, xdst, (size_t)c * n * es, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * c, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    trace_collect();
+    std::memcpy(all.data() + s0, p->st_host, sizeof(VecState) * c);
+  }
+  fill_info(all.data(), o->nsamples, info);
+  return worst_status(all.data(), o->nsamples);
+}
+
+int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, double* std_err, double* q_out,
+                gmrf_result_info* info) {
+  if (!p || !o || !logdet || !std_err) return GMRF_ERR_INVALID;
+  if (!(o->tol > 0.0) || !std::isfinite(o->tol) || o->m_max < 1 || o->m_max > 8192 || o->nprobes < 1 ||
+      o->reserved != 0)
+    return GMRF_ERR_INVALID;
+  const size_t n = p->g.n, es = esize(p);
+  const int m_max = o->m_max;
+  const bool z_dev = o->probes_in && is_device_ptr(o->probes_in);
+  int chunk = batch_size(p, o->nprobes, 2, m_max, false, 0);
+  if (chunk < 1) return GMRF_ERR_OOM;
+  cudaStream_t s = p->stream;
+  CKR(ensure(p->stage2, sizeof(double) * (o->nprobes + 2)));
+  double* qall = (double*)p->stage2.p;
+  std::vector<VecState> all((size_t)o->nprobes);
+  for (int s0 = 0; s0 < o->nprobes; s0 += chunk) {
+    const int c = std::min(chunk, o->nprobes - s0);
+    LanczosBufs b;
+    CKR(ensure_lanczos(p, c, 2, m_max, false, b));
+    if (o->probes_in) {
+      const char* src = (const char*)o->probes_in + (size_t)s0 * n * es;
+      CK(cudaMemcpyAsync(b.W[0], src, (size_t)c * n * es, z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         s));
+    } else {
+      CK(traced(KC_RNG, s, 1, [&] { return launch_rng(1, p->fp64, c, (int64_t)n, o->seed, s0, b.W[0], s); }));
+    }
+    CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
+    CK(traced(KC_TM, s, 2, [&] { return launch_tm_log(b, p->fp64, (TmNodes*)p->nodes.p, qall + s0, s); }));
+    CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * c, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::memcpy(all.data() + s0, p->st_host, sizeof(VecState) * c);
+  }
+  // log det Q = mean q_i + log det M(tau-free) + n log tau   (Section 6.2, plus sign)
+  const double shift = p->logdet_M + (double)n * std::log(p->tau);
+  CK(traced(KC_TM, s, 1, [&] { return launch_logdet_reduce(qall, o->nprobes, shift, qall + o->nprobes, s); }));
+  double res[2];
+  CK(cudaMemcpyAsync(res, qall + o->nprobes, sizeof(res), cudaMemcpyDeviceToHost, s));
+  if (q_out) CK(cudaMemcpyAsync(q_out, qall, sizeof(double) * o->nprobes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  trace_collect();
+  *logdet = res[0];
+  *std_err = res[1];
+  fill_info(all.data(), o->nprobes, info);
+  return worst_status(all.data(), o->nprobes);
+}
+
+int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void* y) {
+  if (!p || !v || !y || nvec < 1 || nvec > 65535 || which < 0 || which > 2) return GMRF_ERR_INVALID;
+  if (which > 0 && p->precond == GMRF_PREC_NONE) return GMRF_ERR_INVALID;
+  const size_t n = p->g.n, es = esize(p), bytes = (size_t)nvec * n * es;
+  cudaStream_t s = p->stream;
+  const bool vd = is_device_ptr(v), yd = is_device_ptr(y);
+  const void* vin = v;
+  void* yout = y;
+  if (!vd) {
+    CKR(ensure(p->stage, bytes));
+    CK(cudaMemcpyAsync(p->stage.p, v, bytes, cudaMemcpyHostToDevice, s));
+    vin = p->stage.p;
+  }
+  if (!yd) {
+    CKR(ensure(p->stage2, bytes));
+    yout = p->stage2.p;
+  }
+  if (which == 0) {
+    CK(traced(KC_STENCIL_STEP, s, 1, [&] {
+      return launch_stencil_apply(p->g, p->fp64, p->kappa2.p, p->kappa2_const, vin, yout, (int)nvec, s);
+    }));
+    CK(traced(KC_OTHER, s, 1, [&] { return launch_scale(p->fp64, yout, (size_t)nvec * n, p->tau, s); }));
+  } else if (which == 1) {
+    CK(traced(KC_PRE_APPLY, s, 5, [&] {
+      return launch_precond_operator(p->pre, p->g, p->fp64, p->kappa2.p, p->kappa2_const, vin, yout, (int)nvec, s);
+    }));
+  } else {
+    CK(traced(KC_PRE_APPLY, s, 3,
+              [&] { return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, vin, yout, (int)nvec, s); }));
+    CK(traced(KC_OTHER, s, 1, [&] { return launch_scale(p->fp64, yout, (size_t)nvec * n, 1.0 / std::sqrt(p->tau), s); }));
+  }
+  if (!yd) CK(cudaMemcpyAsync(y, yout, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  trace_collect();
+  return GMRF_OK;
+}
+
+int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t seed, void* out, void* stream) {
+  if (!out || kind < 0 || kind > 2 || nvec < 1 || n < 1 || nvec > 65535 || n > ((int64_t)1 << 34)) return GMRF_ERR_INVALID;
+  if (precision != GMRF_FP32 && precision != GMRF_FP64) return GMRF_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool fp64 = precision == GMRF_FP64;
+  const size_t es = kind == 2 ? 4 : (fp64 ? 8 : 4);
+  const size_t per = kind == 2 ? (size_t)4 * ((n + 3) / 4) : (size_t)n;
+  const size_t bytes = (size_t)nvec * per * es;
+  if (is_device_ptr(out)) {
+    CK(launch_rng(kind, fp64, nvec, n, seed, 0, out, s));
+    CK(cudaStreamSynchronize(s));
+    return GMRF_OK;
+  }
+  void* d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRF_ERR_OOM;
+  }
+  int rc = GMRF_OK;
+  if (launch_rng(kind, fp64, nvec, n, seed, 0, d, s) != cudaSuccess ||
+      cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    rc = GMRF_ERR_CUDA;
+  }
+  cudaFree(d);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// internal.h -- launchers shared between the kernel translation units and the
+// host driver (gmrf_api.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gmrf {
+
+// Geometry + operator of a lattice problem, as the kernels see it.
+struct Grid {
+  int dim;
+  int nx, ny, nz;
+  size_t n;
+  int bc;   // gmrf_bc
+  int op;   // gmrf_op
+};
+
+// Per-batch Lanczos buffers (all device pointers).  Element type T is float
+// or double; `V` holds `nslots` basis vectors per vector:
+// V[(s * nslots + slot) * n + i].
+struct LanczosBufs {
+  void* W[2];          // q of the previous / current step, [nvec][n]
+  void* V;             // basis ring
+  VecState* st;        // [nvec]
+  double* alpha;       // [nvec][m_max]
+  double* beta;        // [nvec][m_max]
+  float* alpha_f;      // [nvec][m_max]
+  float* beta2_f;      // [nvec][m_max]
+  void* partials;      // [nvec][max blocks] Dots<T>
+  unsigned* counters;  // [nvec]
+  int nvec;
+  int nslots;
+  int m_max;
+};
+
+// lanczos_stencil.cu --------------------------------------------------------
+// Blocks per vector of the fused stencil step for this grid.
+int stencil_blocks_per_vector(const Grid& g);
+// Fused step j of Algorithm 1 with the matrix-free stencil Q: forms v_j,
+// stores it, q_j = Q v_j - beta_{j-1} v_{j-1}, dot products, alpha_j, beta_j,
+// stopping rule.  W[j&1] is read, W[(j+1)&1] written.
+cudaError_t launch_stencil_step(const Grid& g, bool fp64, const void* kappa2, double kappa2_const,
+                                const LanczosBufs& b, const StepParams& P, cudaStream_t s);
+// y = Q v for nvec vectors (no Lanczos bookkeeping).
+cudaError_t launch_stencil_apply(const Grid& g, bool fp64, const void* kappa2, double kappa2_const,
+                                 const void* v, void* y, int nvec, cudaStream_t s);
+
+// misc.cu --------------------------------------------------------------------
+cudaError_t launch_rng(int kind, bool fp64, int64_t nvec, int64_t n, uint64_t seed, int64_t soff, void* out,
+                       cudaStream_t s);
+// out4[0] = #(kappa2 < 0 or not finite), [1] = #zeros, [2] = sum log kappa2 over positives.
+cudaError_t launch_field_stats(const float* k, size_t n, double* out4, cudaStream_t s);
+// ||z|| of each vector of W[0] into st[].znorm, and resets the state.
+cudaError_t launch_lanczos_init(bool fp64, size_t n, const LanczosBufs& b, cudaStream_t s);
+// x[s] = scale[s] * V_m y  (scale = ||z|| * extra), y from tm buffers.
+cudaError_t launch_assemble(bool fp64, size_t n, const LanczosBufs& b, const double* y, int y_stride,
+                            double extra_scale, void* x, cudaStream_t s);
+cudaError_t launch_convert(bool to_fp64, const void* in, void* out, size_t count, cudaStream_t s);
+cudaError_t launch_scale(bool fp64, void* x, size_t count, double a, cudaStream_t s);
+
+// tridiag.cu ----------------------------------------------------------------
+struct TmNodes {
+  double s_lo;  // first node
+  double h;     // node spacing
+  int L;        // number of nodes
+  int pad;
+};
+constexpr int kMaxNodes = 384;
+// y[s] = T_m^{-1/2} e_1 (rational approximation from the Stieltjes integral),
+// y stride = m_max.  scratch: >= nvec * kMaxNodes * m_max * 2 doubles.
+cudaError_t launch_tm_inv_sqrt(const LanczosBufs& b, bool fp64, TmNodes* nodes, double* scratch, double* y,
+                               cudaStream_t s);
+// q[s] = ||v_s||^2 e_1^T log(T_m) e_1 (Gauss quadrature, rational form).
+cudaError_t launch_tm_log(const LanczosBufs& b, bool fp64, TmNodes* nodes, double* q, cudaStream_t s);
+// out[0] = mean(q) + shift, out[1] = sd(q)/sqrt(N) (one block).
+cudaError_t launch_logdet_reduce(const double* q, int nq, double shift, double* out, cudaStream_t s);
+
+}  // namespace gmrf

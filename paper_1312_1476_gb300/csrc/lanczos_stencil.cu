@@ -1,0 +1,397 @@
+// lanczos_stencil.cu -- one Lanczos step of Algorithm 1 fused with the
+// matrix-free lattice apply of Q (Section 2: "a routine that computes the
+// matrix-vector product without ever forming or storing Q").
+//
+// Step j (0-based) for vector s, in one pass over the grid:
+//   v_j   = (q_{j-1} - alpha_{j-1} v_{j-1}) / beta_{j-1}     (v_0 = z / ||z||)
+//           formed on load from W_in = q_{j-1} and the stored v_{j-1}, also
+//           on the halo cells, and written to the basis ring;
+//   q_j   = Q v_j - beta_{j-1} v_{j-1}                         -> W_out
+//   sums  v_j.q_j, q_j.q_j, v_j.v_j  (compensated FP32 or FP64)
+// and the last block of the vector forms alpha_j = v_j.q_j and
+//   beta_j = ||q_j - alpha_j v_j|| = sqrt(q.q - 2 alpha v.q + alpha^2 v.v)
+// and applies the stopping rule (common.cuh).
+//
+// Stencils (difference form: (L v)_i = sum over existing edges (v_i - v_nb),
+// which keeps the FP32 rounding relative to the result for smooth v):
+//   shifted:  B v = kappa^2 v + L v            (5-point 2-D, 7-point 3-D)
+//   squared:  Q v = B (B v)                    (13-point 2-D, two passes in smem)
+// 2-D: 32x16 tiles with a halo of 1 (shifted) or 2 (squared) in shared memory.
+// 3-D: 32x16 tiles in x-y marching over a chunk of z planes; the centre
+// column is kept in registers, the plane with its x-y halo in shared memory.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace gmrf {
+namespace {
+
+constexpr int TX = 32;
+constexpr int TY = 16;
+constexpr int NT = TX * TY;
+
+template <typename T>
+struct StencilArgs {
+  const T* Win;
+  T* Wout;
+  T* V;  // basis ring base
+  const float* kappa2;
+  T kappa2_const;
+  int nx, ny, nz;
+  size_t n;
+  int nzc;  // z chunks (3-D)
+  StepParams P;
+  VecState* st;
+  double* alpha;
+  double* beta;
+  float* alpha_f;
+  float* beta2_f;
+  Dots<T>* partials;
+  unsigned* counters;
+};
+
+__device__ __forceinline__ int wrapi(int g, int n) {
+  g %= n;
+  return g < 0 ? g + n : g;
+}
+
+template <typename T>
+__device__ __forceinline__ T kap_at(const float* k, T kc, size_t i) {
+  return k ? (T)__ldg(k + i) : kc;
+}
+
+// B applied at smem position (cx, cy) of array a with pitch W, for the cell at
+// global (gx, gy) with coefficient kap.  Neumann edges leaving the grid are
+// absent; Dirichlet and periodic neighbours come from the (zero / wrapped) halo.
+template <typename T, int BC, int W>
+__device__ __forceinline__ T bop2(const T* a, int cx, int cy, int gx, int gy, int nx, int ny, T kap) {
+  const T c = a[cy * W + cx];
+  T r = kap * c;
+  if (BC != GMRF_BC_NEUMANN || gx > 0) r += c - a[cy * W + cx - 1];
+  if (BC != GMRF_BC_NEUMANN || gx < nx - 1) r += c - a[cy * W + cx + 1];
+  if (BC != GMRF_BC_NEUMANN || gy > 0) r += c - a[(cy - 1) * W + cx];
+  if (BC != GMRF_BC_NEUMANN || gy < ny - 1) r += c - a[(cy + 1) * W + cx];
+  return r;
+}
+
+// STEP = true: fused Lanczos step.  STEP = false: y = Q v (Win = v, Wout = y).
+template <typename T, int OP, int BC, bool STEP>
+__global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
+  constexpr int H = (OP == GMRF_OP_SPDE_SQUARED) ? 2 : 1;
+  constexpr int VW = TX + 2 * H, VH = TY + 2 * H;
+  constexpr int GW = TX + 2, GH = TY + 2;
+  __shared__ T vs[VH * VW];
+  __shared__ T gs[(OP == GMRF_OP_SPDE_SQUARED) ? GH * GW : 1];
+  __shared__ Dots<T> red[NT / 32];
+  __shared__ int s_int[4];
+  __shared__ float s_flt[4];
+
+  const int s = blockIdx.z;
+  const int j = a.P.j;
+  if (STEP && a.st[s].status != VS_RUNNING) return;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int nx = a.nx, ny = a.ny;
+  const size_t n = a.n;
+  const T* Win = a.Win + (size_t)s * n;
+  const T* Vp = nullptr;
+  T* Vc = nullptr;
+  T coef = 0, inv_b = 1, bprev = 0;
+  if (STEP) {
+    const size_t base = (size_t)s * a.P.nslots;
+    Vc = a.V + (base + (size_t)(j % a.P.nslots)) * n;
+    if (j == 0) {
+      inv_b = (T)(1.0 / a.st[s].znorm);
+    } else {
+      Vp = a.V + (base + (size_t)((j - 1) % a.P.nslots)) * n;
+      const size_t mo = (size_t)s * a.P.m_max + (j - 1);
+      coef = (T)a.alpha[mo];
+      bprev = (T)a.beta[mo];
+      inv_b = (T)(1.0 / a.beta[mo]);
+    }
+  }
+  // ---- load v_j on tile + halo
+  for (int idx = tid; idx < VH * VW; idx += NT) {
+    const int cy = idx / VW, cx = idx - cy * VW;
+    int gx = x0 - H + cx, gy = y0 - H + cy;
+    bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    if (!in && BC == GMRF_BC_PERIODIC) {
+      gx = wrapi(gx, nx);
+      gy = wrapi(gy, ny);
+      in = true;
+    }
+    T val = 0;
+    if (in) {
+      const size_t i = (size_t)gx + (size_t)nx * gy;
+      const T w = Win[i];
+      if (!STEP) val = w;
+      else if (j == 0) val = w * inv_b;
+      else val = (w - coef * Vp[i]) * inv_b;
+    }
+    vs[idx] = val;
+  }
+  __syncthreads();
+  if (OP == GMRF_OP_SPDE_SQUARED) {
+    for (int idx = tid; idx < GH * GW; idx += NT) {
+      const int py = idx / GW, px = idx - py * GW;
+      int gx = x0 - 1 + px, gy = y0 - 1 + py;
+      bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+      if (!in && BC == GMRF_BC_PERIODIC) {
+        gx = wrapi(gx, nx);
+        gy = wrapi(gy, ny);
+        in = true;
+      }
+      T g = 0;
+      if (in) {
+        const T kap = kap_at<T>(a.kappa2, a.kappa2_const, (size_t)gx + (size_t)nx * gy);
+        g = bop2<T, BC, VW>(vs, px + 1, py + 1, gx, gy, nx, ny, kap);
+      }
+      gs[idx] = g;
+    }
+    __syncthreads();
+  }
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool own = gx < nx && gy < ny;
+  Dots<T> d;
+  d.zero();
+  if (own) {
+    const size_t i = (size_t)gx + (size_t)nx * gy;
+    const T kap = kap_at<T>(a.kappa2, a.kappa2_const, i);
+    T qv;
+    if (OP == GMRF_OP_SPDE_SQUARED) qv = bop2<T, BC, GW>(gs, tx + 1, ty + 1, gx, gy, nx, ny, kap);
+    else qv = bop2<T, BC, VW>(vs, tx + H, ty + H, gx, gy, nx, ny, kap);
+    if (!STEP) {
+      a.Wout[(size_t)s * n + i] = qv;
+    } else {
+      const T v = vs[(ty + H) * VW + tx + H];
+      T q = qv;
+      if (j > 0) q -= bprev * Vp[i];
+      a.Wout[(size_t)s * n + i] = q;
+      Vc[i] = v;
+      d.add(v, q);
+    }
+  }
+  if (!STEP) return;
+  d = block_reduce(d, red);
+  const int nblk = gridDim.x * gridDim.y;
+  if (tid == 0) a.partials[(size_t)s * nblk + blockIdx.x + gridDim.x * blockIdx.y] = d;
+  if (last_block(a.counters, s, nblk, &s_int[3]))
+    finish_step<T>(a.P, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
+}
+
+// 3-D shifted Laplacian (7-point), z-march over a chunk of planes.
+template <typename T, int BC, bool STEP>
+__global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
+  constexpr int PW = TX + 2, PH = TY + 2;
+  __shared__ T ps[PH * PW];
+  __shared__ Dots<T> red[NT / 32];
+  __shared__ int s_int[4];
+  __shared__ float s_flt[4];
+  const int s = blockIdx.z / a.nzc;
+  const int zc = blockIdx.z - s * a.nzc;
+  const int j = a.P.j;
+  if (STEP && a.st[s].status != VS_RUNNING) return;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const size_t n = a.n, plane = (size_t)nx * ny;
+  const int zper = (nz + a.nzc - 1) / a.nzc;
+  const int z0 = zc * zper, z1 = min(nz, z0 + zper);
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const T* Win = a.Win + (size_t)s * n;
+  const T* Vp = nullptr;
+  T* Vc = nullptr;
+  T coef = 0, inv_b = 1, bprev = 0;
+  if (STEP) {
+    const size_t base = (size_t)s * a.P.nslots;
+    Vc = a.V + (base + (size_t)(j % a.P.nslots)) * n;
+    if (j == 0) {
+      inv_b = (T)(1.0 / a.st[s].znorm);
+    } else {
+      Vp = a.V + (base + (size_t)((j - 1) % a.P.nslots)) * n;
+      const size_t mo = (size_t)s * a.P.m_max + (j - 1);
+      coef = (T)a.alpha[mo];
+      bprev = (T)a.beta[mo];
+      inv_b = (T)(1.0 / a.beta[mo]);
+    }
+  }
+  // value of v_j at global (gx, gy, gz); out-of-grid per boundary condition
+  auto form = [&](int gx, int gy, int gz, T* vp_out) -> T {
+    bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+    if (!in && BC == GMRF_BC_PERIODIC) {
+      gx = wrapi(gx, nx);
+      gy = wrapi(gy, ny);
+      gz = wrapi(gz, nz);
+      in = true;
+    }
+    if (!in) {
+      if (vp_out) *vp_out = 0;
+      return 0;
+    }
+    const size_t i = (size_t)gx + (size_t)nx * gy + plane * gz;
+    const T w = Win[i];
+    if (!STEP) return w;
+    if (j == 0) {
+      if (vp_out) *vp_out = 0;
+      return w * inv_b;
+    }
+    const T vp = Vp[i];
+    if (vp_out) *vp_out = vp;
+    return (w - coef * vp) * inv_b;
+  };
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool own = gx < nx && gy < ny;
+  Dots<T> d;
+  d.zero();
+  T vdn = 0, vc = 0, vpc = 0;
+  if (own && z0 < z1) {
+    vdn = form(gx, gy, z0 - 1, nullptr);
+    vc = form(gx, gy, z0, &vpc);
+  }
+  for (int z = z0; z < z1; ++z) {
+    T vpu = 0, vup = 0;
+    if (own) vup = form(gx, gy, z + 1, &vpu);
+    // plane z with x-y halo: centre from registers, ring from global
+    if (own) ps[(ty + 1) * PW + tx + 1] = vc;
+    for (int r = tid; r < 2 * PW + 2 * TY; r += NT) {
+      int cx, cy;
+      if (r < PW) { cx = r; cy = 0; }
+      else if (r < 2 * PW) { cx = r - PW; cy = PH - 1; }
+      else if (r < 2 * PW + TY) { cx = 0; cy = r - 2 * PW + 1; }
+      else { cx = PW - 1; cy = r - 2 * PW - TY + 1; }
+      ps[cy * PW + cx] = form(x0 - 1 + cx, y0 - 1 + cy, z, nullptr);
+    }
+    // partial tiles: centre cells outside the grid still need a value for neighbours
+    if (!own) {
+      const int cgx = x0 + tx, cgy = y0 + ty;
+      ps[(ty + 1) * PW + tx + 1] = form(cgx, cgy, z, nullptr);
+    }
+    __syncthreads();
+    if (own) {
+      const size_t i = (size_t)gx + (size_t)nx * gy + plane * z;
+      const T kap = kap_at<T>(a.kappa2, a.kappa2_const, i);
+      T r = bop2<T, BC, PW>(ps, tx + 1, ty + 1, gx, gy, nx, ny, kap);
+      if (BC != GMRF_BC_NEUMANN || z > 0) r += vc - vdn;
+      if (BC != GMRF_BC_NEUMANN || z < nz - 1) r += vc - vup;
+      if (!STEP) {
+        a.Wout[(size_t)s * n + i] = r;
+      } else {
+        T q = r;
+        if (j > 0) q -= bprev * vpc;
+        a.Wout[(size_t)s * n + i] = q;
+        Vc[i] = vc;
+        d.add(vc, q);
+      }
+    }
+    __syncthreads();
+    vdn = vc;
+    vc = vup;
+    vpc = vpu;
+  }
+  if (!STEP) return;
+  d = block_reduce(d, red);
+  const int nblk = gridDim.x * gridDim.y * a.nzc;
+  if (tid == 0) a.partials[(size_t)s * nblk + blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc)] = d;
+  if (last_block(a.counters, s, nblk, &s_int[3]))
+    finish_step<T>(a.P, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
+}
+
+int nz_chunks(const Grid& g) {
+  if (g.dim != 3) return 1;
+  const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+  int c = 1;
+  while (c < g.nz && tiles * c < 4 * 152 && (g.nz + 2 * c - 1) / (2 * c) >= 8) c *= 2;
+  return c;
+}
+
+template <typename T, bool STEP>
+cudaError_t dispatch(const Grid& g, StencilArgs<T> a, int nvec, cudaStream_t s) {
+  dim3 blk(TX, TY);
+  dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, nvec);
+  if (g.dim == 3) {
+    if (g.op != GMRF_OP_SHIFTED_LAPLACIAN) return cudaErrorNotSupported;
+    a.nzc = nz_chunks(g);
+    grd.z = nvec * a.nzc;
+    switch (g.bc) {
+      case GMRF_BC_PERIODIC: k_stencil3d<T, GMRF_BC_PERIODIC, STEP><<<grd, blk, 0, s>>>(a); break;
+      case GMRF_BC_NEUMANN: k_stencil3d<T, GMRF_BC_NEUMANN, STEP><<<grd, blk, 0, s>>>(a); break;
+      default: k_stencil3d<T, GMRF_BC_DIRICHLET, STEP><<<grd, blk, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
+  a.nzc = 1;
+#define GMRF_L2(OPV, BCV) k_stencil2d<T, OPV, BCV, STEP><<<grd, blk, 0, s>>>(a)
+  if (g.op == GMRF_OP_SPDE_SQUARED) {
+    switch (g.bc) {
+      case GMRF_BC_PERIODIC: GMRF_L2(GMRF_OP_SPDE_SQUARED, GMRF_BC_PERIODIC); break;
+      case GMRF_BC_NEUMANN: GMRF_L2(GMRF_OP_SPDE_SQUARED, GMRF_BC_NEUMANN); break;
+      default: GMRF_L2(GMRF_OP_SPDE_SQUARED, GMRF_BC_DIRICHLET); break;
+    }
+  } else {
+    switch (g.bc) {
+      case GMRF_BC_PERIODIC: GMRF_L2(GMRF_OP_SHIFTED_LAPLACIAN, GMRF_BC_PERIODIC); break;
+      case GMRF_BC_NEUMANN: GMRF_L2(GMRF_OP_SHIFTED_LAPLACIAN, GMRF_BC_NEUMANN); break;
+      default: GMRF_L2(GMRF_OP_SHIFTED_LAPLACIAN, GMRF_BC_DIRICHLET); break;
+    }
+  }
+#undef GMRF_L2
+  return cudaGetLastError();
+}
+
+template <typename T>
+StencilArgs<T> make_args(const Grid& g, const void* kappa2, double kc) {
+  StencilArgs<T> a{};
+  a.kappa2 = (const float*)kappa2;
+  a.kappa2_const = (T)kc;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.dim == 3 ? g.nz : 1;
+  a.n = g.n;
+  return a;
+}
+
+}  // namespace
+
+int stencil_blocks_per_vector(const Grid& g) {
+  return ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * nz_chunks(g);
+}
+
+cudaError_t launch_stencil_step(const Grid& g, bool fp64, const void* kappa2, double kappa2_const,
+                                const LanczosBufs& b, const StepParams& P, cudaStream_t s) {
+  const int j = P.j;
+  if (fp64) {
+    auto a = make_args<double>(g, kappa2, kappa2_const);
+    a.Win = (const double*)b.W[j & 1];
+    a.Wout = (double*)b.W[(j + 1) & 1];
+    a.V = (double*)b.V;
+    a.P = P;
+    a.st = b.st; a.alpha = b.alpha; a.beta = b.beta; a.alpha_f = b.alpha_f; a.beta2_f = b.beta2_f;
+    a.partials = (Dots<double>*)b.partials;
+    a.counters = b.counters;
+    return dispatch<double, true>(g, a, b.nvec, s);
+  }
+  auto a = make_args<float>(g, kappa2, kappa2_const);
+  a.Win = (const float*)b.W[j & 1];
+  a.Wout = (float*)b.W[(j + 1) & 1];
+  a.V = (float*)b.V;
+  a.P = P;
+  a.st = b.st; a.alpha = b.alpha; a.beta = b.beta; a.alpha_f = b.alpha_f; a.beta2_f = b.beta2_f;
+  a.partials = (Dots<float>*)b.partials;
+  a.counters = b.counters;
+  return dispatch<float, true>(g, a, b.nvec, s);
+}
+
+cudaError_t launch_stencil_apply(const Grid& g, bool fp64, const void* kappa2, double kappa2_const,
+                                 const void* v, void* y, int nvec, cudaStream_t s) {
+  if (fp64) {
+    auto a = make_args<double>(g, kappa2, kappa2_const);
+    a.Win = (const double*)v;
+    a.Wout = (double*)y;
+    return dispatch<double, false>(g, a, nvec, s);
+  }
+  auto a = make_args<float>(g, kappa2, kappa2_const);
+  a.Win = (const float*)v;
+  a.Wout = (float*)y;
+  return dispatch<float, false>(g, a, nvec, s);
+}
+
+}  // namespace gmrf

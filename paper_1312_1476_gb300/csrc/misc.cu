@@ -1,0 +1,281 @@
+// misc.cu -- noise generation (Algorithm 1, first step; Section 6 probes),
+// Lanczos start-up (v_1 = z / ||z||), sample assembly x_m = ||z|| V_m y
+// (Algorithm 1, last step) and small elementwise helpers.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.h"
+
+namespace gmrf {
+namespace {
+
+// Gaussian stream: group g of vector s -> counter (g, s, 0, 0); Box-Muller on
+// (w0, w1) and (w2, w3), u = ((w >> 8) + 1/2) 2^-24.
+template <typename T>
+__global__ void k_rng_gauss(T* out, int64_t nvec, int64_t n, uint32_t k0, uint32_t k1, int64_t soff) {
+  const int64_t ng = (n + 3) / 4;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nvec * ng;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx / ng, g = idx - s * ng;
+    uint32_t c[4] = {(uint32_t)g, (uint32_t)(s + soff), 0u, 0u};
+    philox4x32_10(c, k0, k1);
+    T z[4];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      if (sizeof(T) == 4) {
+        float ua = ((float)(c[2 * p] >> 8) + 0.5f) * 5.9604644775390625e-8f;
+        float ub = ((float)(c[2 * p + 1] >> 8) + 0.5f) * 5.9604644775390625e-8f;
+        float r = sqrtf(-2.0f * logf(ua));
+        float sn, cs;
+        sincospif(2.0f * ub, &sn, &cs);
+        z[2 * p] = (T)(r * cs);
+        z[2 * p + 1] = (T)(r * sn);
+      } else {
+        double ua = ((double)(c[2 * p] >> 8) + 0.5) * 5.9604644775390625e-8;
+        double ub = ((double)(c[2 * p + 1] >> 8) + 0.5) * 5.9604644775390625e-8;
+        double r = sqrt(-2.0 * log(ua));
+        double sn, cs;
+        sincospi(2.0 * ub, &sn, &cs);
+        z[2 * p] = (T)(r * cs);
+        z[2 * p + 1] = (T)(r * sn);
+      }
+    }
+    T* o = out + s * n + 4 * g;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * g + e < n) o[e] = z[e];
+  }
+}
+
+__global__ void k_rng_words(uint32_t* out, int64_t nvec, int64_t n, uint32_t k0, uint32_t k1, int64_t soff) {
+  const int64_t ng = (n + 3) / 4;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nvec * ng;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx / ng, g = idx - s * ng;
+    uint32_t c[4] = {(uint32_t)g, (uint32_t)(s + soff), 0u, 0u};
+    philox4x32_10(c, k0, k1);
+    uint32_t* o = out + s * (4 * ng) + 4 * g;
+    o[0] = c[0];
+    o[1] = c[1];
+    o[2] = c[2];
+    o[3] = c[3];
+  }
+}
+
+// Rademacher stream: element e of probe s is bit e%32 of word (e/32)%4 of
+// Philox counter (e/128, s, 1, 0).  One thread per 32 elements.
+template <typename T>
+__global__ void k_rng_rademacher(T* out, int64_t nvec, int64_t n, uint32_t k0, uint32_t k1, int64_t soff) {
+  const int64_t nw = (n + 31) / 32;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nvec * nw;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx / nw, w = idx - s * nw;
+    uint32_t c[4] = {(uint32_t)(w / 4), (uint32_t)(s + soff), 1u, 0u};
+    philox4x32_10(c, k0, k1);
+    const uint32_t word = c[w & 3];
+    T* o = out + s * n + 32 * w;
+    for (int b = 0; b < 32 && 32 * w + b < n; ++b) o[b] = ((word >> b) & 1u) ? (T)1 : (T)-1;
+  }
+}
+
+// ||z|| per vector and state reset.  grid (nblk, nvec).
+template <typename T>
+__global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>* partials, unsigned* counters) {
+  __shared__ Dots<T> red[8];
+  __shared__ int s_flag;
+  const int s = blockIdx.y;
+  const T* z = W + (size_t)s * n;
+  Dots<T> d;
+  d.zero();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    d.add(z[i], (T)0);
+  d = block_reduce(d, red);
+  const int nblk = gridDim.x;
+  if (threadIdx.x == 0) partials[(size_t)s * nblk + blockIdx.x] = d;
+  if (!last_block(counters, s, nblk, &s_flag)) return;
+  Dots<T> acc;
+  acc.zero();
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc.merge(partials[(size_t)s * nblk + b]);
+  acc = block_reduce(acc, red);
+  if (threadIdx.x == 0) {
+    double s1, s2, s3;
+    acc.get(s1, s2, s3);
+    VecState v = {};
+    v.znorm = sqrt(s3);
+    v.m = 0;
+    if (!isfinite(v.znorm)) v.status = GMRF_ERR_NUMERIC;
+    else if (v.znorm == 0.0) v.status = VS_DONE;
+    else v.status = VS_RUNNING;
+    st[s] = v;
+  }
+}
+
+// x[s][i] = scale_s * sum_j V[s][j][i] y[s][j], scale_s = ||z_s|| * extra.
+// FP32: y split into float hi + lo, compensated (Neumaier) accumulation.
+template <typename T>
+__global__ void k_assemble(const T* __restrict__ V, int nslots, size_t n, const VecState* st, const double* y,
+                           int y_stride, double extra, T* x) {
+  extern __shared__ unsigned char smem_raw[];
+  const int s = blockIdx.y;
+  const VecState v = st[s];
+  const int m = v.m;
+  T* xo = x + (size_t)s * n;
+  const bool bad = !(v.status == VS_DONE || v.status == GMRF_ERR_NOT_CONVERGED);
+  if (bad || m == 0) {
+    const T fill = (bad && v.status != VS_DONE) ? (T)NAN : (T)0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+      xo[i] = fill;
+    return;
+  }
+  const double scale = v.znorm * extra;
+  const double* ys = y + (size_t)s * y_stride;
+  const T* Vs = V + (size_t)s * nslots * n;
+  if (sizeof(T) == 4) {
+    float* yh = (float*)smem_raw;
+    float* yl = yh + m;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const double yy = ys[j] * scale;
+      const float h = (float)yy;
+      yh[j] = h;
+      yl[j] = (float)(yy - (double)h);
+    }
+    __syncthreads();
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      float sum = 0.f, comp = 0.f;
+      for (int j = 0; j < m; ++j) {
+        const float vv = (float)Vs[(size_t)j * n + i];
+        const float t = __fmaf_rn(vv, yh[j], __fmul_rn(vv, yl[j]));
+        const float s2 = __fadd_rn(sum, t);
+        comp = __fadd_rn(comp, fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t)
+                                                       : __fadd_rn(__fsub_rn(t, s2), sum));
+        sum = s2;
+      }
+      xo[i] = (T)__fadd_rn(sum, comp);
+    }
+  } else {
+    double* yd = (double*)smem_raw;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) yd[j] = ys[j] * scale;
+    __syncthreads();
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      double sum = 0.0;
+      for (int j = 0; j < m; ++j) sum = fma((double)Vs[(size_t)j * n + i], yd[j], sum);
+      xo[i] = (T)sum;
+    }
+  }
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A* in, B* out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+
+template <typename T>
+__global__ void k_scale(T* x, size_t count, T a) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
+// Coefficient-field checks and mean log: counts of negative / non-finite
+// entries and of zeros, and sum of log kappa^2 over the positive entries
+// (compensated FP32).  One block, fixed summation order.
+__global__ void k_field_stats(const float* k, size_t n, double* out4) {
+  __shared__ Dots<float> red[8];
+  Dots<float> d;  // s1 = sum log, s2 = #bad, s3 = #zero (as compensated sums)
+  d.zero();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = k[i];
+    if (!(v >= 0.f) || !isfinite(v)) d.s2 = df_add(d.s2, df{1.f, 0.f});
+    else if (v == 0.f) d.s3 = df_add(d.s3, df{1.f, 0.f});
+    else d.s1 = df_add(d.s1, df{logf(v), 0.f});
+  }
+  d = block_reduce(d, red);
+  if (threadIdx.x == 0) {
+    double a, b, c;
+    d.get(a, b, c);
+    out4[0] = b;
+    out4[1] = c;
+    out4[2] = a;
+  }
+}
+
+int grid_for(size_t work, int threads) {
+  size_t b = (work + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_rng(int kind, bool fp64, int64_t nvec, int64_t n, uint64_t seed, int64_t soff, void* out,
+                       cudaStream_t s) {
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  if (kind == 0) {
+    const int grid = grid_for((size_t)nvec * ((n + 3) / 4), 256);
+    if (fp64) k_rng_gauss<double><<<grid, 256, 0, s>>>((double*)out, nvec, n, k0, k1, soff);
+    else k_rng_gauss<float><<<grid, 256, 0, s>>>((float*)out, nvec, n, k0, k1, soff);
+  } else if (kind == 1) {
+    const int grid = grid_for((size_t)nvec * ((n + 31) / 32), 256);
+    if (fp64) k_rng_rademacher<double><<<grid, 256, 0, s>>>((double*)out, nvec, n, k0, k1, soff);
+    else k_rng_rademacher<float><<<grid, 256, 0, s>>>((float*)out, nvec, n, k0, k1, soff);
+  } else {
+    const int grid = grid_for((size_t)nvec * ((n + 3) / 4), 256);
+    k_rng_words<<<grid, 256, 0, s>>>((uint32_t*)out, nvec, n, k0, k1, soff);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_stats(const float* k, size_t n, double* out4, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out4, 0, 4 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_field_stats<<<1, 256, 0, s>>>(k, n, out4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_init(bool fp64, size_t n, const LanczosBufs& b, cudaStream_t s) {
+  int nblk = (int)((n + 255) / 256);
+  if (nblk > 256) nblk = 256;
+  dim3 grd(nblk, b.nvec);
+  if (fp64)
+    k_init<double><<<grd, 256, 0, s>>>((const double*)b.W[0], n, b.st, (Dots<double>*)b.partials, b.counters);
+  else
+    k_init<float><<<grd, 256, 0, s>>>((const float*)b.W[0], n, b.st, (Dots<float>*)b.partials, b.counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(bool fp64, size_t n, const LanczosBufs& b, const double* y, int y_stride,
+                            double extra_scale, void* x, cudaStream_t s) {
+  int nblk = (int)((n + 255) / 256);
+  if (nblk > 2048) nblk = 2048;
+  dim3 grd(nblk, b.nvec);
+  const size_t sm = (size_t)b.m_max * 8;
+  if (fp64) {
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_assemble<double><<<grd, 256, sm, s>>>((const double*)b.V, b.nslots, n, b.st, y, y_stride, extra_scale,
+                                            (double*)x);
+  } else {
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_assemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_assemble<float><<<grd, 256, sm, s>>>((const float*)b.V, b.nslots, n, b.st, y, y_stride, extra_scale,
+                                           (float*)x);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(bool to_fp64, const void* in, void* out, size_t count, cudaStream_t s) {
+  const int grid = grid_for(count, 256);
+  if (to_fp64) k_convert<float, double><<<grid, 256, 0, s>>>((const float*)in, (double*)out, count);
+  else k_convert<double, float><<<grid, 256, 0, s>>>((const double*)in, (float*)out, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(bool fp64, void* x, size_t count, double a, cudaStream_t s) {
+  const int grid = grid_for(count, 256);
+  if (fp64) k_scale<double><<<grid, 256, 0, s>>>((double*)x, count, a);
+  else k_scale<float><<<grid, 256, 0, s>>>((float*)x, count, (float)a);
+  return cudaGetLastError();
+}
+
+}  // namespace gmrf

@@ -1,0 +1,57 @@
+// precond.h -- the constant-coefficient preconditioner of Section 5.1 and the
+// preconditioned Lanczos step (Proposition 1).  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "internal.h"
+
+namespace gmrf {
+
+enum { PRE_INV_SQRT = 0 };
+
+// Tables and workspace of the preconditioner M = tau * B_bar^p with
+// B_bar = kappa_bar^2 I + L_prec (L_prec the torus Laplacian for CIRCULANT,
+// the cell-centred Neumann Laplacian for MIRROR), p = 1 (shifted Laplacian)
+// or 2 (SPDE squared).  Its inverse square root (without tau) is
+// P = B_bar^{-p/2}, diagonal in the transform basis with symbol
+// (kappa_bar^2 + lambda_x + lambda_y)^{-p/2}.
+struct PrecondTables {
+  int kind = 0;   // GMRF_PREC_CIRCULANT or GMRF_PREC_MIRROR
+  int power = 1;  // p
+  int nx = 0, ny = 0, lognx = 0, logny = 0;
+  bool fp64 = false;
+  double kbar2 = 0.0;
+  void* lamx = nullptr;  // R[nx]: 1-D Laplacian eigenvalues in transform order
+  void* lamy = nullptr;  // R[ny]
+  void* twx = nullptr;   // C[nx]: exp(-2 pi i t / nx)
+  void* twy = nullptr;   // C[ny]
+  void* dctx = nullptr;  // C[nx+1]: exp(-i pi t / (2 nx))
+  void* dcty = nullptr;  // C[ny+1]
+  void* S = nullptr;     // spectral workspace, per vector spec_elems() complex/real pairs
+  size_t S_bytes = 0;
+  void* G = nullptr;     // g = C v workspace (SPDE squared), per vector n reals
+  size_t G_bytes = 0;
+  int rb = 4;            // rows per row-kernel block
+};
+
+bool precond_size_ok(int64_t n);
+int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar2, bool fp64, cudaStream_t s,
+                  double* logdet_M);
+void precond_free(PrecondTables& t);
+int precond_blocks_per_vector(const PrecondTables& t);
+size_t precond_extra_bytes(const PrecondTables& t, size_t es);
+// Fused preconditioned Lanczos step j (A = M^{-1/2} Q M^{-1/2}, applied as
+// C^T C with C = I + R B_bar^{-1} for the squared operator and as
+// I + P R P for the shifted one, R = B - B_bar).
+cudaError_t launch_precond_step(PrecondTables& t, const Grid& g, bool fp64, const void* kappa2, double kappa2_const,
+                                const LanczosBufs& b, const StepParams& P, cudaStream_t s);
+// out = B_bar^{-p/2} in for nvec vectors (tau not applied).
+cudaError_t launch_precond_apply(PrecondTables& t, const Grid& g, bool fp64, int which, const void* in, void* out,
+                                 int nvec, cudaStream_t s);
+// y = A v for nvec vectors.
+cudaError_t launch_precond_operator(PrecondTables& t, const Grid& g, bool fp64, const void* kappa2,
+                                    double kappa2_const, const void* v, void* y, int nvec, cudaStream_t s);
+
+}  // namespace gmrf

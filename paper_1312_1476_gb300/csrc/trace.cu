@@ -1,0 +1,128 @@
+// trace.cu -- see trace.h.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/gmrf.h"
+#include "trace.h"
+
+namespace gmrf {
+namespace {
+
+struct Pending {
+  int kc;
+  cudaEvent_t a, b;
+};
+
+struct Registry {
+  bool timing = false;
+  int64_t launches[KC_COUNT] = {};
+  int64_t timed[KC_COUNT] = {};
+  double ms[KC_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  Pending open = {-1, nullptr, nullptr};
+};
+
+Registry& reg() {
+  static Registry r;
+  return r;
+}
+
+cudaEvent_t take() {
+  Registry& r = reg();
+  if (!r.pool.empty()) {
+    cudaEvent_t e = r.pool.back();
+    r.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+}  // namespace
+
+void trace_begin(int kc, cudaStream_t s, int nkernels) {
+  Registry& r = reg();
+  r.launches[kc] += nkernels;
+  if (!r.timing) return;
+  r.open.kc = kc;
+  r.open.a = take();
+  r.open.b = take();
+  if (r.open.a) cudaEventRecord(r.open.a, s);
+}
+
+void trace_end(int kc, cudaStream_t s) {
+  Registry& r = reg();
+  if (!r.timing || r.open.kc != kc) return;
+  if (r.open.a && r.open.b) {
+    cudaEventRecord(r.open.b, s);
+    r.pending.push_back(r.open);
+  }
+  r.open.kc = -1;
+  // keep the number of outstanding pairs bounded
+  if (r.pending.size() > 8192) trace_collect();
+}
+
+void trace_collect() {
+  Registry& r = reg();
+  for (Pending& p : r.pending) {
+    if (cudaEventSynchronize(p.b) == cudaSuccess) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+        r.ms[p.kc] += t;
+        r.timed[p.kc] += 1;
+      }
+    }
+    cudaGetLastError();
+    r.pool.push_back(p.a);
+    r.pool.push_back(p.b);
+  }
+  r.pending.clear();
+}
+
+}  // namespace gmrf
+
+extern "C" int gmrf_trace(int32_t op, int32_t kclass, double* total_ms, int64_t* launches, int64_t* timed) {
+  using namespace gmrf;
+  Registry& r = reg();
+  switch (op) {
+    case 0:
+      trace_collect();
+      for (int k = 0; k < KC_COUNT; ++k) {
+        r.launches[k] = 0;
+        r.timed[k] = 0;
+        r.ms[k] = 0.0;
+      }
+      return GMRF_OK;
+    case 1:
+      r.timing = true;
+      return GMRF_OK;
+    case 2:
+      trace_collect();
+      r.timing = false;
+      return GMRF_OK;
+    case 3: {
+      if (kclass < -1 || kclass >= KC_COUNT) return GMRF_ERR_INVALID;
+      trace_collect();
+      double ms = 0.0;
+      int64_t l = 0, t = 0;
+      for (int k = 0; k < KC_COUNT; ++k) {
+        if (kclass != -1 && k != kclass) continue;
+        ms += r.ms[k];
+        l += r.launches[k];
+        t += r.timed[k];
+      }
+      if (total_ms) *total_ms = ms;
+      if (launches) *launches = l;
+      if (timed) *timed = t;
+      return GMRF_OK;
+    }
+    default:
+      return GMRF_ERR_INVALID;
+  }
+}

@@ -1,0 +1,42 @@
+// trace.h -- kernel launch counting and per-kernel-class CUDA-event timing.
+//
+// Every kernel launch of the library goes through trace_begin / trace_end.
+// Launch counts are always kept.  When event timing is enabled
+// (gmrf_trace(1, ...)), a pair of events is recorded around the launch on
+// its own stream and the elapsed times are accumulated at the next host
+// synchronisation point (trace_collect).  Host-side, single-threaded use.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gmrf {
+
+enum KernelClass {
+  KC_STENCIL_STEP = 0,  // fused stencil + Lanczos step
+  KC_PRE_ROW_FWD = 1,   // preconditioned step: form v_j + row forward transform
+  KC_PRE_COL = 2,       // column transform * symbol * inverse
+  KC_PRE_ROW_MID = 3,   // inverse rows, R, forward rows
+  KC_PRE_ROW_LAST = 4,  // inverse rows, A v, recurrence, reductions
+  KC_INIT = 5,          // ||z||
+  KC_RNG = 6,           // Philox streams
+  KC_TM = 7,            // T_m functions (nodes, poles, sums, log)
+  KC_ASSEMBLE = 8,      // x = ||z|| V_m y
+  KC_PRE_APPLY = 9,     // plain M^{-1/2} / A applies, final M^{-1/2} u
+  KC_OTHER = 10,        // scale, convert, field statistics, log det M
+  KC_COUNT = 11
+};
+
+void trace_begin(int kc, cudaStream_t s, int nkernels = 1);
+void trace_end(int kc, cudaStream_t s);
+void trace_collect();
+
+template <typename F>
+inline cudaError_t traced(int kc, cudaStream_t s, int nkernels, F f) {
+  trace_begin(kc, s, nkernels);
+  cudaError_t e = f();
+  trace_end(kc, s);
+  return e;
+}
+
+}  // namespace gmrf

@@ -1,0 +1,265 @@
+"""Python binding of the C ABI in include/gmrf.h (argument marshalling only).
+
+Every computation runs in ``libgmrf.so``'s CUDA kernels.  Arrays may be
+``torch`` tensors (CUDA or CPU) or ``numpy`` arrays; they are passed to the
+library as raw pointers, which accepts host or device memory.  There is no
+fallback: if the library is missing or fails to load, importing the module
+raises.
+
+Names follow the paper's notation: Q (precision), z (noise), x = Q^{-1/2} z
+(Section 4, Algorithm 1), M (preconditioner, Proposition 1), log det Q
+(Section 6).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgmrf.so")
+
+OK = 0
+ERR_INVALID = -1
+ERR_OOM = -2
+ERR_NOT_CONVERGED = -3
+ERR_NOT_SPD = -4
+ERR_NUMERIC = -5
+ERR_CUDA = -6
+ERR_TIMEOUT = -7
+ERR_UNSUPPORTED = -8
+
+BC = {"periodic": 0, "neumann": 1, "dirichlet": 2}
+OP = {"shifted_laplacian": 0, "spde_squared": 1}
+PREC = {"none": 0, "circulant": 1, "mirror": 2}
+PRECISION = {"fp32": 0, "fp64": 1}
+
+
+class GmrfDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("bc", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("nz", ctypes.c_int64), ("kappa2", ctypes.c_void_p), ("kappa2_const", ctypes.c_double),
+                ("tau", ctypes.c_double), ("kappa2_precond", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class GmrfSampleOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("m_max", ctypes.c_int32), ("nsamples", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("z_in", ctypes.c_void_p), ("check_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class GmrfResultInfo(ctypes.Structure):
+    _fields_ = [("m_used", ctypes.c_int32), ("status", ctypes.c_int32), ("err_est", ctypes.c_double)]
+
+
+class GmrfLogdetOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("m_max", ctypes.c_int32), ("nprobes", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("probes_in", ctypes.c_void_p), ("check_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libgmrf.so is not built; run paper_1312_1476_gb300._build.build() "
+                          "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    sig = {
+        "gmrf_create": (ctypes.c_int, [ctypes.POINTER(GmrfDesc), P, ctypes.POINTER(P)]),
+        "gmrf_size": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "gmrf_sample": (ctypes.c_int, [P, ctypes.POINTER(GmrfSampleOpts), P, ctypes.POINTER(GmrfResultInfo)]),
+        "gmrf_logdet": (ctypes.c_int, [P, ctypes.POINTER(GmrfLogdetOpts), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(GmrfResultInfo)]),
+        "gmrf_apply": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int64, P, P]),
+        "gmrf_rng": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_uint64, P, P]),
+        "gmrf_trace": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "gmrf_destroy": (None, [P]),
+        "gmrf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+class GmrfError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, _lib.gmrf_strerror(code).decode(), code))
+
+
+def strerror(code: int) -> str:
+    return _lib.gmrf_strerror(code).decode()
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(a))
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+@dataclass
+class SampleInfo:
+    m_used: int
+    status: int
+    err_est: float
+
+
+class Problem:
+    """A lattice GMRF precision Q (gmrf_create) with its sampler and log det."""
+
+    def __init__(self, shape, bc="periodic", op="shifted_laplacian", kappa2=None, kappa2_const=0.0, tau=1.0,
+                 precond="none", kappa2_precond=0.0, precision="fp32", stream=None):
+        shape = tuple(int(s) for s in shape)
+        if len(shape) not in (2, 3):
+            raise ValueError("shape must be (ny, nx) or (nz, ny, nx)")
+        d = GmrfDesc()
+        d.dim = len(shape)
+        d.bc = BC[bc]
+        d.op = OP[op]
+        d.precond = PREC[precond]
+        d.nx = shape[-1]
+        d.ny = shape[-2]
+        d.nz = shape[0] if len(shape) == 3 else 1
+        self._kappa2 = None
+        if kappa2 is not None:
+            if hasattr(kappa2, "dtype") and str(kappa2.dtype) not in ("float32", "torch.float32"):
+                raise TypeError("kappa2 must be float32")
+            self._kappa2 = kappa2
+            d.kappa2 = _ptr(kappa2)
+        else:
+            d.kappa2 = None
+        d.kappa2_const = float(kappa2_const)
+        d.tau = float(tau)
+        d.kappa2_precond = float(kappa2_precond)
+        d.precision = PRECISION[precision]
+        d.reserved = 0
+        self.shape = shape
+        self.precision = precision
+        self.n = int(np.prod(shape))
+        self._h = ctypes.c_void_p()
+        rc = _lib.gmrf_create(ctypes.byref(d), _stream(stream), ctypes.byref(self._h))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_create")
+        self._stream = stream
+
+    @property
+    def dtype(self):
+        return np.float64 if self.precision == "fp64" else np.float32
+
+    def close(self):
+        if self._h:
+            _lib.gmrf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sample(self, out, nsamples=1, tol=1e-6, m_max=300, seed=2, z=None, check_every=16, raise_on_error=True):
+        """x ~= Q^{-1/2} z into ``out`` ([nsamples][n], host or device); returns
+        (return code, list of SampleInfo)."""
+        o = GmrfSampleOpts(float(tol), int(m_max), int(nsamples), int(seed) & (2 ** 64 - 1),
+                           _ptr(z) if z is not None else None, int(check_every), 0)
+        info = (GmrfResultInfo * int(nsamples))()
+        rc = _lib.gmrf_sample(self._h, ctypes.byref(o), _ptr(out), info)
+        infos = [SampleInfo(i.m_used, i.status, i.err_est) for i in info]
+        if raise_on_error and rc not in (OK, ERR_NOT_CONVERGED):
+            raise GmrfError(rc, "gmrf_sample")
+        return rc, infos
+
+    def logdet(self, nprobes=16, tol=1e-6, m_max=300, seed=3, probes=None, check_every=16, raise_on_error=True):
+        """Hutchinson / Lanczos-quadrature log det Q; returns
+        (logdet, std_err, q_i array, list of SampleInfo, return code)."""
+        o = GmrfLogdetOpts(float(tol), int(m_max), int(nprobes), int(seed) & (2 ** 64 - 1),
+                           _ptr(probes) if probes is not None else None, int(check_every), 0)
+        ld = ctypes.c_double()
+        se = ctypes.c_double()
+        q = np.zeros(int(nprobes), dtype=np.float64)
+        info = (GmrfResultInfo * int(nprobes))()
+        rc = _lib.gmrf_logdet(self._h, ctypes.byref(o), ctypes.byref(ld), ctypes.byref(se),
+                              ctypes.c_void_p(q.ctypes.data), info)
+        infos = [SampleInfo(i.m_used, i.status, i.err_est) for i in info]
+        if raise_on_error and rc not in (OK, ERR_NOT_CONVERGED):
+            raise GmrfError(rc, "gmrf_logdet")
+        return ld.value, se.value, q, infos, rc
+
+    def apply(self, which, v, y, nvec=1):
+        """which 0: y = Q v; 1: y = A v (preconditioned operator); 2: y = M^{-1/2} v."""
+        rc = _lib.gmrf_apply(self._h, int(which), int(nvec), _ptr(v), _ptr(y))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_apply")
+
+
+def rng(kind, nvec, n, seed, out, precision="fp32", stream=None):
+    """Device Philox streams: kind 0 Gaussian, 1 Rademacher, 2 raw words."""
+    rc = _lib.gmrf_rng(int(kind), PRECISION[precision], int(nvec), int(n), int(seed) & (2 ** 64 - 1),
+                       _ptr(out), _stream(stream))
+    if rc != OK:
+        raise GmrfError(rc, "gmrf_rng")
+
+
+KERNEL_CLASSES = {"stencil_step": 0, "pre_row_fwd": 1, "pre_col": 2, "pre_row_mid": 3, "pre_row_last": 4,
+                  "init": 5, "rng": 6, "tm": 7, "assemble": 8, "pre_apply": 9, "other": 10}
+
+
+def trace_reset():
+    _lib.gmrf_trace(0, -1, None, None, None)
+
+
+def trace_timing(enable: bool):
+    _lib.gmrf_trace(1 if enable else 2, -1, None, None, None)
+
+
+def trace_query(kclass="all"):
+    """(total kernel ms, launches, timed launches) of a kernel class or all."""
+    k = -1 if kclass == "all" else KERNEL_CLASSES[kclass]
+    ms = ctypes.c_double()
+    la = ctypes.c_int64()
+    ti = ctypes.c_int64()
+    rc = _lib.gmrf_trace(3, k, ctypes.byref(ms), ctypes.byref(la), ctypes.byref(ti))
+    if rc != OK:
+        raise GmrfError(rc, "gmrf_trace")
+    return ms.value, la.value, ti.value

@@ -1,0 +1,79 @@
+"""GPU parity of gmrf_logdet (Section 6 Hutchinson estimator with Lanczos /
+Gauss quadrature; Section 6.2 preconditioned split) against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import exact, lanczos as olz, precond, stencil
+from paper_1312_1476_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_1312_1476_gb300 import gmrf
+    assert torch.cuda.is_available()
+    return gmrf
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,bc,op", [((12, 10), "neumann", "spde_squared"),
+                                         ((14, 14), "periodic", "shifted_laplacian"),
+                                         ((5, 6, 7), "dirichlet", "shifted_laplacian")])
+def test_fixed_probes_match_exact_quadforms(g, precision, shape, bc, op):
+    n = int(np.prod(shape))
+    k2 = inputs.kappa2_uniform_field(shape, seed=2, lo=0.1, hi=1.0)
+    tau = 1.7
+    Q = stencil.precision_matrix(shape, bc, op, k2.astype(np.float64), tau=tau)
+    dt = np.float64 if precision == "fp64" else np.float32
+    V = inputs.rademacher_vectors(6, n, seed=3, dtype=dt)
+    with g.Problem(shape, bc, op, kappa2=_dev(k2), tau=tau, precision=precision) as p:
+        ld, se, q, info, rc = p.logdet(nprobes=6, tol=1e-10 if precision == "fp64" else 1e-6, m_max=n,
+                                       probes=_dev(V))
+    # the library's q_i are for Q / tau (tau enters as n log tau)
+    qe = exact.quadform_log_dense(Q / tau, V.astype(np.float64))
+    rtol = 1e-8 if precision == "fp64" else 1e-6
+    np.testing.assert_allclose(q, qe, rtol=rtol, atol=rtol * np.abs(qe).max())
+    est = qe.mean() + n * np.log(tau)
+    assert abs(ld - est) <= rtol * abs(est) + rtol
+    assert abs(se - qe.std(ddof=1) / np.sqrt(6)) <= 1e-6 * abs(se) + 1e-6
+
+
+@pytest.mark.parametrize("kind", ["circulant", "mirror"])
+def test_preconditioned_logdet_split(g, kind):
+    shape = (16, 16)
+    n = 256
+    k2 = inputs.kappa2_gp_field(shape, seed=1, ell=4.0)
+    kb = precond.kappa2_bar(k2)
+    tau = 2.0
+    okind = "periodic" if kind == "circulant" else "neumann"
+    Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2.astype(np.float64), tau=tau)
+    A, P = precond.preconditioned_operator_dense(Q, shape, okind, "spde_squared", kb, tau)
+    V = inputs.rademacher_vectors(8, n, seed=5, dtype=np.float64)
+    with g.Problem(shape, "neumann", "spde_squared", kappa2=_dev(k2), tau=tau, precond=kind, kappa2_precond=kb,
+                   precision="fp64") as p:
+        ld, se, q, info, rc = p.logdet(nprobes=8, tol=1e-11, m_max=256, probes=_dev(V))
+    qe = exact.quadform_log_dense(A, V)
+    np.testing.assert_allclose(q, qe, rtol=1e-8, atol=1e-8 * np.abs(qe).max())
+    ldm = precond.logdet(shape, okind, "spde_squared", kb, tau)
+    assert abs(ld - (qe.mean() + ldm)) <= 1e-8 * abs(ld)
+    # and the split estimates the true log det within its standard error
+    assert abs(ld - exact.logdet_cholesky(Q)) <= 5 * se + 1e-6
+
+
+def test_device_probes_unbiased(g):
+    shape = (8, 8)
+    k2 = inputs.kappa2_uniform_field(shape, seed=3, lo=0.2, hi=1.0)
+    Q = stencil.precision_matrix(shape, "periodic", "spde_squared", k2.astype(np.float64))
+    with g.Problem(shape, "periodic", "spde_squared", kappa2=_dev(k2), precision="fp64") as p:
+        ld, se, q, info, rc = p.logdet(nprobes=2000, tol=1e-9, m_max=64, seed=11)
+    from oracle import philox
+    V = philox.rademacher(2000, 64, 11)
+    np.testing.assert_allclose(q, exact.quadform_log_dense(Q, V), rtol=1e-7, atol=1e-7)
+    assert abs(ld - exact.logdet_cholesky(Q)) <= 4 * se
