@@ -155,11 +155,14 @@ struct VecState {
   double pad;
 };
 
+// Loop-invariant parameters of the Lanczos steps.  The step index j (the
+// basis vector v_j formed in the step, 0-based) is not a parameter: every
+// step kernel reads it from its vector's state (VecState.m = completed
+// steps), so one captured CUDA graph of c steps can be replayed.
 struct StepParams {
-  int j;          // index of the basis vector formed in this step (0-based)
   int m_max;      // largest subspace size
   int nslots;     // ring size of the stored basis (m_max + 1, or 2 when V_m is not kept)
-  int n_sturm;    // unused padding
+  int pad0;
   double tol;     // stopping tolerance on the relative estimate
   double bd_tol;  // breakdown threshold relative to ||T_m||
 };
@@ -239,7 +242,7 @@ __device__ __noinline__ static double smallest_ritz(const float* af, const float
 //   est = theta_min^{-1/2} ||r_m|| / ||x_m||,
 //   ||r_m|| / ||z|| = beta_{m-1} |u_{m-1} / d_{m-1}|,  ||x_m|| / ||z|| = sqrt(e_1^T T_m^{-1} e_1).
 template <typename T>
-__device__ static void finish_step(const StepParams& P, int s, const Dots<T>* __restrict__ partials, int nblk,
+__device__ static void finish_step(const StepParams& P, int j, int s, const Dots<T>* __restrict__ partials, int nblk,
                             VecState* __restrict__ st, double* __restrict__ alpha, double* __restrict__ beta,
                             float* __restrict__ alpha_f, float* __restrict__ beta2_f, Dots<T>* red_scratch,
                             int* s_int, float* s_flt) {
@@ -251,7 +254,6 @@ __device__ static void finish_step(const StepParams& P, int s, const Dots<T>* __
   acc = block_reduce(acc, red_scratch);
   __shared__ int s_need_theta;
   __shared__ double s_theta_hi, s_pfac;
-  const int j = P.j;
   const size_t mo = (size_t)s * P.m_max;
   if (tid == 0) {
     double s1, s2, s3;

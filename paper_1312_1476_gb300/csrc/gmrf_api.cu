@@ -77,6 +77,24 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+// The Lanczos loop's CUDA graph: `c` steps captured once and replayed until
+// every vector has converged (the kernels read the step index from device
+// state).  Keyed by everything the captured launches depend on.
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  GraphTrace tr;
+  int nvec = -1, nslots = 0, m_max = 0, c = 0, kernels_per_step = 1;
+  double tol = 0.0;
+  const void *W0 = nullptr, *V = nullptr, *st = nullptr, *S = nullptr, *partials = nullptr;
+  bool timed = false;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    tr.release();
+    nvec = -1;
+  }
+};
+
 struct gmrf_problem {
   Grid g;
   int precond = GMRF_PREC_NONE;
@@ -85,7 +103,10 @@ struct gmrf_problem {
   double kappa2_const = 0.0;
   double kbar2 = 0.0;
   double logdet_M = 0.0;  // log det of the tau-free preconditioner (B_bar^p)
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;   // the caller's stream
+  cudaStream_t ws = nullptr;       // the library's work stream (graphs are captured on it)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  StepGraph graph;
   DevBuf kappa2;  // float [n] or empty (constant)
   PrecondTables pre;
   // Lanczos workspace (grow-only)
@@ -98,6 +119,19 @@ struct gmrf_problem {
 namespace {
 
 size_t esize(const gmrf_problem* p) { return p->fp64 ? 8 : 4; }
+
+// Order the work stream after the caller's stream (entry) and the caller's
+// stream after the work stream (exit).
+int enter(gmrf_problem* p) {
+  CK(cudaEventRecord(p->ev_in, p->stream));
+  CK(cudaStreamWaitEvent(p->ws, p->ev_in, 0));
+  return GMRF_OK;
+}
+int leave(gmrf_problem* p) {
+  CK(cudaEventRecord(p->ev_out, p->ws));
+  CK(cudaStreamWaitEvent(p->stream, p->ev_out, 0));
+  return GMRF_OK;
+}
 
 int ensure_host_states(gmrf_problem* p, int nvec) {
   if (p->st_host_cap >= nvec) return GMRF_OK;
@@ -128,7 +162,7 @@ int ensure_lanczos(gmrf_problem* p, int nvec, int nslots, int m_max, bool need_t
   CKR(ensure(p->partials, (size_t)nvec * nblk * sizeof(Dots<double>)));
   const bool fresh_counters = p->counters.bytes < sizeof(unsigned) * nvec;
   CKR(ensure(p->counters, sizeof(unsigned) * nvec));
-  if (fresh_counters) CK(cudaMemsetAsync(p->counters.p, 0, sizeof(unsigned) * nvec, p->stream));
+  if (fresh_counters) CK(cudaMemsetAsync(p->counters.p, 0, sizeof(unsigned) * nvec, p->ws));
   CKR(ensure(p->nodes, sizeof(TmNodes) * nvec));
   CKR(ensure(p->y, sizeof(double) * nvec * m_max));
   CKR(ensure(p->q, sizeof(double) * nvec));
@@ -183,31 +217,88 @@ int worst_status(const VecState* st, int nvec) {
 
 // Runs the Lanczos iteration on the vectors already in W[0].  Returns a
 // gmrf code for launch failures only; per-vector outcomes are in st_host.
+int launch_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, int c, cudaStream_t s) {
+  for (int k = 0; k < c; ++k) {
+    if (p->precond == GMRF_PREC_NONE)
+      CK(traced(KC_STENCIL_STEP, s, 1,
+                [&] { return launch_stencil_step(p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s); }));
+    else
+      CK(launch_precond_step(p->pre, p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s));
+  }
+  return GMRF_OK;
+}
+
+int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, int c) {
+  StepGraph& G = p->graph;
+  const bool timed = trace_timing_enabled();
+  const void* S = p->precond ? p->pre.S : nullptr;
+  if (G.exec && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c && G.tol == P.tol &&
+      G.W0 == b.W[0] && G.V == b.V && G.st == b.st && G.S == S && G.partials == b.partials && G.timed == timed)
+    return GMRF_OK;
+  G.reset();
+  cudaStream_t s = p->ws;
+  cudaGraph_t graph = nullptr;
+  trace_capture_begin(&G.tr);
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const int r = launch_steps(p, b, P, c, s);
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  trace_capture_end();
+  if (r != GMRF_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    G.reset();
+    return r != GMRF_OK ? r : GMRF_ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    G.exec = nullptr;
+    G.reset();
+    return GMRF_ERR_CUDA;
+  }
+  G.nvec = b.nvec;
+  G.nslots = b.nslots;
+  G.m_max = P.m_max;
+  G.c = c;
+  G.tol = P.tol;
+  G.W0 = b.W[0];
+  G.V = b.V;
+  G.st = b.st;
+  G.S = S;
+  G.partials = b.partials;
+  G.timed = timed;
+  G.kernels_per_step = p->precond ? 5 : 1;
+  return GMRF_OK;
+}
+
 int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, int check_every) {
-  cudaStream_t s = p->stream;
+  cudaStream_t s = p->ws;
   CK(traced(KC_INIT, s, 1, [&] { return launch_lanczos_init(p->fp64, p->g.n, b, s); }));
   StepParams P{};
   P.m_max = m_max;
   P.nslots = b.nslots;
   P.tol = tol;
   P.bd_tol = p->fp64 ? 1e-13 : 1e-6;
-  const int c = check_every > 0 ? check_every : 16;
+  const int c = std::min(check_every > 0 ? check_every : 16, m_max);
+  if (p->precond != GMRF_PREC_NONE) CKR(precond_prepare(p->pre, b.nvec));
+  CKR(capture_steps(p, b, P, c));
+  StepGraph& G = p->graph;
   int j = 0;
   while (j < m_max) {
-    const int jend = std::min(m_max, j + c);
-    for (; j < jend; ++j) {
-      P.j = j;
-      if (p->precond == GMRF_PREC_NONE)
-        CK(traced(KC_STENCIL_STEP, s, 1,
-                  [&] { return launch_stencil_step(p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s); }));
-      else
-        CK(launch_precond_step(p->pre, p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s));
-    }
+    CK(cudaGraphLaunch(G.exec, s));
     CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * b.nvec, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    trace_collect();
     bool running = false;
-    for (int v = 0; v < b.nvec; ++v) running |= (p->st_host[v].status == VS_RUNNING);
+    int mmax = 0;
+    for (int v = 0; v < b.nvec; ++v) {
+      running |= (p->st_host[v].status == VS_RUNNING);
+      mmax = std::max(mmax, p->st_host[v].m);
+    }
+    // steps of this replay in which some vector still iterated
+    const int useful = std::max(0, std::min(c, mmax - j));
+    trace_replayed(&G.tr, useful * G.kernels_per_step);
+    j += c;
     if (!running) break;
   }
   return GMRF_OK;
@@ -264,6 +355,8 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
   const double nd = (double)d->nx * (double)d->ny * (double)nz;
   if (nd > 4.0e9) return GMRF_ERR_INVALID;
   if (!d->kappa2 && (!(d->kappa2_const >= 0.0) || !std::isfinite(d->kappa2_const))) return GMRF_ERR_INVALID;
+  // a constant kappa^2 = 0 leaves the constant vector in the null space unless the boundary is Dirichlet
+  if (!d->kappa2 && d->bc != GMRF_BC_DIRICHLET && !(d->kappa2_const > 0.0)) return GMRF_ERR_INVALID;
   if (d->dim == 3 && d->op == GMRF_OP_SPDE_SQUARED) return GMRF_ERR_UNSUPPORTED;
   if (d->precond != GMRF_PREC_NONE) {
     if (d->dim != 2) return GMRF_ERR_UNSUPPORTED;
@@ -288,18 +381,27 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
     gmrf_destroy(p);
     return code;
   };
+  if (cudaStreamCreateWithFlags(&p->ws, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GMRF_ERR_CUDA);
+  }
+  if (enter(p) != GMRF_OK) return fail(GMRF_ERR_CUDA);
   double sum_log = 0.0, nzero = 0.0;
   if (d->kappa2) {
     if (ensure(p->kappa2, sizeof(float) * p->g.n) != GMRF_OK) return fail(GMRF_ERR_OOM);
     const cudaMemcpyKind kind = is_device_ptr(d->kappa2) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (cudaMemcpyAsync(p->kappa2.p, d->kappa2, sizeof(float) * p->g.n, kind, p->stream) != cudaSuccess)
+    if (cudaMemcpyAsync(p->kappa2.p, d->kappa2, sizeof(float) * p->g.n, kind, p->ws) != cudaSuccess)
       return fail(GMRF_ERR_CUDA);
     DevBuf stats;
     if (ensure(stats, 4 * sizeof(double)) != GMRF_OK) return fail(GMRF_ERR_OOM);
     double h[4] = {0, 0, 0, 0};
-    bool ok = launch_field_stats((const float*)p->kappa2.p, p->g.n, (double*)stats.p, p->stream) == cudaSuccess &&
-              cudaMemcpyAsync(h, stats.p, sizeof(h), cudaMemcpyDeviceToHost, p->stream) == cudaSuccess &&
-              cudaStreamSynchronize(p->stream) == cudaSuccess;
+    trace_begin(KC_OTHER, p->ws);
+    bool ok = launch_field_stats((const float*)p->kappa2.p, p->g.n, (double*)stats.p, p->ws) == cudaSuccess;
+    trace_end(KC_OTHER, p->ws);
+    ok = ok && cudaMemcpyAsync(h, stats.p, sizeof(h), cudaMemcpyDeviceToHost, p->ws) == cudaSuccess &&
+         cudaStreamSynchronize(p->ws) == cudaSuccess;
     release(stats);
     if (!ok) return fail(GMRF_ERR_CUDA);
     if (h[0] > 0.5) return fail(GMRF_ERR_INVALID);
@@ -320,24 +422,28 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
     if (!(kb > 0.0) && d->precond != GMRF_PREC_NONE && d->bc != GMRF_BC_DIRICHLET) return fail(GMRF_ERR_INVALID);
     if (!(kb > 0.0)) return fail(GMRF_ERR_INVALID);
     p->kbar2 = kb;
-    const int r = precond_build(p->pre, p->g, d->precond, d->op, kb, p->fp64, p->stream, &p->logdet_M);
+    const int r = precond_build(p->pre, p->g, d->precond, d->op, kb, p->fp64, p->ws, &p->logdet_M);
     if (r != GMRF_OK) return fail(r);
   }
-  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(GMRF_ERR_CUDA);
+  if (leave(p) != GMRF_OK || cudaStreamSynchronize(p->ws) != cudaSuccess) return fail(GMRF_ERR_CUDA);
+  trace_collect();
   *out = p;
   return GMRF_OK;
 }
 
 void gmrf_destroy(gmrf_problem* p) {
   if (!p) return;
-  if (p->stream) cudaStreamSynchronize(p->stream);
-  else cudaDeviceSynchronize();
+  if (p->ws) cudaStreamSynchronize(p->ws);
+  p->graph.reset();
   DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,
                     &p->partials, &p->counters, &p->y, &p->scratch, &p->nodes, &p->q, &p->out2, &p->stage,
                     &p->stage2, &p->work};
   for (DevBuf* b : bufs) release(*b);
   precond_free(p->pre);
   if (p->st_host) cudaFreeHost(p->st_host);
+  if (p->ev_in) cudaEventDestroy(p->ev_in);
+  if (p->ev_out) cudaEventDestroy(p->ev_out);
+  if (p->ws) cudaStreamDestroy(p->ws);
   delete p;
 }
 
@@ -354,7 +460,8 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
   const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) : 0);
   int chunk = batch_size(p, o->nsamples, nslots, m_max, true, extra);
   if (chunk < 1) return GMRF_ERR_OOM;
-  cudaStream_t s = p->stream;
+  cudaStream_t s = p->ws;
+  CKR(enter(p));
   std::vector<VecState> all((size_t)o->nsamples);
   for (int s0 = 0; s0 < o->nsamples; s0 += chunk) {
     const int c = std::min(chunk, o->nsamples - s0);
@@ -397,6 +504,7 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
     trace_collect();
     std::memcpy(all.data() + s0, p->st_host, sizeof(VecState) * c);
   }
+  CKR(leave(p));
   fill_info(all.data(), o->nsamples, info);
   return worst_status(all.data(), o->nsamples);
 }
@@ -412,7 +520,8 @@ int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, doub
   const bool z_dev = o->probes_in && is_device_ptr(o->probes_in);
   int chunk = batch_size(p, o->nprobes, 2, m_max, false, 0);
   if (chunk < 1) return GMRF_ERR_OOM;
-  cudaStream_t s = p->stream;
+  cudaStream_t s = p->ws;
+  CKR(enter(p));
   CKR(ensure(p->stage2, sizeof(double) * (o->nprobes + 2)));
   double* qall = (double*)p->stage2.p;
   std::vector<VecState> all((size_t)o->nprobes);
@@ -441,6 +550,7 @@ int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, doub
   if (q_out) CK(cudaMemcpyAsync(q_out, qall, sizeof(double) * o->nprobes, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   trace_collect();
+  CKR(leave(p));
   *logdet = res[0];
   *std_err = res[1];
   fill_info(all.data(), o->nprobes, info);
@@ -451,7 +561,8 @@ int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void
   if (!p || !v || !y || nvec < 1 || nvec > 65535 || which < 0 || which > 2) return GMRF_ERR_INVALID;
   if (which > 0 && p->precond == GMRF_PREC_NONE) return GMRF_ERR_INVALID;
   const size_t n = p->g.n, es = esize(p), bytes = (size_t)nvec * n * es;
-  cudaStream_t s = p->stream;
+  cudaStream_t s = p->ws;
+  CKR(enter(p));
   const bool vd = is_device_ptr(v), yd = is_device_ptr(y);
   const void* vin = v;
   void* yout = y;
@@ -481,6 +592,7 @@ int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void
   if (!yd) CK(cudaMemcpyAsync(y, yout, bytes, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   trace_collect();
+  CKR(leave(p));
   return GMRF_OK;
 }
 

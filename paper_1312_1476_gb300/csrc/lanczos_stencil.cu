@@ -32,8 +32,10 @@ constexpr int NT = TX * TY;
 
 template <typename T>
 struct StencilArgs {
-  const T* Win;
-  T* Wout;
+  const T* Win;  // apply mode: v
+  T* Wout;       // apply mode: y
+  T* W0;         // step mode: q ping-pong, W[j & 1] read, W[(j+1) & 1] written
+  T* W1;
   T* V;  // basis ring base
   const float* kappa2;
   T kappa2_const;
@@ -87,13 +89,17 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
   __shared__ float s_flt[4];
 
   const int s = blockIdx.z;
-  const int j = a.P.j;
-  if (STEP && a.st[s].status != VS_RUNNING) return;
+  int j = 0;
+  if (STEP) {
+    if (a.st[s].status != VS_RUNNING) return;
+    j = a.st[s].m;
+  }
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int nx = a.nx, ny = a.ny;
   const size_t n = a.n;
-  const T* Win = a.Win + (size_t)s * n;
+  const T* Win = (STEP ? ((j & 1) ? a.W1 : a.W0) : a.Win) + (size_t)s * n;
+  T* Wout = (STEP ? ((j & 1) ? a.W0 : a.W1) : a.Wout) + (size_t)s * n;
   const T* Vp = nullptr;
   T* Vc = nullptr;
   T coef = 0, inv_b = 1, bprev = 0;
@@ -161,12 +167,12 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
     if (OP == GMRF_OP_SPDE_SQUARED) qv = bop2<T, BC, GW>(gs, tx + 1, ty + 1, gx, gy, nx, ny, kap);
     else qv = bop2<T, BC, VW>(vs, tx + H, ty + H, gx, gy, nx, ny, kap);
     if (!STEP) {
-      a.Wout[(size_t)s * n + i] = qv;
+      Wout[i] = qv;
     } else {
       const T v = vs[(ty + H) * VW + tx + H];
       T q = qv;
       if (j > 0) q -= bprev * Vp[i];
-      a.Wout[(size_t)s * n + i] = q;
+      Wout[i] = q;
       Vc[i] = v;
       d.add(v, q);
     }
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
   const int nblk = gridDim.x * gridDim.y;
   if (tid == 0) a.partials[(size_t)s * nblk + blockIdx.x + gridDim.x * blockIdx.y] = d;
   if (last_block(a.counters, s, nblk, &s_int[3]))
-    finish_step<T>(a.P, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
+    finish_step<T>(a.P, j, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
 }
 
 // 3-D shifted Laplacian (7-point), z-march over a chunk of planes.
@@ -189,15 +195,19 @@ __global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
   __shared__ float s_flt[4];
   const int s = blockIdx.z / a.nzc;
   const int zc = blockIdx.z - s * a.nzc;
-  const int j = a.P.j;
-  if (STEP && a.st[s].status != VS_RUNNING) return;
+  int j = 0;
+  if (STEP) {
+    if (a.st[s].status != VS_RUNNING) return;
+    j = a.st[s].m;
+  }
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t n = a.n, plane = (size_t)nx * ny;
   const int zper = (nz + a.nzc - 1) / a.nzc;
   const int z0 = zc * zper, z1 = min(nz, z0 + zper);
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const T* Win = a.Win + (size_t)s * n;
+  const T* Win = (STEP ? ((j & 1) ? a.W1 : a.W0) : a.Win) + (size_t)s * n;
+  T* Wout = (STEP ? ((j & 1) ? a.W0 : a.W1) : a.Wout) + (size_t)s * n;
   const T* Vp = nullptr;
   T* Vc = nullptr;
   T coef = 0, inv_b = 1, bprev = 0;
@@ -273,11 +283,11 @@ __global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
       if (BC != GMRF_BC_NEUMANN || z > 0) r += vc - vdn;
       if (BC != GMRF_BC_NEUMANN || z < nz - 1) r += vc - vup;
       if (!STEP) {
-        a.Wout[(size_t)s * n + i] = r;
+        Wout[i] = r;
       } else {
         T q = r;
         if (j > 0) q -= bprev * vpc;
-        a.Wout[(size_t)s * n + i] = q;
+        Wout[i] = q;
         Vc[i] = vc;
         d.add(vc, q);
       }
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
   const int nblk = gridDim.x * gridDim.y * a.nzc;
   if (tid == 0) a.partials[(size_t)s * nblk + blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc)] = d;
   if (last_block(a.counters, s, nblk, &s_int[3]))
-    finish_step<T>(a.P, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
+    finish_step<T>(a.P, j, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
 }
 
 int nz_chunks(const Grid& g) {
@@ -357,11 +367,10 @@ int stencil_blocks_per_vector(const Grid& g) {
 
 cudaError_t launch_stencil_step(const Grid& g, bool fp64, const void* kappa2, double kappa2_const,
                                 const LanczosBufs& b, const StepParams& P, cudaStream_t s) {
-  const int j = P.j;
   if (fp64) {
     auto a = make_args<double>(g, kappa2, kappa2_const);
-    a.Win = (const double*)b.W[j & 1];
-    a.Wout = (double*)b.W[(j + 1) & 1];
+    a.W0 = (double*)b.W[0];
+    a.W1 = (double*)b.W[1];
     a.V = (double*)b.V;
     a.P = P;
     a.st = b.st; a.alpha = b.alpha; a.beta = b.beta; a.alpha_f = b.alpha_f; a.beta2_f = b.beta2_f;
@@ -370,8 +379,8 @@ cudaError_t launch_stencil_step(const Grid& g, bool fp64, const void* kappa2, do
     return dispatch<double, true>(g, a, b.nvec, s);
   }
   auto a = make_args<float>(g, kappa2, kappa2_const);
-  a.Win = (const float*)b.W[j & 1];
-  a.Wout = (float*)b.W[(j + 1) & 1];
+  a.W0 = (float*)b.W[0];
+  a.W1 = (float*)b.W[1];
   a.V = (float*)b.V;
   a.P = P;
   a.st = b.st; a.alpha = b.alpha; a.beta = b.beta; a.alpha_f = b.alpha_f; a.beta2_f = b.beta2_f;

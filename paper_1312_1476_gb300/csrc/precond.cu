@@ -55,9 +55,9 @@ struct PArgs {
   const float* kappa2;
   R kappa2_const;
   size_t n;
-  // Lanczos
-  const R* Win;
-  R* Wout;
+  // Lanczos: q ping-pong, W[j & 1] holds q_{j-1}, W[(j+1) & 1] receives q_j
+  R* W0;
+  R* W1;
   R* V;
   StepParams P;
   VecState* st;
@@ -205,7 +205,11 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
   typedef typename Cplx<R>::T C;
   const int s = blockIdx.y;
   const bool step = (MODE == M_FWD_FORM || MODE == M_LAST || (MODE == M_MID && a.in == nullptr));
-  if (step && a.st[s].status != VS_RUNNING) return;
+  int j = 0;
+  if (step) {
+    if (a.st[s].status != VS_RUNNING) return;
+    j = a.st[s].m;  // step index: completed steps of this vector
+  }
   const int tid = block_tid(), nt = block_nt();
   const int nx = a.nx, ny = a.ny, rb = a.rb;
   const int PL = nx + 2;
@@ -252,7 +256,6 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
   R* GL = B2 + (size_t)LMAX * PL;
   R* Sv = a.S + (size_t)s * a.sstride;
   const size_t n = a.n;
-  const int j = a.P.j;
 
   if (MODE == M_FWD_PLAIN || MODE == M_FWD_FORM) {
     const R* Win = nullptr;
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
     R coef = 0, inv_b = 1;
     if (MODE == M_FWD_FORM) {
       const size_t base = (size_t)s * a.P.nslots;
-      Win = a.Win + (size_t)s * n;
+      Win = ((j & 1) ? a.W1 : a.W0) + (size_t)s * n;
       Vc = a.V + (base + (size_t)(j % a.P.nslots)) * n;
       if (j == 0) {
         inv_b = (R)(1.0 / a.st[s].znorm);
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
     const R* Vc = a.V + (base + (size_t)(j % a.P.nslots)) * n;
     const R* Vp = j > 0 ? a.V + (base + (size_t)((j - 1) % a.P.nslots)) * n : nullptr;
     const R bprev = j > 0 ? (R)a.beta[(size_t)s * a.P.m_max + (j - 1)] : (R)0;
-    R* Wo = a.Wout + (size_t)s * n;
+    R* Wo = ((j & 1) ? a.W0 : a.W1) + (size_t)s * n;
     for (int idx = tid; idx < rb * nx; idx += nt) {
       const int l = idx / nx, x = idx - l * nx;
       const size_t i = (size_t)(y0 + l) * nx + x;
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
   const int nblk = gridDim.x;
   if (tid == 0) a.partials[(size_t)s * nblk + blockIdx.x] = d;
   if (last_block(a.counters, s, nblk, &s_int[3]))
-    finish_step<R>(a.P, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
+    finish_step<R>(a.P, j, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
 }
 
 // Column pass: forward transform along y, multiply by the symbol of
@@ -577,10 +580,46 @@ int ensure_ws(PrecondTables& t, int nvec) {
   return 0;
 }
 
+int smem_optin() {
+  static int v = 0;
+  if (!v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaGetLastError();
+      v = 48 * 1024;
+    }
+  }
+  return v;
+}
+
+// Raise the dynamic shared memory limit of a kernel once per process.
+template <typename K>
+cudaError_t allow_smem(K* k, bool& done) {
+  if (done) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin() - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <typename R, int KIND, int MODE>
+cudaError_t row_attr() {
+  static bool done = false;
+  return allow_smem(k_prow<R, KIND, MODE>, done);
+}
+template <typename R, int KIND>
+cudaError_t col_attr() {
+  static bool done = false;
+  return allow_smem(k_pcol<R, KIND>, done);
+}
+
 template <typename R, int KIND, int MODE>
 cudaError_t row_launch(const PrecondTables& t, const PArgs<R>& a, int nvec, cudaStream_t s, int kc) {
   const size_t sm = row_smem<R>(t);
-  cudaError_t e = cudaFuncSetAttribute(k_prow<R, KIND, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = row_attr<R, KIND, MODE>();
   if (e != cudaSuccess) return e;
   dim3 grd(t.ny / t.rb, nvec);
   trace_begin(kc, s);
@@ -594,7 +633,7 @@ cudaError_t col_launch(const PrecondTables& t, PArgs<R> a, int nvec, int step_mo
   const int cw = col_width(t);
   a.cw = cw;
   const size_t sm = col_smem<R>(t, cw);
-  cudaError_t e = cudaFuncSetAttribute(k_pcol<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = col_attr<R, KIND>();
   if (e != cudaSuccess) return e;
   const int ncols = KIND == GMRF_PREC_CIRCULANT ? t.nx / 2 + 1 : t.nx;
   dim3 grd((ncols + cw - 1) / cw, nvec);
@@ -617,9 +656,8 @@ cudaError_t run_step(PrecondTables& t, const Grid& g, const void* kappa2, double
   PArgs<R> a = base_args<R>(t, g, kappa2, kc);
   a.G = (R*)t.G;
   a.S = (R*)t.S;
-  const int j = P.j;
-  a.Win = (const R*)b.W[j & 1];
-  a.Wout = (R*)b.W[(j + 1) & 1];
+  a.W0 = (R*)b.W[0];
+  a.W1 = (R*)b.W[1];
   a.V = (R*)b.V;
   a.P = P;
   a.st = b.st;
@@ -666,6 +704,18 @@ cudaError_t run_operator(PrecondTables& t, const Grid& g, const void* kappa2, do
   CKE((col_launch<R, KIND>(t, a, nvec, 0, s, KC_PRE_APPLY)));
   CKE((row_launch<R, KIND, M_LAST_PLAIN>(t, a, nvec, s, KC_PRE_APPLY)));
   return cudaSuccess;
+}
+
+template <typename R, int KIND>
+cudaError_t set_attrs() {
+  cudaError_t e;
+  if ((e = row_attr<R, KIND, M_FWD_PLAIN>()) != cudaSuccess) return e;
+  if ((e = row_attr<R, KIND, M_FWD_FORM>()) != cudaSuccess) return e;
+  if ((e = row_attr<R, KIND, M_INV_PLAIN>()) != cudaSuccess) return e;
+  if ((e = row_attr<R, KIND, M_MID>()) != cudaSuccess) return e;
+  if ((e = row_attr<R, KIND, M_LAST>()) != cudaSuccess) return e;
+  if ((e = row_attr<R, KIND, M_LAST_PLAIN>()) != cudaSuccess) return e;
+  return col_attr<R, KIND>();
 }
 
 template <typename R>
@@ -775,6 +825,16 @@ void precond_free(PrecondTables& t) {
 }
 
 int precond_blocks_per_vector(const PrecondTables& t) { return t.nx ? t.ny / t.rb : 0; }
+
+int precond_prepare(PrecondTables& t, int nvec) {
+  if (ensure_ws(t, nvec)) return GMRF_ERR_OOM;
+  cudaError_t e;
+  if (t.fp64) e = t.kind == GMRF_PREC_CIRCULANT ? set_attrs<double, GMRF_PREC_CIRCULANT>()
+                                               : set_attrs<double, GMRF_PREC_MIRROR>();
+  else e = t.kind == GMRF_PREC_CIRCULANT ? set_attrs<float, GMRF_PREC_CIRCULANT>()
+                                         : set_attrs<float, GMRF_PREC_MIRROR>();
+  return e == cudaSuccess ? GMRF_OK : GMRF_ERR_CUDA;
+}
 
 size_t precond_extra_bytes(const PrecondTables& t, size_t es) {
   return (size_t)t.ny * (t.nx + 2) * es + (size_t)t.nx * t.ny * es;

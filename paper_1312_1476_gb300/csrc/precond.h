@@ -41,6 +41,9 @@ int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar
                   double* logdet_M);
 void precond_free(PrecondTables& t);
 int precond_blocks_per_vector(const PrecondTables& t);
+// Workspace for nvec vectors and kernel attributes; call before capturing
+// the preconditioned steps into a CUDA graph.
+int precond_prepare(PrecondTables& t, int nvec);
 size_t precond_extra_bytes(const PrecondTables& t, size_t es);
 // Fused preconditioned Lanczos step j (A = M^{-1/2} Q M^{-1/2}, applied as
 // C^T C with C = I + R B_bar^{-1} for the squared operator and as

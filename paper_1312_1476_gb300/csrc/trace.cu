@@ -29,6 +29,9 @@ Registry& reg() {
   return r;
 }
 
+GraphTrace* g_sink = nullptr;
+int g_open_kc = -1;
+
 cudaEvent_t take() {
   Registry& r = reg();
   if (!r.pool.empty()) {
@@ -48,6 +51,24 @@ cudaEvent_t take() {
 
 void trace_begin(int kc, cudaStream_t s, int nkernels) {
   Registry& r = reg();
+  if (g_sink) {
+    g_sink->launches[kc] += nkernels;
+    g_open_kc = -1;
+    if (g_sink->timed && g_sink->npairs < 4096) {
+      const int i = g_sink->npairs;
+      g_sink->a[i] = g_sink->b[i] = nullptr;
+      if (cudaEventCreate(&g_sink->a[i]) == cudaSuccess && cudaEventCreate(&g_sink->b[i]) == cudaSuccess &&
+          cudaEventRecordWithFlags(g_sink->a[i], s, cudaEventRecordExternal) == cudaSuccess) {
+        g_sink->kc[i] = kc;
+        g_open_kc = kc;
+      } else {
+        cudaGetLastError();
+        if (g_sink->a[i]) cudaEventDestroy(g_sink->a[i]);
+        if (g_sink->b[i]) cudaEventDestroy(g_sink->b[i]);
+      }
+    }
+    return;
+  }
   r.launches[kc] += nkernels;
   if (!r.timing) return;
   r.open.kc = kc;
@@ -58,6 +79,15 @@ void trace_begin(int kc, cudaStream_t s, int nkernels) {
 
 void trace_end(int kc, cudaStream_t s) {
   Registry& r = reg();
+  if (g_sink) {
+    if (g_open_kc == kc) {
+      const int i = g_sink->npairs;
+      if (cudaEventRecordWithFlags(g_sink->b[i], s, cudaEventRecordExternal) == cudaSuccess) g_sink->npairs++;
+      else cudaGetLastError();
+    }
+    g_open_kc = -1;
+    return;
+  }
   if (!r.timing || r.open.kc != kc) return;
   if (r.open.a && r.open.b) {
     cudaEventRecord(r.open.b, s);
@@ -83,6 +113,45 @@ void trace_collect() {
     r.pool.push_back(p.b);
   }
   r.pending.clear();
+}
+
+bool trace_timing_enabled() { return reg().timing; }
+
+void GraphTrace::release() {
+  for (int i = 0; i < npairs; ++i) {
+    cudaEventDestroy(a[i]);
+    cudaEventDestroy(b[i]);
+  }
+  npairs = 0;
+  for (int k = 0; k < KC_COUNT; ++k) launches[k] = 0;
+}
+
+void trace_capture_begin(GraphTrace* g) {
+  g->release();
+  g->timed = reg().timing;
+  g_sink = g;
+  g_open_kc = -1;
+}
+
+void trace_capture_end() {
+  g_sink = nullptr;
+  g_open_kc = -1;
+}
+
+void trace_replayed(const GraphTrace* g, int useful_pairs) {
+  Registry& r = reg();
+  for (int k = 0; k < KC_COUNT; ++k) r.launches[k] += g->launches[k];
+  if (!r.timing || !g->timed) return;
+  const int np = useful_pairs < g->npairs ? useful_pairs : g->npairs;
+  for (int i = 0; i < np; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, g->a[i], g->b[i]) == cudaSuccess) {
+      r.ms[g->kc[i]] += t;
+      r.timed[g->kc[i]] += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
 }
 
 }  // namespace gmrf

@@ -30,6 +30,26 @@ enum KernelClass {
 void trace_begin(int kc, cudaStream_t s, int nkernels = 1);
 void trace_end(int kc, cudaStream_t s);
 void trace_collect();
+bool trace_timing_enabled();
+
+// Launches and event pairs recorded while a CUDA graph is being captured.
+// The events become external event-record nodes of the graph, so every replay
+// re-records them; trace_replayed() accounts one completed replay.
+struct GraphTrace {
+  bool timed = false;
+  int64_t launches[KC_COUNT] = {};
+  int kc[4096];
+  cudaEvent_t a[4096];
+  cudaEvent_t b[4096];
+  int npairs = 0;
+  void release();
+};
+void trace_capture_begin(GraphTrace* g);  // route trace_begin/end into g
+void trace_capture_end();
+// After a replay has completed: adds its launches, and the times of its
+// first `useful_pairs` timed launches (launches of steps in which some
+// vector was still iterating; later steps exit at entry and are not timed).
+void trace_replayed(const GraphTrace* g, int useful_pairs);
 
 template <typename F>
 inline cudaError_t traced(int kc, cudaStream_t s, int nkernels, F f) {
