@@ -24,11 +24,14 @@
 //   -> row-last (inverse rows, A v_j, q_j, dot products, alpha/beta, stopping rule).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "fft.cuh"
 #include "precond.h"
+#include "precond_fast.h"
 #include "trace.h"
 
 namespace gmrf {
@@ -577,7 +580,40 @@ int ensure_ws(PrecondTables& t, int nvec) {
     if (cudaMalloc(&t.G, gb) != cudaSuccess) return -1;
     t.G_bytes = gb;
   }
+  const bool edges = t.kind == GMRF_PREC_CIRCULANT ? t.bc != GMRF_BC_PERIODIC : t.bc != GMRF_BC_NEUMANN;
+  const size_t wb = (t.fast && edges) ? (size_t)nvec * t.nx * t.ny * es : 16;
+  if (t.Wg_bytes < wb) {
+    if (t.Wg) cudaFree(t.Wg);
+    t.Wg = nullptr;
+    t.Wg_bytes = 0;
+    if (cudaMalloc(&t.Wg, wb) != cudaSuccess) return -1;
+    t.Wg_bytes = wb;
+  }
   return 0;
+}
+
+fast::Args fast_args(const PrecondTables& t, const Grid& g, const void* kappa2, double kc) {
+  fast::Args a{};
+  a.nx = t.nx;
+  a.ny = t.ny;
+  a.bc = g.bc;
+  a.power = t.power;
+  a.kbar2 = (float)t.kbar2;
+  a.dscale = (float)(t.kind == GMRF_PREC_CIRCULANT ? 2.0 / ((double)t.nx * t.ny) : 4.0 / ((double)t.nx * t.ny));
+  a.lamx = (const float*)t.lamx;
+  a.lamy = (const float*)t.lamy;
+  a.twx = (const float2*)t.twx;
+  a.twy = (const float2*)t.twy;
+  a.dctx = (const float2*)t.dctx;
+  a.dcty = (const float2*)t.dcty;
+  a.T = (float*)t.S;
+  a.tstride = (size_t)t.ny * (t.nx + 2);
+  a.G = (float*)t.G;
+  a.Wg = (float*)t.Wg;
+  a.kappa2 = (const float*)kappa2;
+  a.kappa2_const = (float)kc;
+  a.n = g.n;
+  return a;
 }
 
 int smem_optin() {
@@ -653,6 +689,22 @@ template <typename R, int KIND>
 cudaError_t run_step(PrecondTables& t, const Grid& g, const void* kappa2, double kc, const LanczosBufs& b,
                      const StepParams& P, cudaStream_t s) {
   if (ensure_ws(t, b.nvec)) return cudaErrorMemoryAllocation;
+  if (t.fast) {
+    fast::Args a = fast_args(t, g, kappa2, kc);
+    a.W0 = (float*)b.W[0];
+    a.W1 = (float*)b.W[1];
+    a.V = (float*)b.V;
+    a.P = P;
+    a.st = b.st;
+    a.alpha = b.alpha;
+    a.beta = b.beta;
+    a.alpha_f = b.alpha_f;
+    a.beta2_f = b.beta2_f;
+    a.partials = (Dots<float>*)b.partials;
+    a.counters = b.counters;
+    a.in = nullptr;
+    return KIND == GMRF_PREC_CIRCULANT ? fast_step_circ(a, b.nvec, s) : fast_step_mirror(a, b.nvec, s);
+  }
   PArgs<R> a = base_args<R>(t, g, kappa2, kc);
   a.G = (R*)t.G;
   a.S = (R*)t.S;
@@ -679,6 +731,12 @@ cudaError_t run_step(PrecondTables& t, const Grid& g, const void* kappa2, double
 template <typename R, int KIND>
 cudaError_t run_apply(PrecondTables& t, const Grid& g, const void* in, void* out, int nvec, cudaStream_t s) {
   if (ensure_ws(t, nvec)) return cudaErrorMemoryAllocation;
+  if (t.fast) {
+    fast::Args a = fast_args(t, g, nullptr, 0.0);
+    a.in = (const float*)in;
+    a.out = (float*)out;
+    return KIND == GMRF_PREC_CIRCULANT ? fast_apply_circ(a, nvec, s) : fast_apply_mirror(a, nvec, s);
+  }
   PArgs<R> a = base_args<R>(t, g, nullptr, 0.0);
   a.S = (R*)t.S;
   a.in = (const R*)in;
@@ -693,6 +751,12 @@ template <typename R, int KIND>
 cudaError_t run_operator(PrecondTables& t, const Grid& g, const void* kappa2, double kc, const void* v, void* y,
                          int nvec, cudaStream_t s) {
   if (ensure_ws(t, nvec)) return cudaErrorMemoryAllocation;
+  if (t.fast) {
+    fast::Args a = fast_args(t, g, kappa2, kc);
+    a.in = (const float*)v;
+    a.out = (float*)y;
+    return KIND == GMRF_PREC_CIRCULANT ? fast_operator_circ(a, nvec, s) : fast_operator_mirror(a, nvec, s);
+  }
   PArgs<R> a = base_args<R>(t, g, kappa2, kc);
   a.S = (R*)t.S;
   a.G = (R*)t.G;
@@ -781,6 +845,8 @@ int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar
   t.logny = ilog2(g.ny);
   t.fp64 = fp64;
   t.kbar2 = kbar2;
+  t.bc = g.bc;
+  t.fast = fast_eligible(kind, fp64, g.nx, g.ny);
   if (fp64 && (g.nx > 2048 || g.ny > 2048)) return GMRF_ERR_UNSUPPORTED;
   int rb = (fp64 ? 2048 : 4096) / g.nx;
   if (rb < 1) rb = 1;
@@ -818,13 +884,18 @@ int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar
 }
 
 void precond_free(PrecondTables& t) {
-  void* ps[] = {t.lamx, t.lamy, t.twx, t.twy, t.dctx, t.dcty, t.S, t.G};
+  void* ps[] = {t.lamx, t.lamy, t.twx, t.twy, t.dctx, t.dcty, t.S, t.G, t.Wg};
   for (void* p : ps)
     if (p) cudaFree(p);
   t = PrecondTables();
 }
 
-int precond_blocks_per_vector(const PrecondTables& t) { return t.nx ? t.ny / t.rb : 0; }
+int precond_blocks_per_vector(const PrecondTables& t) {
+  if (!t.nx) return 0;
+  int nb = t.ny / t.rb;
+  if (t.fast) nb = std::max(nb, t.ny / fast_rows_per_block(t.kind, t.nx));
+  return nb;
+}
 
 int precond_prepare(PrecondTables& t, int nvec) {
   if (ensure_ws(t, nvec)) return GMRF_ERR_OOM;

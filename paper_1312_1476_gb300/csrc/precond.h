@@ -33,7 +33,11 @@ struct PrecondTables {
   size_t S_bytes = 0;
   void* G = nullptr;     // g = C v workspace (SPDE squared), per vector n reals
   size_t G_bytes = 0;
-  int rb = 4;            // rows per row-kernel block
+  void* Wg = nullptr;    // w workspace (fast path with boundary terms in y), per vector n reals
+  size_t Wg_bytes = 0;
+  int rb = 4;            // rows per row-kernel block (generic path)
+  int bc = 0;            // boundary condition of the problem
+  bool fast = false;     // FP32 register-FFT kernels with the transposed spectrum
 };
 
 bool precond_size_ok(int64_t n);
