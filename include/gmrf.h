@@ -179,6 +179,35 @@ int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t 
  * Process-wide, not thread-safe; any output pointer may be NULL. */
 int gmrf_trace(int32_t op, int32_t kclass, double* total_ms, int64_t* launches, int64_t* timed);
 
+/* Allocation-free y = M^{-1/2} v (the operation of gmrf_apply with which = 2).
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory during the call -- code that is inside CUDA stream capture
+ * (cudaMalloc is not allowed there), code that hands all device memory to its
+ * own pool or allocator and forbids allocations behind its back, and
+ * latency-critical loops that cannot afford an allocation.  gmrf_apply may
+ * grow the problem's transform workspace with cudaMalloc on first use; this
+ * entry point calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Its transform scratch is one library-wide static device array of
+ * GMRF_NOALLOC_SCRATCH_BYTES (32 MiB), held on every GPU that loads the
+ * library until the process exits.  A call needs nvec * ny * (nx + 2) *
+ * (4 for FP32, 8 for FP64) bytes of it; larger requests return
+ * GMRF_ERR_INVALID (a 1024 x 1024 FP32 grid fits 7 vectors per call).
+ * v and y: device pointers, [nvec][n] of the problem's precision; host
+ * pointers return GMRF_ERR_INVALID.  The problem needs a preconditioner.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents; nothing in it needs to start at zero,
+ * because every call overwrites the part it reads.  Calls whose GPU work
+ * overlaps -- from different problems, streams or host threads -- race on
+ * the array and must be serialised by the caller.  With kernel tracing
+ * enabled (gmrf_trace op 1) the library still creates CUDA events, which are
+ * not device memory. */
+#define GMRF_NOALLOC_SCRATCH_BYTES (32 << 20)
+int gmrf_apply_inv_sqrt_noalloc(gmrf_problem* p, int64_t nvec, const void* v, void* y);
+
 void gmrf_destroy(gmrf_problem* p);
 const char* gmrf_strerror(int code);
 

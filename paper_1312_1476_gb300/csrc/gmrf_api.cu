@@ -13,6 +13,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -626,3 +627,61 @@ int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of gmrf_apply(which = 2): y = M^{-1/2} v.
+//
+// Its only scratch, the transform workspace, is this file-scope device array
+// of GMRF_NOALLOC_SCRATCH_BYTES.  Every GPU that loads the library holds it
+// until the process exits.  In host code the symbol is only a stand-in, so
+// its device address is looked up with cudaGetSymbolAddress once per device,
+// with that device current, on the first call made on it.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GMRF_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return GMRF_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return GMRF_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return GMRF_OK;
+}
+
+}  // namespace
+
+extern "C" int gmrf_apply_inv_sqrt_noalloc(gmrf_problem* p, int64_t nvec, const void* v, void* y) {
+  if (!p || !v || !y || nvec < 1 || nvec > 65535) return GMRF_ERR_INVALID;
+  if (p->precond == GMRF_PREC_NONE) return GMRF_ERR_INVALID;
+  if (!is_device_ptr(v) || !is_device_ptr(y)) return GMRF_ERR_INVALID;
+  if (precond_apply_scratch_bytes(p->pre, (int)nvec) > (size_t)GMRF_NOALLOC_SCRATCH_BYTES) return GMRF_ERR_INVALID;
+  void* scratch = nullptr;
+  CKR(noalloc_scratch(&scratch));
+  cudaStream_t s = p->ws;
+  CKR(enter(p));
+  // the spectrum is fully written by the forward row pass before it is read:
+  // nothing in the shared scratch has to start at zero
+  CK(traced(KC_PRE_APPLY, s, 3, [&] {
+    return launch_precond_apply_with(p->pre, p->g, p->fp64, v, y, (int)nvec, scratch, s);
+  }));
+  CK(traced(KC_OTHER, s, 1, [&] { return launch_scale(p->fp64, y, (size_t)nvec * p->g.n, 1.0 / std::sqrt(p->tau), s); }));
+  CK(cudaStreamSynchronize(s));
+  trace_collect();
+  CKR(leave(p));
+  return GMRF_OK;
+}

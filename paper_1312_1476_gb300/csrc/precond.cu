@@ -728,17 +728,21 @@ cudaError_t run_step(PrecondTables& t, const Grid& g, const void* kappa2, double
   return cudaSuccess;
 }
 
+// Sbuf: spectrum workspace (nullptr = the tables' own, grown on demand)
 template <typename R, int KIND>
-cudaError_t run_apply(PrecondTables& t, const Grid& g, const void* in, void* out, int nvec, cudaStream_t s) {
-  if (ensure_ws(t, nvec)) return cudaErrorMemoryAllocation;
+cudaError_t run_apply(PrecondTables& t, const Grid& g, const void* in, void* out, int nvec, cudaStream_t s,
+                      void* Sbuf = nullptr) {
+  if (!Sbuf && ensure_ws(t, nvec)) return cudaErrorMemoryAllocation;
+  void* S = Sbuf ? Sbuf : t.S;
   if (t.fast) {
     fast::Args a = fast_args(t, g, nullptr, 0.0);
+    a.T = (float*)S;
     a.in = (const float*)in;
     a.out = (float*)out;
     return KIND == GMRF_PREC_CIRCULANT ? fast_apply_circ(a, nvec, s) : fast_apply_mirror(a, nvec, s);
   }
   PArgs<R> a = base_args<R>(t, g, nullptr, 0.0);
-  a.S = (R*)t.S;
+  a.S = (R*)S;
   a.in = (const R*)in;
   a.out = (R*)out;
   CKE((row_launch<R, KIND, M_FWD_PLAIN>(t, a, nvec, s, KC_PRE_APPLY)));
@@ -930,6 +934,21 @@ cudaError_t launch_precond_apply(PrecondTables& t, const Grid& g, bool fp64, int
   }
   if (t.kind == GMRF_PREC_CIRCULANT) return run_apply<float, GMRF_PREC_CIRCULANT>(t, g, in, out, nvec, s);
   return run_apply<float, GMRF_PREC_MIRROR>(t, g, in, out, nvec, s);
+}
+
+size_t precond_apply_scratch_bytes(const PrecondTables& t, int nvec) {
+  return (size_t)nvec * t.ny * (t.nx + 2) * (t.fp64 ? 8 : 4);
+}
+
+cudaError_t launch_precond_apply_with(PrecondTables& t, const Grid& g, bool fp64, const void* in, void* out, int nvec,
+                                      void* S, cudaStream_t s) {
+  if (!S) return cudaErrorInvalidValue;
+  if (fp64) {
+    if (t.kind == GMRF_PREC_CIRCULANT) return run_apply<double, GMRF_PREC_CIRCULANT>(t, g, in, out, nvec, s, S);
+    return run_apply<double, GMRF_PREC_MIRROR>(t, g, in, out, nvec, s, S);
+  }
+  if (t.kind == GMRF_PREC_CIRCULANT) return run_apply<float, GMRF_PREC_CIRCULANT>(t, g, in, out, nvec, s, S);
+  return run_apply<float, GMRF_PREC_MIRROR>(t, g, in, out, nvec, s, S);
 }
 
 cudaError_t launch_precond_operator(PrecondTables& t, const Grid& g, bool fp64, const void* kappa2,

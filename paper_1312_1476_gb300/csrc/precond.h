@@ -57,6 +57,12 @@ cudaError_t launch_precond_step(PrecondTables& t, const Grid& g, bool fp64, cons
 // out = B_bar^{-p/2} in for nvec vectors (tau not applied).
 cudaError_t launch_precond_apply(PrecondTables& t, const Grid& g, bool fp64, int which, const void* in, void* out,
                                  int nvec, cudaStream_t s);
+// Same as launch_precond_apply, but the spectrum lives in the caller's
+// workspace S of at least precond_apply_scratch_bytes(t, nvec) bytes; no
+// device memory is allocated.
+size_t precond_apply_scratch_bytes(const PrecondTables& t, int nvec);
+cudaError_t launch_precond_apply_with(PrecondTables& t, const Grid& g, bool fp64, const void* in, void* out, int nvec,
+                                      void* S, cudaStream_t s);
 // y = A v for nvec vectors.
 cudaError_t launch_precond_operator(PrecondTables& t, const Grid& g, bool fp64, const void* kappa2,
                                     double kappa2_const, const void* v, void* y, int nvec, cudaStream_t s);

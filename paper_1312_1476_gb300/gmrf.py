@@ -78,6 +78,7 @@ def _load():
                                     ctypes.c_uint64, P, P]),
         "gmrf_trace": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "gmrf_apply_inv_sqrt_noalloc": (ctypes.c_int, [P, ctypes.c_int64, P, P]),
         "gmrf_destroy": (None, [P]),
         "gmrf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -225,6 +226,13 @@ class Problem:
         if raise_on_error and rc not in (OK, ERR_NOT_CONVERGED):
             raise GmrfError(rc, "gmrf_logdet")
         return ld.value, se.value, q, infos, rc
+
+    def apply_inv_sqrt_noalloc(self, v, y, nvec=1):
+        """y = M^{-1/2} v without any device allocation (device pointers only;
+        scratch in a fixed library-wide device array, see include/gmrf.h)."""
+        rc = _lib.gmrf_apply_inv_sqrt_noalloc(self._h, int(nvec), _ptr(v), _ptr(y))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_apply_inv_sqrt_noalloc")
 
     def apply(self, which, v, y, nvec=1):
         """which 0: y = Q v; 1: y = A v (preconditioned operator); 2: y = M^{-1/2} v."""
