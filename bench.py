@@ -66,9 +66,10 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv"
+        fd, self.path = tempfile.mkstemp(prefix="gmrf_clocks_", suffix=".csv")
+        os.close(fd)
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
@@ -306,11 +307,87 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.precond, m_scale=int(round(np.mean(ms_used))))
+        if not args.no_variants:
+            out["variants"] = measure_variants(args, gmrf, torch, flush, peak)
         print(json.dumps(out), flush=True)
     prob.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def measure_variants(args, gmrf, torch, flush, peak):
+    """Other measured workloads, reported beside the headline."""
+    from paper_1312_1476_gb300 import inputs
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        ms = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn(i)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.mean(ms)), r
+
+    # plain-torus circulant preconditioner on the headline input
+    shape = (GRID, GRID)
+    n = GRID * GRID
+    k2 = torch.from_numpy(inputs.kappa2_gp_field(shape, seed=KAPPA_SEED)).cuda()
+    with gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond="circulant",
+                      stream=stream.cuda_stream) as p:
+        x = torch.empty(n, dtype=torch.float32, device="cuda")
+        p.sample(x, nsamples=1, tol=TOL, m_max=M_MAX, seed=1)
+        ms, (rc, info) = timed(lambda i: p.sample(x, nsamples=1, tol=TOL, m_max=M_MAX, seed=10 + i), 3)
+        out["circulant"] = {"workload": "same input, plain-torus circulant M", "samples_per_s": 1e3 / ms,
+                            "ms_per_sample": ms, "m_used": info[0].m_used, "status": rc}
+
+    # batched 512^2: 256 samples + log det with 64 Rademacher probes in one call each
+    shape = (512, 512)
+    n = 512 * 512
+    k2 = torch.from_numpy(inputs.kappa2_gp_field(shape, seed=KAPPA_SEED, ell=64.0)).cuda()
+    with gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond="mirror",
+                      stream=stream.cuda_stream) as p:
+        ns = 256
+        x = torch.empty(ns * n, dtype=torch.float32, device="cuda")
+        p.sample(x, nsamples=ns, tol=TOL, m_max=M_MAX, seed=1)
+        gmrf.trace_reset()
+        ms, (rc, info) = timed(lambda i: p.sample(x, nsamples=ns, tol=TOL, m_max=M_MAX, seed=20 + i), 2)
+        mld, ld = timed(lambda i: p.logdet(nprobes=64, tol=TOL, m_max=M_MAX, seed=30 + i), 2)
+        out["batched_512"] = {
+            "workload": "512x512 SPDE (same recipe, ell 64), mirror M, 256 samples per call; log det with 64 "
+                        "Rademacher probes per call",
+            "samples_per_s": ns * 1e3 / ms, "ms_per_call": ms,
+            "m_mean": float(np.mean([i.m_used for i in info])), "status": rc,
+            "logdets_per_s": 1e3 / mld, "logdet": ld[0], "logdet_std_err": ld[1],
+            "logdet_m_mean": float(np.mean([i.m_used for i in ld[3]]))}
+
+    # 3-D 256^3 Dirichlet 7-point, kappa^2 ~ U[0.01, 1], 16 samples
+    shape = (256, 256, 256)
+    n = 256 ** 3
+    k3 = torch.from_numpy(inputs.kappa2_uniform_field(shape, seed=KAPPA_SEED)).cuda()
+    with gmrf.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=k3, stream=stream.cuda_stream) as p:
+        ns = 16
+        x = torch.empty(ns * n, dtype=torch.float32, device="cuda")
+        p.sample(x, nsamples=ns, tol=TOL, m_max=400, seed=1)
+        gmrf.trace_reset()
+        gmrf.trace_timing(True)
+        ms, (rc, info) = timed(lambda i: p.sample(x, nsamples=ns, tol=TOL, m_max=400, seed=40 + i), 1)
+        gmrf.trace_timing(False)
+        st_ms, st_l, st_t = gmrf.trace_query("stencil_step")
+        avg_s = st_ms / max(st_t, 1) / 1e3
+        ach = 20.0 * n * ns / avg_s / 1e9   # 20 n bytes per vector per fused step
+        out["3d_256"] = {
+            "workload": "256^3 Dirichlet, Q = 7-point Laplacian + kappa^2 (i.i.d. U[0.01,1]), 16 samples, tol 1e-6",
+            "samples_per_s": ns * 1e3 / ms, "ms_per_call": ms,
+            "m_mean": float(np.mean([i.m_used for i in info])), "status": rc,
+            "stencil_step": {"avg_launch_us": avg_s * 1e6, "achieved_GBps": ach, "frac": ach / peak,
+                             "algorithmic_bytes_per_launch": 20 * n * ns}}
+    return out
 
 
 def run_reference(args):
@@ -346,6 +423,7 @@ def main():
     ap.add_argument("--precond", choices=["circulant", "mirror"], default="mirror")
     ap.add_argument("--check-every", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="headline workload only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -103,7 +103,7 @@ __device__ __forceinline__ void wfft_fwd(float2 (&v)[32], float2* sm, const floa
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
-      for (int k1 = 1; k1 < E; ++k1) v[g * E + k1] = mul2(v[g * E + k1], __ldg(tw + lane * k1 * tws));
+      for (int k1 = 1; k1 < E; ++k1) v[g * E + k1] = mul2(v[g * E + k1], tw[lane * k1 * tws]);
   }
   __syncwarp();
 #pragma unroll
@@ -123,7 +123,7 @@ __device__ __forceinline__ void wfft_inv(float2 (&v)[32], float2* sm, const floa
   reg_fft<32, true>(v);
   if (E > 1) {
 #pragma unroll
-    for (int l = 1; l < 32; ++l) v[l] = mulc2(v[l], __ldg(tw + l * k1 * tws));
+    for (int l = 1; l < 32; ++l) v[l] = mulc2(v[l], tw[l * k1 * tws]);
   }
   __syncwarp();
 #pragma unroll
@@ -146,6 +146,34 @@ __host__ __device__ constexpr int rows_per_block() {
 template <int KIND, int LOGL>
 __host__ __device__ constexpr int tile_pitch() {  // floats per tile row
   return KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 4 : 2 * (1 << LOGL) + 6;
+}
+
+// Copy `count` float2 from global memory to shared memory (all block threads).
+__device__ __forceinline__ void stage_table(float2* dst, const float2* __restrict__ src, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+__device__ __forceinline__ void stage_table(float* dst, const float* __restrict__ src, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+constexpr int kColWarps = 4;
+
+// Dynamic shared memory of the row kernel:
+//   tile[RB][TP] floats | per-warp scratch [WPC][32 * 33] float2 | twx[NX] | dctx[NX + 1] (MIRROR only)
+template <int KIND, int LOGL>
+__host__ __device__ constexpr size_t row_smem_bytes() {
+  return (size_t)rows_per_block<KIND, LOGL>() * tile_pitch<KIND, LOGL>() * sizeof(float) +
+         (size_t)(rows_per_block<KIND, LOGL>() / (32 / ((1 << LOGL) / 32))) * 32 * 33 * sizeof(float2) +
+         (size_t)(2 * (1 << LOGL) + (KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 1 : 0)) * sizeof(float2);
+}
+// Dynamic shared memory of the column kernel:
+//   per-warp scratch [kColWarps][32 * 33] float2 | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny] floats
+template <int KIND, int LOGL>
+__host__ __device__ constexpr size_t col_smem_bytes() {
+  return (size_t)kColWarps * 32 * 33 * sizeof(float2) +
+         (size_t)((KIND == GMRF_PREC_CIRCULANT ? (1 << LOGL) : 2 * (1 << LOGL)) +
+                  (KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 1 : 0)) * sizeof(float2) +
+         (size_t)(KIND == GMRF_PREC_CIRCULANT ? (1 << LOGL) : 2 * (1 << LOGL)) * sizeof(float);
 }
 
 template <int KIND>
@@ -246,27 +274,27 @@ __device__ __forceinline__ void post_pair(const float2* zl, int k, const float2*
       outc[L] = f2(xl, 0.f);
     } else {
       outr[0] = x0;
-      outr[L] = __ldg(&dct[L].x) * xl;
+      outr[L] = dct[L].x * xl;
     }
     return;
   }
   const float2 zc = conj2(zr);
-  const float2 d = mul2(__ldg(tw + k), sub2(zk, zc));
+  const float2 d = mul2(tw[k], sub2(zk, zc));
   const float2 Xk = f2(0.5f * (zk.x + zc.x + d.y), 0.5f * (zk.y + zc.y - d.x));
   if (KIND == GMRF_PREC_CIRCULANT) outc[k] = Xk;
   else {
-    outr[k] = mul2(__ldg(dct + k), Xk).x;
-    outr[N - k] = mulc2(__ldg(dct + N - k), Xk).x;
+    outr[k] = mul2(dct[k], Xk).x;
+    outr[N - k] = mulc2(dct[N - k], Xk).x;
   }
   if (2 * k == L) return;
   const int kp = L - k;
   const float2 zkc = conj2(zk);
-  const float2 d2 = mul2(__ldg(tw + kp), sub2(zr, zkc));
+  const float2 d2 = mul2(tw[kp], sub2(zr, zkc));
   const float2 Xp = f2(0.5f * (zr.x + zkc.x + d2.y), 0.5f * (zr.y + zkc.y - d2.x));
   if (KIND == GMRF_PREC_CIRCULANT) outc[kp] = Xp;
   else {
-    outr[kp] = mul2(__ldg(dct + kp), Xp).x;
-    outr[N - kp] = mulc2(__ldg(dct + N - kp), Xp).x;
+    outr[kp] = mul2(dct[kp], Xp).x;
+    outr[N - kp] = mulc2(dct[N - kp], Xp).x;
   }
 }
 
@@ -285,20 +313,20 @@ __device__ __forceinline__ void pre_pair(const float2* inc, const float* inr, in
   } else {
     const float ck = inr[k], cnk = k == 0 ? 0.f : inr[N - k];
     const float cp = inr[kp], cnp = inr[N - kp];
-    Vk = mulc2(f2(ck, -cnk), __ldg(dct + k));
-    Vp = mulc2(f2(cp, -cnp), __ldg(dct + kp));
+    Vk = mulc2(f2(ck, -cnk), dct[k]);
+    Vp = mulc2(f2(cp, -cnp), dct[kp]);
   }
   {
     const float2 c = conj2(Vp);
     const float2 E = scl2(add2(Vk, c), 0.5f);
-    const float2 O = mulc2(scl2(sub2(Vk, c), 0.5f), __ldg(tw + k));
+    const float2 O = mulc2(scl2(sub2(Vk, c), 0.5f), tw[k]);
     zl[k] = f2(E.x - O.y, E.y + O.x);
   }
   if (k == 0 || 2 * k == L) return;
   {
     const float2 c = conj2(Vk);
     const float2 E = scl2(add2(Vp, c), 0.5f);
-    const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), __ldg(tw + kp));
+    const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), tw[kp]);
     zl[kp] = f2(E.x - O.y, E.y + O.x);
   }
 }
@@ -368,13 +396,14 @@ __device__ __forceinline__ void tile_load_T(const Args& a, float* tile, const fl
 // forward real transform of the warp's G rows held as pairs p[g][E]; spectrum
 // rows written to the tile rows tr0 + g.
 template <int KIND, int LOGL>
-__device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[32], float2* sm, float* tile, int tr0) {
+__device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[32], float2* sm, float* tile, int tr0,
+                                             const float2* twx, const float2* dctx) {
   constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E, TP = tile_pitch<KIND, LOGL>();
   const int lane = threadIdx.x & 31;
   float2 v[32];
 #pragma unroll
   for (int g = 0; g < G; ++g) pack_row<KIND, E>(p + g * E, v + g * E);
-  wfft_fwd<LOGL>(v, sm, a.twx, 2);
+  wfft_fwd<LOGL>(v, sm, twx, 2);
   __syncwarp();
   {
     const int g = lane / E, k1 = lane % E;
@@ -386,13 +415,14 @@ __device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[32], flo
   for (int idx = lane; idx < G * NP; idx += 32) {
     const int g = idx / NP, k = idx - g * NP;
     float* trow = tile + (tr0 + g) * TP;
-    post_pair<KIND, L>(sm + g * L, k, a.twx, a.dctx, reinterpret_cast<float2*>(trow), trow);
+    post_pair<KIND, L>(sm + g * L, k, twx, dctx, reinterpret_cast<float2*>(trow), trow);
   }
 }
 
 // inverse real transform: tile rows tr0 + g -> pairs p[g][E] (times L).
 template <int KIND, int LOGL>
-__device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[32], float2* sm, const float* tile, int tr0) {
+__device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[32], float2* sm, const float* tile, int tr0,
+                                             const float2* twx, const float2* dctx) {
   constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E, TP = tile_pitch<KIND, LOGL>();
   const int lane = threadIdx.x & 31;
   constexpr int NP = L / 2 + 1;
@@ -400,7 +430,7 @@ __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[32], flo
   for (int idx = lane; idx < G * NP; idx += 32) {
     const int g = idx / NP, k = idx - g * NP;
     const float* trow = tile + (tr0 + g) * TP;
-    pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, k, a.twx, a.dctx, sm + g * L);
+    pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, k, twx, dctx, sm + g * L);
   }
   __syncwarp();
   float2 v[32];
@@ -409,7 +439,7 @@ __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[32], flo
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) v[k2] = sm[g * L + k1 + E * k2];
   }
-  wfft_inv<LOGL>(v, sm, a.twx, 2);
+  wfft_inv<LOGL>(v, sm, twx, 2);
 #pragma unroll
   for (int g = 0; g < G; ++g) unpack_row<KIND, E>(v + g * E, p + g * E);
 }
@@ -423,9 +453,12 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
   __shared__ Dots<float> red[8];
   __shared__ int s_int[4];
   __shared__ float s_flt[4];
+  constexpr int WPC = RB / G;
   float* tile = smf;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* sm = reinterpret_cast<float2*>(smf + RB * TP) + warp * (32 * 33);
+  float2* twx = reinterpret_cast<float2*>(smf + RB * TP) + WPC * (32 * 33);  // [NX] exp(-2 pi i t / NX)
+  float2* dctx = twx + NX;                                                    // [NX + 1] (MIRROR)
   const int s = blockIdx.y;
   const bool step = (MODE == R_FWD || MODE == R_LAST || MODE == R_MID || MODE == R_MIDW || MODE == R_MIDG) &&
                     a.in == nullptr;
@@ -434,6 +467,9 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
     if (a.st[s].status != VS_RUNNING) return;
     j = a.st[s].m;
   }
+  stage_table(twx, a.twx, NX);
+  if (KIND == GMRF_PREC_MIRROR) stage_table(dctx, a.dctx, NX + 1);
+  __syncthreads();
   const int y0 = blockIdx.x * RB;
   const int tr0 = warp * G;       // first tile row of this warp
   const size_t n = a.n;
@@ -472,7 +508,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
         store_row<KIND, E>(p + g * E, Vc + ro);
       }
     }
-    rows_forward<KIND, LOGL>(a, p, sm, tile, tr0);
+    rows_forward<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);
     __syncthreads();
     tile_store_T<KIND, LOGL>(a, tile, Tv, y0);
     return;
@@ -482,7 +518,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
   if (MODE != R_MIDG) {
     tile_load_T<KIND, LOGL>(a, tile, Tv, y0);
     __syncthreads();
-    rows_inverse<KIND, LOGL>(a, p, sm, tile, tr0);
+    rows_inverse<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);
   }
   if (MODE == R_INV) {
 #pragma unroll
@@ -580,7 +616,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
       }
     }
     __syncthreads();  // tile rows consumed by every warp before they are rewritten
-    rows_forward<KIND, LOGL>(a, p, sm, tile, tr0);
+    rows_forward<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);
     __syncthreads();
     tile_store_T<KIND, LOGL>(a, tile, Tv, y0);
     return;
@@ -629,22 +665,29 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
 }
 
 // ----------------------------------------------------------------- columns
-// symbol of B_bar^{-p/2} (times the transform normalisation)
-__device__ __forceinline__ float sym(const Args& a, int kx, int ky) {
-  const float lam = a.kbar2 + __ldg(a.lamx + kx) + __ldg(a.lamy + ky);
+// symbol of B_bar^{-p/2} (times the transform normalisation); cx = kappa_bar^2 + lambda_x
+__device__ __forceinline__ float sym(const Args& a, float cx, const float* lamy, int ky) {
+  const float lam = cx + lamy[ky];
   return (a.power == 2 ? 1.f / lam : rsqrtf(lam)) * a.dscale;
 }
-
-constexpr int kColWarps = 4;
 
 template <int KIND, int LOGL>
 __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
   constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E;
-  __shared__ float2 smw[kColWarps][32 * 33];
+  constexpr int NYc = KIND == GMRF_PREC_CIRCULANT ? L : 2 * L;  // ny
+  extern __shared__ __align__(16) float smf[];
   const int s = blockIdx.y;
   if (step_mode && a.st[s].status != VS_RUNNING) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* sm = smw[warp];
+  float2* sm = reinterpret_cast<float2*>(smf) + warp * (32 * 33);
+  // layout (must match col_smem_bytes): warp scratch | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny]
+  float2* twy = reinterpret_cast<float2*>(smf) + kColWarps * (32 * 33);
+  float2* dcty = twy + NYc;
+  float* lamy = reinterpret_cast<float*>(dcty + (KIND == GMRF_PREC_MIRROR ? NYc + 1 : 0));
+  stage_table(twy, a.twy, NYc);
+  if (KIND == GMRF_PREC_MIRROR) stage_table(dcty, a.dcty, NYc + 1);
+  stage_table(lamy, a.lamy, NYc);
+  __syncthreads();
   float* Tv = a.T + (size_t)s * a.tstride;
   const int line0 = (blockIdx.x * kColWarps + warp) * G;
   float2 v[32];
@@ -658,15 +701,16 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
 #pragma unroll
       for (int r = 0; r < E; ++r) v[g * E + r] = kx < ncl ? src[lane + 32 * r] : f2(0.f, 0.f);
     }
-    wfft_fwd<LOGL>(v, sm, a.twy, 1);
+    wfft_fwd<LOGL>(v, sm, twy, 1);
     {
       const int g = lane / E, k1 = lane % E, kx = line0 + g;
       if (kx < ncl) {
+        const float cx = a.kbar2 + __ldg(a.lamx + kx);
 #pragma unroll
-        for (int k2 = 0; k2 < 32; ++k2) v[k2] = scl2(v[k2], sym(a, kx, k1 + E * k2));
+        for (int k2 = 0; k2 < 32; ++k2) v[k2] = scl2(v[k2], sym(a, cx, lamy, k1 + E * k2));
       }
     }
-    wfft_inv<LOGL>(v, sm, a.twy, 1);
+    wfft_inv<LOGL>(v, sm, twy, 1);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int kx = line0 + g;
@@ -691,18 +735,25 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
   }
 #pragma unroll
   for (int g = 0; g < G; ++g) pack_row<KIND, E>(p + g * E, v + g * E);
-  wfft_fwd<LOGL>(v, sm, a.twy, 2);
+  wfft_fwd<LOGL>(v, sm, twy, 2);
   __syncwarp();
   {
     const int g = lane / E, k1 = lane % E;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) sm[g * L + k1 + E * k2] = v[k2];
   }
+  float cxl[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) cxl[g] = line0 + g < a.nx ? a.kbar2 + __ldg(a.lamx + line0 + g) : 1.f;
   __syncwarp();
   constexpr int NP = L / 2 + 1;
   for (int idx = lane; idx < G * NP; idx += 32) {
     const int g = idx / NP, k = idx - g * NP;
     const int kx = line0 + g;
+    float cx = cxl[0];
+#pragma unroll
+    for (int q = 1; q < G; ++q)
+      if (g == q) cx = cxl[q];
     float C[4] = {0.f, 0.f, 0.f, 0.f};
     int ci[4] = {0, 0, 0, 0};
     int nc = 0;
@@ -714,47 +765,47 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
       const float2 zr = zl[(L - k) & (L - 1)];
       if (k == 0) {
         ci[0] = 0; C[0] = zk.x + zk.y;
-        ci[1] = L; C[1] = __ldg(&a.dcty[L].x) * (zk.x - zk.y);
+        ci[1] = L; C[1] = dcty[L].x * (zk.x - zk.y);
         nc = 2;
       } else {
         const float2 zc = conj2(zr);
-        const float2 d = mul2(__ldg(a.twy + k), sub2(zk, zc));
+        const float2 d = mul2(twy[k], sub2(zk, zc));
         const float2 Xk = f2(0.5f * (zk.x + zc.x + d.y), 0.5f * (zk.y + zc.y - d.x));
-        ci[0] = k; C[0] = mul2(__ldg(a.dcty + k), Xk).x;
-        ci[1] = NY - k; C[1] = mulc2(__ldg(a.dcty + NY - k), Xk).x;
+        ci[0] = k; C[0] = mul2(dcty[k], Xk).x;
+        ci[1] = NY - k; C[1] = mulc2(dcty[NY - k], Xk).x;
         nc = 2;
         if (2 * k != L) {
           const int kp = L - k;
           const float2 zkc = conj2(zk);
-          const float2 d2 = mul2(__ldg(a.twy + kp), sub2(zr, zkc));
+          const float2 d2 = mul2(twy[kp], sub2(zr, zkc));
           const float2 Xp = f2(0.5f * (zr.x + zkc.x + d2.y), 0.5f * (zr.y + zkc.y - d2.x));
-          ci[2] = kp; C[2] = mul2(__ldg(a.dcty + kp), Xp).x;
-          ci[3] = NY - kp; C[3] = mulc2(__ldg(a.dcty + NY - kp), Xp).x;
+          ci[2] = kp; C[2] = mul2(dcty[kp], Xp).x;
+          ci[3] = NY - kp; C[3] = mulc2(dcty[NY - kp], Xp).x;
           nc = 4;
         }
       }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      if (i < nc) C[i] = live ? C[i] * sym(a, kx, ci[i]) : 0.f;
+      if (i < nc) C[i] = live ? C[i] * sym(a, cx, lamy, ci[i]) : 0.f;
     // inverse pre-processing of the same pair
     const int kp = L - k;
     float ck, cnk, cp, cnp;
     if (k == 0) { ck = C[0]; cnk = 0.f; cp = C[1]; cnp = C[1]; }
     else if (2 * k == L) { ck = C[0]; cnk = C[1]; cp = C[0]; cnp = C[1]; }
     else { ck = C[0]; cnk = C[1]; cp = C[2]; cnp = C[3]; }
-    const float2 Vk = mulc2(f2(ck, -cnk), __ldg(a.dcty + k));
-    const float2 Vp = mulc2(f2(cp, -cnp), __ldg(a.dcty + kp));
+    const float2 Vk = mulc2(f2(ck, -cnk), dcty[k]);
+    const float2 Vp = mulc2(f2(cp, -cnp), dcty[kp]);
     {
       const float2 c = conj2(Vp);
       const float2 Ev = scl2(add2(Vk, c), 0.5f);
-      const float2 O = mulc2(scl2(sub2(Vk, c), 0.5f), __ldg(a.twy + k));
+      const float2 O = mulc2(scl2(sub2(Vk, c), 0.5f), twy[k]);
       zl[k] = f2(Ev.x - O.y, Ev.y + O.x);
     }
     if (k != 0 && 2 * k != L) {
       const float2 c = conj2(Vk);
       const float2 Ev = scl2(add2(Vp, c), 0.5f);
-      const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), __ldg(a.twy + kp));
+      const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), twy[kp]);
       zl[kp] = f2(Ev.x - O.y, Ev.y + O.x);
     }
   }
@@ -764,7 +815,7 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) v[k2] = sm[g * L + k1 + E * k2];
   }
-  wfft_inv<LOGL>(v, sm, a.twy, 2);
+  wfft_inv<LOGL>(v, sm, twy, 2);
 #pragma unroll
   for (int g = 0; g < G; ++g) unpack_row<KIND, E>(v + g * E, p + g * E);
 #pragma unroll
@@ -784,7 +835,7 @@ cudaError_t row_launch_t(const Args& a, int nvec, cudaStream_t s, int kc) {
   constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E;
   constexpr int RB = rows_per_block<KIND, LOGL>(), TP = tile_pitch<KIND, LOGL>();
   constexpr int WPC = RB / G;
-  const size_t sm = (size_t)RB * TP * sizeof(float) + (size_t)WPC * 32 * 33 * sizeof(float2);
+  const size_t sm = row_smem_bytes<KIND, LOGL>();
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_row<KIND, LOGL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -815,9 +866,16 @@ cudaError_t col_launch_t(const Args& a, int nvec, int step_mode, cudaStream_t s,
   constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E;
   const int nlines = KIND == GMRF_PREC_CIRCULANT ? a.nx / 2 + 1 : a.nx;
   const int per = kColWarps * G;
+  const size_t sm = col_smem_bytes<KIND, LOGL>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_col<KIND, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   dim3 grd((nlines + per - 1) / per, nvec);
   trace_begin(kc, s);
-  k_col<KIND, LOGL><<<grd, 32 * kColWarps, 0, s>>>(a, step_mode);
+  k_col<KIND, LOGL><<<grd, 32 * kColWarps, sm, s>>>(a, step_mode);
   trace_end(kc, s);
   return cudaGetLastError();
 }
