@@ -180,7 +180,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    from paper_1312_1476_gb300 import _build, inputs
+    from paper_1312_1476_gb300 import _build, inputs, replicas
     if rank == 0 or world == 1:
         _build.build()
     if world > 1:
@@ -195,7 +195,7 @@ def run_ours(args):
                         stream=stream.cuda_stream)
     x = torch.empty(n, dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    seed0 = 1000 + 100000 * rank
+    seed0 = replicas.replica_seed(1000, rank)
 
     def step(i, out=None, z=None):
         rc, info = prob.sample(out if out is not None else x, nsamples=1, tol=TOL, m_max=M_MAX,
@@ -239,11 +239,8 @@ def run_ours(args):
     dev_ms, ms_used, errs, t_wall = timed_region(False)
     launches = gmrf.trace_query("all")[1]
     clk = clocks.stop()
-    t_max = dev_ms
+    t_max = replicas.max_over_ranks(dev_ms, dist if world > 1 else None, device="cuda")
     if world > 1:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
         dist.barrier()
     value = world * args.steps / (t_max / 1e3)
     # roofline: the same K steps again with CUDA events around every kernel
@@ -283,11 +280,8 @@ def run_ours(args):
         rc, _ = step(i, out=xh, z=zh)
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev), dist if world > 1 else None,
+                                     device="cuda")
 
     if rank == 0:
         out = {
@@ -387,7 +381,45 @@ def measure_variants(args, gmrf, torch, flush, peak):
             "m_mean": float(np.mean([i.m_used for i in info])), "status": rc,
             "stencil_step": {"avg_launch_us": avg_s * 1e6, "achieved_GBps": ach, "frac": ach / peak,
                              "algorithmic_bytes_per_launch": 20 * n * ns}}
+    out["serving"] = measure_serving()
     return out
+
+
+def measure_serving(nreq=32):
+    """Poisson request stream of the serving mix (2-D SPDE 128^2..1024^2 with
+    the mirror preconditioner, 3-D 7-point 64^3..128^3, tau ~ U[0.5, 5], 1-8
+    samples or a log det with 16-64 probes, tol 1e-6), served with continuous
+    admission at 0.5x and 1x the measured saturation rate, against one request
+    at a time in FP64 on the same stream."""
+    from paper_1312_1476_gb300 import serve
+
+    def stream(rate):
+        return serve.make_mix(nreq, rate=rate, seed=4, max_samples=8)
+
+    res = {}
+    srv = serve.Server(max_inflight=16)
+    burst = stream(1e6)
+    for r in burst:
+        r.arrival = 0.0
+    srv.prepare(burst)
+    srv.serve(burst[:4], realtime=False)
+    _, sat = srv.serve(burst, realtime=False)
+    sat_rate = nreq / sat["wall_s"]
+    res["saturation"] = dict(sat, rate_req_per_s=sat_rate)
+    for frac in (0.5, 1.0):
+        reqs = stream(frac * sat_rate)
+        srv.prepare(reqs)
+        _, met = srv.serve(reqs, realtime=True)
+        res["rate_%.1fx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
+    base = serve.Server(max_inflight=1, precision="fp64")
+    reqs = stream(0.5 * sat_rate)
+    base.prepare(reqs)
+    base.serve(reqs[:2], realtime=False)
+    _, met = base.serve(reqs, realtime=True)
+    res["fp64_one_at_a_time_rate_0.5x"] = dict(met, rate_req_per_s=0.5 * sat_rate)
+    res["workload"] = ("%d requests per run; samples and log dets of 2-D SPDE (mirror M) and 3-D 7-point GMRFs of "
+                       "mixed sizes; latency = completion - arrival" % nreq)
+    return res
 
 
 def run_reference(args):

@@ -40,7 +40,8 @@
  * code to a static string.  On GMRF_ERR_NOT_CONVERGED the sample is still
  * written (with the last subspace size) and each info record carries its own
  * status and error estimate.  A problem must not be used from two threads at
- * once.
+ * once; different problems may be used from different host threads
+ * concurrently, and their device work then overlaps.
  */
 #ifndef GMRF_H
 #define GMRF_H
@@ -176,7 +177,8 @@ int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t 
  *   recorded around every launch on its stream);  op 2: disable timing;
  *   op 3: query class kclass (-1 = all): *total_ms = summed kernel time,
  *   *launches = kernel launches, *timed = launches that were timed.
- * Process-wide, not thread-safe; any output pointer may be NULL. */
+ * Process-wide and thread-safe (counts and times of all threads are summed);
+ * any output pointer may be NULL. */
 int gmrf_trace(int32_t op, int32_t kclass, double* total_ms, int64_t* launches, int64_t* timed);
 
 /* Allocation-free y = M^{-1/2} v (the operation of gmrf_apply with which = 2).

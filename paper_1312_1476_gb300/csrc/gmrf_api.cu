@@ -32,22 +32,26 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
-int ensure(DevBuf& b, size_t bytes) {
+// Workspaces are stream-ordered allocations on the problem's work stream, so
+// growing or freeing them never synchronises the device (other problems keep
+// running concurrently).
+int ensure(DevBuf& b, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return GMRF_OK;
-  if (b.p) cudaFree(b.p);
+  if (b.p) cudaFreeAsync(b.p, s);
   b.p = nullptr;
   b.bytes = 0;
-  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+  if (cudaMallocAsync(&b.p, bytes, s) != cudaSuccess) {
     cudaGetLastError();
+    b.p = nullptr;
     return GMRF_ERR_OOM;
   }
   b.bytes = bytes;
   return GMRF_OK;
 }
 
-void release(DevBuf& b) {
-  if (b.p) cudaFree(b.p);
+void release(DevBuf& b, cudaStream_t s) {
+  if (b.p) cudaFreeAsync(b.p, s);
   b.p = nullptr;
   b.bytes = 0;
 }
@@ -136,38 +140,33 @@ int leave(gmrf_problem* p) {
 
 int ensure_host_states(gmrf_problem* p, int nvec) {
   if (p->st_host_cap >= nvec) return GMRF_OK;
-  if (p->st_host) cudaFreeHost(p->st_host);
-  p->st_host = nullptr;
-  p->st_host_cap = 0;
-  if (cudaMallocHost(&p->st_host, sizeof(VecState) * nvec) != cudaSuccess) {
-    cudaGetLastError();
-    return GMRF_ERR_OOM;
-  }
-  p->st_host_cap = nvec;
-  return GMRF_OK;
+  delete[] p->st_host;
+  p->st_host = new (std::nothrow) VecState[nvec];
+  p->st_host_cap = p->st_host ? nvec : 0;
+  return p->st_host ? GMRF_OK : GMRF_ERR_OOM;
 }
 
 // Buffers for a batch of nvec vectors with nslots stored basis vectors each.
 int ensure_lanczos(gmrf_problem* p, int nvec, int nslots, int m_max, bool need_tm, LanczosBufs& b) {
   const size_t n = p->g.n, es = esize(p);
-  CKR(ensure(p->W0, (size_t)nvec * n * es));
-  CKR(ensure(p->W1, (size_t)nvec * n * es));
-  CKR(ensure(p->V, (size_t)nvec * nslots * n * es));
-  CKR(ensure(p->st, sizeof(VecState) * nvec));
-  CKR(ensure(p->alpha, sizeof(double) * nvec * m_max));
-  CKR(ensure(p->beta, sizeof(double) * nvec * m_max));
-  CKR(ensure(p->alpha_f, sizeof(float) * nvec * m_max));
-  CKR(ensure(p->beta2_f, sizeof(float) * nvec * m_max));
+  CKR(ensure(p->W0, (size_t)nvec * n * es, p->ws));
+  CKR(ensure(p->W1, (size_t)nvec * n * es, p->ws));
+  CKR(ensure(p->V, (size_t)nvec * nslots * n * es, p->ws));
+  CKR(ensure(p->st, sizeof(VecState) * nvec, p->ws));
+  CKR(ensure(p->alpha, sizeof(double) * nvec * m_max, p->ws));
+  CKR(ensure(p->beta, sizeof(double) * nvec * m_max, p->ws));
+  CKR(ensure(p->alpha_f, sizeof(float) * nvec * m_max, p->ws));
+  CKR(ensure(p->beta2_f, sizeof(float) * nvec * m_max, p->ws));
   int nblk = std::max(stencil_blocks_per_vector(p->g), 256);
   nblk = std::max(nblk, precond_blocks_per_vector(p->pre));
-  CKR(ensure(p->partials, (size_t)nvec * nblk * sizeof(Dots<double>)));
+  CKR(ensure(p->partials, (size_t)nvec * nblk * sizeof(Dots<double>), p->ws));
   const bool fresh_counters = p->counters.bytes < sizeof(unsigned) * nvec;
-  CKR(ensure(p->counters, sizeof(unsigned) * nvec));
+  CKR(ensure(p->counters, sizeof(unsigned) * nvec, p->ws));
   if (fresh_counters) CK(cudaMemsetAsync(p->counters.p, 0, sizeof(unsigned) * nvec, p->ws));
-  CKR(ensure(p->nodes, sizeof(TmNodes) * nvec));
-  CKR(ensure(p->y, sizeof(double) * nvec * m_max));
-  CKR(ensure(p->q, sizeof(double) * nvec));
-  if (need_tm) CKR(ensure(p->scratch, sizeof(double) * 2 * (size_t)nvec * m_max * kMaxNodes));
+  CKR(ensure(p->nodes, sizeof(TmNodes) * nvec, p->ws));
+  CKR(ensure(p->y, sizeof(double) * nvec * m_max, p->ws));
+  CKR(ensure(p->q, sizeof(double) * nvec, p->ws));
+  if (need_tm) CKR(ensure(p->scratch, sizeof(double) * 2 * (size_t)nvec * m_max * kMaxNodes, p->ws));
   CKR(ensure_host_states(p, nvec));
   b.W[0] = p->W0.p;
   b.W[1] = p->W1.p;
@@ -282,7 +281,7 @@ int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, in
   P.tol = tol;
   P.bd_tol = p->fp64 ? 1e-13 : 1e-6;
   const int c = std::min(check_every > 0 ? check_every : 16, m_max);
-  if (p->precond != GMRF_PREC_NONE) CKR(precond_prepare(p->pre, b.nvec));
+  if (p->precond != GMRF_PREC_NONE) CKR(precond_prepare(p->pre, b.nvec, s));
   CKR(capture_steps(p, b, P, c));
   StepGraph& G = p->graph;
   int j = 0;
@@ -382,6 +381,23 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
     gmrf_destroy(p);
     return code;
   };
+  {
+    // keep freed workspace in this process's default memory pool (no trim at
+    // every synchronisation), once per device
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+      std::lock_guard<std::mutex> lock(mu);
+      cudaMemPool_t pool;
+      if (!done[dev] && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        done[dev] = true;
+      }
+    }
+    cudaGetLastError();
+  }
   if (cudaStreamCreateWithFlags(&p->ws, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess) {
@@ -391,19 +407,19 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
   if (enter(p) != GMRF_OK) return fail(GMRF_ERR_CUDA);
   double sum_log = 0.0, nzero = 0.0;
   if (d->kappa2) {
-    if (ensure(p->kappa2, sizeof(float) * p->g.n) != GMRF_OK) return fail(GMRF_ERR_OOM);
+    if (ensure(p->kappa2, sizeof(float) * p->g.n, p->ws) != GMRF_OK) return fail(GMRF_ERR_OOM);
     const cudaMemcpyKind kind = is_device_ptr(d->kappa2) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (cudaMemcpyAsync(p->kappa2.p, d->kappa2, sizeof(float) * p->g.n, kind, p->ws) != cudaSuccess)
       return fail(GMRF_ERR_CUDA);
     DevBuf stats;
-    if (ensure(stats, 4 * sizeof(double)) != GMRF_OK) return fail(GMRF_ERR_OOM);
+    if (ensure(stats, kFieldStatsBytes, p->ws) != GMRF_OK) return fail(GMRF_ERR_OOM);
     double h[4] = {0, 0, 0, 0};
-    trace_begin(KC_OTHER, p->ws);
+    trace_begin(KC_OTHER, p->ws, 2);
     bool ok = launch_field_stats((const float*)p->kappa2.p, p->g.n, (double*)stats.p, p->ws) == cudaSuccess;
     trace_end(KC_OTHER, p->ws);
     ok = ok && cudaMemcpyAsync(h, stats.p, sizeof(h), cudaMemcpyDeviceToHost, p->ws) == cudaSuccess &&
          cudaStreamSynchronize(p->ws) == cudaSuccess;
-    release(stats);
+    release(stats, p->ws);
     if (!ok) return fail(GMRF_ERR_CUDA);
     if (h[0] > 0.5) return fail(GMRF_ERR_INVALID);
     nzero = h[1];
@@ -439,9 +455,10 @@ void gmrf_destroy(gmrf_problem* p) {
   DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,
                     &p->partials, &p->counters, &p->y, &p->scratch, &p->nodes, &p->q, &p->out2, &p->stage,
                     &p->stage2, &p->work};
-  for (DevBuf* b : bufs) release(*b);
-  precond_free(p->pre);
-  if (p->st_host) cudaFreeHost(p->st_host);
+  for (DevBuf* b : bufs) release(*b, p->ws);
+  precond_free(p->pre, p->ws);
+  if (p->ws) cudaStreamSynchronize(p->ws);
+  delete[] p->st_host;
   if (p->ev_in) cudaEventDestroy(p->ev_in);
   if (p->ev_out) cudaEventDestroy(p->ev_out);
   if (p->ws) cudaStreamDestroy(p->ws);
@@ -481,7 +498,7 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
     }));
     void* xdst = (char*)x_out + (size_t)s0 * n * es;
     if (!x_dev) {
-      CKR(ensure(p->stage, (size_t)c * n * es));
+      CKR(ensure(p->stage, (size_t)c * n * es, p->ws));
       xdst = p->stage.p;
     }
     if (p->precond == GMRF_PREC_NONE) {
@@ -490,7 +507,7 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
       }));
     } else {
       // u = ||z|| V_m y, then x = M^{-1/2} u = tau^{-1/2} B_bar^{-p/2} u (Proposition 1)
-      CKR(ensure(p->work, (size_t)c * n * es));
+      CKR(ensure(p->work, (size_t)c * n * es, p->ws));
       CK(traced(KC_ASSEMBLE, s, 1,
                 [&] { return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
       CK(traced(KC_PRE_APPLY, s, 3,
@@ -523,7 +540,7 @@ int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, doub
   if (chunk < 1) return GMRF_ERR_OOM;
   cudaStream_t s = p->ws;
   CKR(enter(p));
-  CKR(ensure(p->stage2, sizeof(double) * (o->nprobes + 2)));
+  CKR(ensure(p->stage2, sizeof(double) * (o->nprobes + 2), p->ws));
   double* qall = (double*)p->stage2.p;
   std::vector<VecState> all((size_t)o->nprobes);
   for (int s0 = 0; s0 < o->nprobes; s0 += chunk) {
@@ -568,12 +585,12 @@ int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void
   const void* vin = v;
   void* yout = y;
   if (!vd) {
-    CKR(ensure(p->stage, bytes));
+    CKR(ensure(p->stage, bytes, p->ws));
     CK(cudaMemcpyAsync(p->stage.p, v, bytes, cudaMemcpyHostToDevice, s));
     vin = p->stage.p;
   }
   if (!yd) {
-    CKR(ensure(p->stage2, bytes));
+    CKR(ensure(p->stage2, bytes, p->ws));
     yout = p->stage2.p;
   }
   if (which == 0) {
@@ -611,18 +628,21 @@ int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t 
     return GMRF_OK;
   }
   void* d = nullptr;
-  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+  if (cudaMallocAsync(&d, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     return GMRF_ERR_OOM;
   }
   int rc = GMRF_OK;
   if (launch_rng(kind, fp64, nvec, n, seed, 0, d, s) != cudaSuccess ||
-      cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
     cudaGetLastError();
     rc = GMRF_ERR_CUDA;
   }
-  cudaFree(d);
+  cudaFreeAsync(d, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    rc = GMRF_ERR_CUDA;
+  }
   return rc;
 }
 

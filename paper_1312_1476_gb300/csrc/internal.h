@@ -53,6 +53,8 @@ cudaError_t launch_stencil_apply(const Grid& g, bool fp64, const void* kappa2, d
 cudaError_t launch_rng(int kind, bool fp64, int64_t nvec, int64_t n, uint64_t seed, int64_t soff, void* out,
                        cudaStream_t s);
 // out4[0] = #(kappa2 < 0 or not finite), [1] = #zeros, [2] = sum log kappa2 over positives.
+// out4 must have kFieldStatsBytes of device memory (results + per-block parts).
+constexpr size_t kFieldStatsBytes = 4 * sizeof(double) + 256 * sizeof(Dots<float>);
 cudaError_t launch_field_stats(const float* k, size_t n, double* out4, cudaStream_t s);
 // ||z|| of each vector of W[0] into st[].znorm, and resets the state.
 cudaError_t launch_lanczos_init(bool fp64, size_t n, const LanczosBufs& b, cudaStream_t s);

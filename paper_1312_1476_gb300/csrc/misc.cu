@@ -178,25 +178,35 @@ __global__ void k_scale(T* x, size_t count, T a) {
 
 // Coefficient-field checks and mean log: counts of negative / non-finite
 // entries and of zeros, and sum of log kappa^2 over the positive entries
-// (compensated FP32).  One block, fixed summation order.
-__global__ void k_field_stats(const float* k, size_t n, double* out4) {
+// (compensated FP32).  Each block reduces a contiguous chunk into part[b];
+// k_field_final sums the parts in a fixed order.
+constexpr int kFieldBlocks = 256;
+__global__ void k_field_stats(const float* k, size_t n, Dots<float>* part) {
   __shared__ Dots<float> red[8];
   Dots<float> d;  // s1 = sum log, s2 = #bad, s3 = #zero (as compensated sums)
   d.zero();
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  const size_t per = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = per * blockIdx.x, hi = min(n, lo + per);
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const float v = k[i];
     if (!(v >= 0.f) || !isfinite(v)) d.s2 = df_add(d.s2, df{1.f, 0.f});
     else if (v == 0.f) d.s3 = df_add(d.s3, df{1.f, 0.f});
     else d.s1 = df_add(d.s1, df{logf(v), 0.f});
   }
   d = block_reduce(d, red);
-  if (threadIdx.x == 0) {
-    double a, b, c;
-    d.get(a, b, c);
-    out4[0] = b;
-    out4[1] = c;
-    out4[2] = a;
-  }
+  if (threadIdx.x == 0) part[blockIdx.x] = d;
+}
+__global__ void k_field_final(const Dots<float>* part, int np, double* out4) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Dots<float> d;
+  d.zero();
+  for (int b = 0; b < np; ++b) d.merge(part[b]);
+  double a, b2, c;
+  d.get(a, b2, c);
+  out4[0] = b2;
+  out4[1] = c;
+  out4[2] = a;
+  out4[3] = 0.0;
 }
 
 int grid_for(size_t work, int threads) {
@@ -227,9 +237,9 @@ cudaError_t launch_rng(int kind, bool fp64, int64_t nvec, int64_t n, uint64_t se
 }
 
 cudaError_t launch_field_stats(const float* k, size_t n, double* out4, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(out4, 0, 4 * sizeof(double), s);
-  if (e != cudaSuccess) return e;
-  k_field_stats<<<1, 256, 0, s>>>(k, n, out4);
+  Dots<float>* part = reinterpret_cast<Dots<float>*>(out4 + 4);
+  k_field_stats<<<kFieldBlocks, 256, 0, s>>>(k, n, part);
+  k_field_final<<<1, 32, 0, s>>>(part, kFieldBlocks, out4);
   return cudaGetLastError();
 }
 

@@ -562,31 +562,31 @@ size_t col_smem(const PrecondTables& t, int cw) {
   return (size_t)3 * cw * (t.ny + 2) * sizeof(R);
 }
 
-int ensure_ws(PrecondTables& t, int nvec) {
+int ensure_ws(PrecondTables& t, int nvec, cudaStream_t st) {
   const size_t es = t.fp64 ? 8 : 4;
   const size_t sb = (size_t)nvec * t.ny * (t.nx + 2) * es;
   const size_t gb = t.power == 2 ? (size_t)nvec * t.nx * t.ny * es : 16;
   if (t.S_bytes < sb) {
-    if (t.S) cudaFree(t.S);
+    if (t.S) cudaFreeAsync(t.S, st);
     t.S = nullptr;
     t.S_bytes = 0;
-    if (cudaMalloc(&t.S, sb) != cudaSuccess) return -1;
+    if (cudaMallocAsync(&t.S, sb, st) != cudaSuccess) return -1;
     t.S_bytes = sb;
   }
   if (t.G_bytes < gb) {
-    if (t.G) cudaFree(t.G);
+    if (t.G) cudaFreeAsync(t.G, st);
     t.G = nullptr;
     t.G_bytes = 0;
-    if (cudaMalloc(&t.G, gb) != cudaSuccess) return -1;
+    if (cudaMallocAsync(&t.G, gb, st) != cudaSuccess) return -1;
     t.G_bytes = gb;
   }
   const bool edges = t.kind == GMRF_PREC_CIRCULANT ? t.bc != GMRF_BC_PERIODIC : t.bc != GMRF_BC_NEUMANN;
   const size_t wb = (t.fast && edges) ? (size_t)nvec * t.nx * t.ny * es : 16;
   if (t.Wg_bytes < wb) {
-    if (t.Wg) cudaFree(t.Wg);
+    if (t.Wg) cudaFreeAsync(t.Wg, st);
     t.Wg = nullptr;
     t.Wg_bytes = 0;
-    if (cudaMalloc(&t.Wg, wb) != cudaSuccess) return -1;
+    if (cudaMallocAsync(&t.Wg, wb, st) != cudaSuccess) return -1;
     t.Wg_bytes = wb;
   }
   return 0;
@@ -688,7 +688,7 @@ cudaError_t col_launch(const PrecondTables& t, PArgs<R> a, int nvec, int step_mo
 template <typename R, int KIND>
 cudaError_t run_step(PrecondTables& t, const Grid& g, const void* kappa2, double kc, const LanczosBufs& b,
                      const StepParams& P, cudaStream_t s) {
-  if (ensure_ws(t, b.nvec)) return cudaErrorMemoryAllocation;
+  if (ensure_ws(t, b.nvec, s)) return cudaErrorMemoryAllocation;
   if (t.fast) {
     fast::Args a = fast_args(t, g, kappa2, kc);
     a.W0 = (float*)b.W[0];
@@ -732,7 +732,7 @@ cudaError_t run_step(PrecondTables& t, const Grid& g, const void* kappa2, double
 template <typename R, int KIND>
 cudaError_t run_apply(PrecondTables& t, const Grid& g, const void* in, void* out, int nvec, cudaStream_t s,
                       void* Sbuf = nullptr) {
-  if (!Sbuf && ensure_ws(t, nvec)) return cudaErrorMemoryAllocation;
+  if (!Sbuf && ensure_ws(t, nvec, s)) return cudaErrorMemoryAllocation;
   void* S = Sbuf ? Sbuf : t.S;
   if (t.fast) {
     fast::Args a = fast_args(t, g, nullptr, 0.0);
@@ -754,7 +754,7 @@ cudaError_t run_apply(PrecondTables& t, const Grid& g, const void* in, void* out
 template <typename R, int KIND>
 cudaError_t run_operator(PrecondTables& t, const Grid& g, const void* kappa2, double kc, const void* v, void* y,
                          int nvec, cudaStream_t s) {
-  if (ensure_ws(t, nvec)) return cudaErrorMemoryAllocation;
+  if (ensure_ws(t, nvec, s)) return cudaErrorMemoryAllocation;
   if (t.fast) {
     fast::Args a = fast_args(t, g, kappa2, kc);
     a.in = (const float*)v;
@@ -800,7 +800,7 @@ int upload_tables(PrecondTables& t, cudaStream_t s, std::vector<double>& lx64, s
   lam(t.nx, lx64);
   lam(t.ny, ly64);
   auto up = [&](void** dst, const void* src, size_t bytes) -> int {
-    if (cudaMalloc(dst, bytes) != cudaSuccess) return -1;
+    if (cudaMallocAsync(dst, bytes, s) != cudaSuccess) return -1;
     if (cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return -1;
     return 0;
   };
@@ -864,9 +864,9 @@ int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar
   double *dlx = nullptr, *dly = nullptr, *part = nullptr;
   const int np = 256;
   double h = 0.0;
-  bool ok = cudaMalloc(&dlx, sizeof(double) * t.nx) == cudaSuccess &&
-            cudaMalloc(&dly, sizeof(double) * t.ny) == cudaSuccess &&
-            cudaMalloc(&part, sizeof(double) * (np + 1)) == cudaSuccess &&
+  bool ok = cudaMallocAsync(&dlx, sizeof(double) * t.nx, s) == cudaSuccess &&
+            cudaMallocAsync(&dly, sizeof(double) * t.ny, s) == cudaSuccess &&
+            cudaMallocAsync(&part, sizeof(double) * (np + 1), s) == cudaSuccess &&
             cudaMemcpyAsync(dlx, lx64.data(), sizeof(double) * t.nx, cudaMemcpyHostToDevice, s) == cudaSuccess &&
             cudaMemcpyAsync(dly, ly64.data(), sizeof(double) * t.ny, cudaMemcpyHostToDevice, s) == cudaSuccess;
   if (ok) {
@@ -876,9 +876,9 @@ int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar
          cudaMemcpyAsync(&h, part + np, sizeof(double), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
          cudaStreamSynchronize(s) == cudaSuccess;
   }
-  if (dlx) cudaFree(dlx);
-  if (dly) cudaFree(dly);
-  if (part) cudaFree(part);
+  if (dlx) cudaFreeAsync(dlx, s);
+  if (dly) cudaFreeAsync(dly, s);
+  if (part) cudaFreeAsync(part, s);
   if (!ok) {
     cudaGetLastError();
     return GMRF_ERR_CUDA;
@@ -887,10 +887,10 @@ int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar
   return GMRF_OK;
 }
 
-void precond_free(PrecondTables& t) {
+void precond_free(PrecondTables& t, cudaStream_t s) {
   void* ps[] = {t.lamx, t.lamy, t.twx, t.twy, t.dctx, t.dcty, t.S, t.G, t.Wg};
   for (void* p : ps)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
   t = PrecondTables();
 }
 
@@ -901,8 +901,8 @@ int precond_blocks_per_vector(const PrecondTables& t) {
   return nb;
 }
 
-int precond_prepare(PrecondTables& t, int nvec) {
-  if (ensure_ws(t, nvec)) return GMRF_ERR_OOM;
+int precond_prepare(PrecondTables& t, int nvec, cudaStream_t s) {
+  if (ensure_ws(t, nvec, s)) return GMRF_ERR_OOM;
   cudaError_t e;
   if (t.fp64) e = t.kind == GMRF_PREC_CIRCULANT ? set_attrs<double, GMRF_PREC_CIRCULANT>()
                                                : set_attrs<double, GMRF_PREC_MIRROR>();

@@ -43,11 +43,11 @@ struct PrecondTables {
 bool precond_size_ok(int64_t n);
 int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar2, bool fp64, cudaStream_t s,
                   double* logdet_M);
-void precond_free(PrecondTables& t);
+void precond_free(PrecondTables& t, cudaStream_t s);
 int precond_blocks_per_vector(const PrecondTables& t);
 // Workspace for nvec vectors and kernel attributes; call before capturing
 // the preconditioned steps into a CUDA graph.
-int precond_prepare(PrecondTables& t, int nvec);
+int precond_prepare(PrecondTables& t, int nvec, cudaStream_t s);
 size_t precond_extra_bytes(const PrecondTables& t, size_t es);
 // Fused preconditioned Lanczos step j (A = M^{-1/2} Q M^{-1/2}, applied as
 // C^T C with C = I + R B_bar^{-1} for the squared operator and as

@@ -1,6 +1,7 @@
 // trace.cu -- see trace.h.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <vector>
 
 #include "../../include/gmrf.h"
@@ -21,7 +22,6 @@ struct Registry {
   double ms[KC_COUNT] = {};
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
-  Pending open = {-1, nullptr, nullptr};
 };
 
 Registry& reg() {
@@ -29,8 +29,12 @@ Registry& reg() {
   return r;
 }
 
-GraphTrace* g_sink = nullptr;
-int g_open_kc = -1;
+// Per host thread: the graph being captured by this thread (captures are
+// thread-local), and the class of the launch between trace_begin/trace_end.
+thread_local GraphTrace* g_sink = nullptr;
+thread_local int g_open_kc = -1;
+thread_local Pending t_open = {-1, nullptr, nullptr};
+std::mutex g_mu;  // guards the registry
 
 cudaEvent_t take() {
   Registry& r = reg();
@@ -51,6 +55,7 @@ cudaEvent_t take() {
 
 void trace_begin(int kc, cudaStream_t s, int nkernels) {
   Registry& r = reg();
+  std::lock_guard<std::mutex> lock(g_mu);
   if (g_sink) {
     g_sink->launches[kc] += nkernels;
     g_open_kc = -1;
@@ -71,14 +76,15 @@ void trace_begin(int kc, cudaStream_t s, int nkernels) {
   }
   r.launches[kc] += nkernels;
   if (!r.timing) return;
-  r.open.kc = kc;
-  r.open.a = take();
-  r.open.b = take();
-  if (r.open.a) cudaEventRecord(r.open.a, s);
+  t_open.kc = kc;
+  t_open.a = take();
+  t_open.b = take();
+  if (t_open.a) cudaEventRecord(t_open.a, s);
 }
 
 void trace_end(int kc, cudaStream_t s) {
   Registry& r = reg();
+  std::lock_guard<std::mutex> lock(g_mu);
   if (g_sink) {
     if (g_open_kc == kc) {
       const int i = g_sink->npairs;
@@ -88,18 +94,17 @@ void trace_end(int kc, cudaStream_t s) {
     g_open_kc = -1;
     return;
   }
-  if (!r.timing || r.open.kc != kc) return;
-  if (r.open.a && r.open.b) {
-    cudaEventRecord(r.open.b, s);
-    r.pending.push_back(r.open);
+  if (!r.timing || t_open.kc != kc) return;
+  if (t_open.a && t_open.b) {
+    cudaEventRecord(t_open.b, s);
+    r.pending.push_back(t_open);
   }
-  r.open.kc = -1;
-  // keep the number of outstanding pairs bounded
-  if (r.pending.size() > 8192) trace_collect();
+  t_open.kc = -1;
 }
 
 void trace_collect() {
   Registry& r = reg();
+  std::lock_guard<std::mutex> lock(g_mu);
   for (Pending& p : r.pending) {
     if (cudaEventSynchronize(p.b) == cudaSuccess) {
       float t = 0.f;
@@ -115,7 +120,10 @@ void trace_collect() {
   r.pending.clear();
 }
 
-bool trace_timing_enabled() { return reg().timing; }
+bool trace_timing_enabled() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  return reg().timing;
+}
 
 void GraphTrace::release() {
   for (int i = 0; i < npairs; ++i) {
@@ -128,6 +136,7 @@ void GraphTrace::release() {
 
 void trace_capture_begin(GraphTrace* g) {
   g->release();
+  std::lock_guard<std::mutex> lock(g_mu);
   g->timed = reg().timing;
   g_sink = g;
   g_open_kc = -1;
@@ -140,6 +149,7 @@ void trace_capture_end() {
 
 void trace_replayed(const GraphTrace* g, int useful_pairs) {
   Registry& r = reg();
+  std::lock_guard<std::mutex> lock(g_mu);
   for (int k = 0; k < KC_COUNT; ++k) r.launches[k] += g->launches[k];
   if (!r.timing || !g->timed) return;
   const int np = useful_pairs < g->npairs ? useful_pairs : g->npairs;
@@ -160,24 +170,31 @@ extern "C" int gmrf_trace(int32_t op, int32_t kclass, double* total_ms, int64_t*
   using namespace gmrf;
   Registry& r = reg();
   switch (op) {
-    case 0:
+    case 0: {
       trace_collect();
+      std::lock_guard<std::mutex> lock(g_mu);
       for (int k = 0; k < KC_COUNT; ++k) {
         r.launches[k] = 0;
         r.timed[k] = 0;
         r.ms[k] = 0.0;
       }
       return GMRF_OK;
-    case 1:
+    }
+    case 1: {
+      std::lock_guard<std::mutex> lock(g_mu);
       r.timing = true;
       return GMRF_OK;
-    case 2:
+    }
+    case 2: {
       trace_collect();
+      std::lock_guard<std::mutex> lock(g_mu);
       r.timing = false;
       return GMRF_OK;
+    }
     case 3: {
       if (kclass < -1 || kclass >= KC_COUNT) return GMRF_ERR_INVALID;
       trace_collect();
+      std::lock_guard<std::mutex> lock(g_mu);
       double ms = 0.0;
       int64_t l = 0, t = 0;
       for (int k = 0; k < KC_COUNT; ++k) {

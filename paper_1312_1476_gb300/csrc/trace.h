@@ -4,7 +4,9 @@
 // Launch counts are always kept.  When event timing is enabled
 // (gmrf_trace(1, ...)), a pair of events is recorded around the launch on
 // its own stream and the elapsed times are accumulated at the next host
-// synchronisation point (trace_collect).  Host-side, single-threaded use.
+// synchronisation point (trace_collect).  Thread-safe: the registry is
+// guarded by a mutex and a graph capture only sees launches of the thread
+// that captures.
 #pragma once
 
 #include <cuda_runtime.h>

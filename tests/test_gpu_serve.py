@@ -1,0 +1,55 @@
+"""GPU tests of the serving layer: a request gives the same result alone and
+in a concurrent mix, and admission keeps the in-flight memory estimate inside
+the budget."""
+import numpy as np
+import pytest
+
+from paper_1312_1476_gb300 import serve
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _mix():
+    reqs = serve.make_mix(12, rate=1e6, seed=9, sizes2d=(128, 256), sizes3d=(32, 48), nfields=2,
+                          max_samples=6, probes=(4, 8), p_logdet=0.3)
+    for r in reqs:
+        r.arrival = 0.0
+    return reqs
+
+
+def test_alone_equals_mix():
+    torch.cuda.synchronize()
+    srv = serve.Server(max_inflight=8)
+    reqs = _mix()
+    mixed, metrics = srv.serve(reqs, realtime=False)
+    assert metrics["requests"] == len(reqs)
+    assert all(r.status in (0, -3) for r in mixed)
+    for target in (0, 5, 11):
+        alone, _ = serve.Server(max_inflight=1).serve([reqs[target]], realtime=False)
+        a, b = alone[0], mixed[target]
+        if a.kind == "sample":
+            assert torch.equal(a.x, b.x)
+        else:
+            assert a.logdet == b.logdet and a.std_err == b.std_err
+        assert a.m_used == b.m_used
+
+
+def test_admission_respects_budget():
+    reqs = _mix()
+    probe = serve.Server(max_inflight=8)
+    budget = 3 * max(probe.need(r) for r in reqs)
+    srv = serve.Server(mem_budget=budget, max_inflight=8)
+    peak = [0]
+    orig = srv._run
+
+    def run(req, t0):
+        peak[0] = max(peak[0], srv.used)
+        return orig(req, t0)
+
+    srv._run = run
+    out, metrics = srv.serve(reqs, realtime=False)
+    assert len(out) == len(reqs)
+    assert peak[0] <= budget
+    assert metrics["p99_ms"] >= metrics["p50_ms"] > 0
