@@ -17,8 +17,9 @@
 //   shifted:  B v = kappa^2 v + L v            (5-point 2-D, 7-point 3-D)
 //   squared:  Q v = B (B v)                    (13-point 2-D, two passes in smem)
 // 2-D: 32x16 tiles with a halo of 1 (shifted) or 2 (squared) in shared memory.
-// 3-D: 32x16 tiles in x-y marching over a chunk of z planes; the centre
-// column is kept in registers, the plane with its x-y halo in shared memory.
+// 3-D: 32x8 tiles in x-y marching over a chunk of z planes with the inputs of
+// later planes prefetched; the centre column is kept in registers, the plane
+// with its x-y halo in a double-buffered shared tile.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -185,12 +186,59 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
     finish_step<T>(a.P, j, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
 }
 
-// 3-D shifted Laplacian (7-point), z-march over a chunk of planes.
-template <typename T, int BC, bool STEP>
-__global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
-  constexpr int PW = TX + 2, PH = TY + 2;
-  __shared__ T ps[PH * PW];
-  __shared__ Dots<T> red[NT / 32];
+// 3-D shifted Laplacian (7-point), z-march over a chunk of planes, software
+// pipelined: the raw inputs (q_{j-1}, v_{j-1}, kappa^2) of a thread's own
+// cells are loaded two planes ahead and those of the x-y halo ring one plane
+// ahead, so the loads of later planes are in flight while a plane is
+// computed; the plane with its halo lives in a double-buffered shared tile
+// (one barrier per plane).  Each thread owns VX adjacent cells along x
+// (vector loads), the block a (32 VX) x 8 tile.
+constexpr int TY3 = 8;
+constexpr int NT3 = TX * TY3;
+
+template <typename T, int VX>
+struct Raw {
+  T w[VX], vp[VX];
+  float k[VX];
+};
+
+template <typename T, int VX>
+__device__ __forceinline__ void vload(const T* p, T* o) {
+  if (VX == 1) o[0] = p[0];
+  else if (VX == 2 && sizeof(T) == 4) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  } else if (VX == 4 && sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else if (VX == 2 && sizeof(T) == 8) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < VX; ++e) o[e] = p[e];
+  }
+}
+template <typename T, int VX>
+__device__ __forceinline__ void vstore(T* p, const T* o) {
+  if (VX == 1) p[0] = o[0];
+  else if (VX == 2 && sizeof(T) == 4) *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+  else if (VX == 4 && sizeof(T) == 4) *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  else if (VX == 2 && sizeof(T) == 8) *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+  else {
+#pragma unroll
+    for (int e = 0; e < VX; ++e) p[e] = o[e];
+  }
+}
+
+template <typename T, int BC, bool STEP, int VX>
+__global__ void __launch_bounds__(NT3) k_stencil3d(StencilArgs<T> a) {
+  constexpr int BX = TX * VX;  // tile width in cells
+  constexpr int PW = BX + 2, PH = TY3 + 2, PSZ = PW * PH;
+  constexpr int NRING = 2 * PW + 2 * TY3;
+  constexpr int RPT = (NRING + NT3 - 1) / NT3;  // ring cells per thread
+  __shared__ T ps[2][PSZ];
+  __shared__ Dots<T> red[NT3 / 32];
   __shared__ int s_int[4];
   __shared__ float s_flt[4];
   const int s = blockIdx.z / a.nzc;
@@ -205,7 +253,7 @@ __global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
   const size_t n = a.n, plane = (size_t)nx * ny;
   const int zper = (nz + a.nzc - 1) / a.nzc;
   const int z0 = zc * zper, z1 = min(nz, z0 + zper);
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * TY3;
   const T* Win = (STEP ? ((j & 1) ? a.W1 : a.W0) : a.Win) + (size_t)s * n;
   T* Wout = (STEP ? ((j & 1) ? a.W0 : a.W1) : a.Wout) + (size_t)s * n;
   const T* Vp = nullptr;
@@ -224,8 +272,14 @@ __global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
       inv_b = (T)(1.0 / a.beta[mo]);
     }
   }
-  // value of v_j at global (gx, gy, gz); out-of-grid per boundary condition
-  auto form = [&](int gx, int gy, int gz, T* vp_out) -> T {
+  auto fv = [&](T w, T vp) -> T {
+    if (!STEP) return w;
+    if (j == 0) return w * inv_b;
+    return (w - coef * vp) * inv_b;
+  };
+  // raw inputs of one cell (ring); outside the grid per boundary condition
+  auto load1 = [&](int gx, int gy, int gz, T& w, T& vp) {
+    w = vp = (T)0;
     bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
     if (!in && BC == GMRF_BC_PERIODIC) {
       gx = wrapi(gx, nx);
@@ -233,69 +287,136 @@ __global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
       gz = wrapi(gz, nz);
       in = true;
     }
-    if (!in) {
-      if (vp_out) *vp_out = 0;
-      return 0;
-    }
+    if (!in) return;
     const size_t i = (size_t)gx + (size_t)nx * gy + plane * gz;
-    const T w = Win[i];
-    if (!STEP) return w;
-    if (j == 0) {
-      if (vp_out) *vp_out = 0;
-      return w * inv_b;
-    }
-    const T vp = Vp[i];
-    if (vp_out) *vp_out = vp;
-    return (w - coef * vp) * inv_b;
+    w = Win[i];
+    if (STEP && j > 0) vp = Vp[i];
   };
-  const int gx = x0 + tx, gy = y0 + ty;
+  // raw inputs of the thread's VX cells (x = gx .. gx + VX - 1, all inside or
+  // all outside the grid in x since nx % VX == 0)
+  const int gx = x0 + tx * VX, gy = y0 + ty;
   const bool own = gx < nx && gy < ny;
+  auto loadv = [&](int gz, Raw<T, VX>& r) {
+#pragma unroll
+    for (int e = 0; e < VX; ++e) {
+      r.w[e] = r.vp[e] = (T)0;
+      r.k[e] = 0.f;
+    }
+    int zz = gz, yy = gy;
+    bool in = own && gz >= 0 && gz < nz;
+    if (!in && BC == GMRF_BC_PERIODIC && own) {
+      zz = wrapi(gz, nz);
+      in = true;
+    }
+    if (!in) {
+      if (BC == GMRF_BC_PERIODIC && !own) {
+        // partial tile in a periodic grid: wrapped neighbours still needed
+#pragma unroll
+        for (int e = 0; e < VX; ++e) load1(gx + e, gy, gz, r.w[e], r.vp[e]);
+      }
+      return;
+    }
+    const size_t i = (size_t)gx + (size_t)nx * yy + plane * zz;
+    vload<T, VX>(Win + i, r.w);
+    if (STEP && j > 0) vload<T, VX>(Vp + i, r.vp);
+    if (a.kappa2) {
+      if (VX == 4) {
+        const float4 kk = *reinterpret_cast<const float4*>(a.kappa2 + i);
+        r.k[0] = kk.x; r.k[1] = kk.y; r.k[2 % VX] = kk.z; r.k[3 % VX] = kk.w;
+      } else if (VX == 2) {
+        const float2 kk = *reinterpret_cast<const float2*>(a.kappa2 + i);
+        r.k[0] = kk.x; r.k[1 % VX] = kk.y;
+      } else {
+        r.k[0] = __ldg(a.kappa2 + i);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VX; ++e) r.k[e] = (float)a.kappa2_const;
+    }
+  };
+  // halo ring cells of this thread
+  int rcx[RPT], rcy[RPT];
+  bool rin[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = tid + q * NT3;
+    rin[q] = r < NRING;
+    rcx[q] = rcy[q] = 0;
+    if (r < PW) { rcx[q] = r; rcy[q] = 0; }
+    else if (r < 2 * PW) { rcx[q] = r - 2 * 0 - PW; rcy[q] = PH - 1; }
+    else if (r < 2 * PW + TY3) { rcx[q] = 0; rcy[q] = r - 2 * PW + 1; }
+    else if (r < NRING) { rcx[q] = PW - 1; rcy[q] = r - 2 * PW - TY3 + 1; }
+  }
   Dots<T> d;
   d.zero();
-  T vdn = 0, vc = 0, vpc = 0;
-  if (own && z0 < z1) {
-    vdn = form(gx, gy, z0 - 1, nullptr);
-    vc = form(gx, gy, z0, &vpc);
+  Raw<T, VX> rc, r1, r2;
+  T rgw[RPT], rgv[RPT];
+  T vdn[VX], vc[VX];
+#pragma unroll
+  for (int e = 0; e < VX; ++e) vdn[e] = vc[e] = (T)0;
+  if (z0 < z1) {
+    Raw<T, VX> rm;
+    loadv(z0 - 1, rm);
+    loadv(z0, rc);
+    loadv(z0 + 1, r1);
+    loadv(z0 + 2, r2);
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+      if (rin[q]) load1(x0 - 1 + rcx[q], y0 - 1 + rcy[q], z0, rgw[q], rgv[q]);
+#pragma unroll
+    for (int e = 0; e < VX; ++e) {
+      vdn[e] = fv(rm.w[e], rm.vp[e]);
+      vc[e] = fv(rc.w[e], rc.vp[e]);
+    }
   }
   for (int z = z0; z < z1; ++z) {
-    T vpu = 0, vup = 0;
-    if (own) vup = form(gx, gy, z + 1, &vpu);
-    // plane z with x-y halo: centre from registers, ring from global
-    if (own) ps[(ty + 1) * PW + tx + 1] = vc;
-    for (int r = tid; r < 2 * PW + 2 * TY; r += NT) {
-      int cx, cy;
-      if (r < PW) { cx = r; cy = 0; }
-      else if (r < 2 * PW) { cx = r - PW; cy = PH - 1; }
-      else if (r < 2 * PW + TY) { cx = 0; cy = r - 2 * PW + 1; }
-      else { cx = PW - 1; cy = r - 2 * PW - TY + 1; }
-      ps[cy * PW + cx] = form(x0 - 1 + cx, y0 - 1 + cy, z, nullptr);
+    const int b = (z - z0) & 1;
+    T vup[VX];
+#pragma unroll
+    for (int e = 0; e < VX; ++e) vup[e] = fv(r1.w[e], r1.vp[e]);
+    // loads for later planes, in flight while this plane is computed
+    Raw<T, VX> r3;
+    loadv(z + 3, r3);
+    T rgwn[RPT], rgvn[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      rgwn[q] = rgvn[q] = (T)0;
+      if (rin[q]) load1(x0 - 1 + rcx[q], y0 - 1 + rcy[q], z + 1, rgwn[q], rgvn[q]);
     }
-    // partial tiles: centre cells outside the grid still need a value for neighbours
-    if (!own) {
-      const int cgx = x0 + tx, cgy = y0 + ty;
-      ps[(ty + 1) * PW + tx + 1] = form(cgx, cgy, z, nullptr);
-    }
+#pragma unroll
+    for (int e = 0; e < VX; ++e) ps[b][(ty + 1) * PW + tx * VX + e + 1] = vc[e];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+      if (rin[q]) ps[b][rcy[q] * PW + rcx[q]] = fv(rgw[q], rgv[q]);
     __syncthreads();
     if (own) {
       const size_t i = (size_t)gx + (size_t)nx * gy + plane * z;
-      const T kap = kap_at<T>(a.kappa2, a.kappa2_const, i);
-      T r = bop2<T, BC, PW>(ps, tx + 1, ty + 1, gx, gy, nx, ny, kap);
-      if (BC != GMRF_BC_NEUMANN || z > 0) r += vc - vdn;
-      if (BC != GMRF_BC_NEUMANN || z < nz - 1) r += vc - vup;
-      if (!STEP) {
-        Wout[i] = r;
-      } else {
-        T q = r;
-        if (j > 0) q -= bprev * vpc;
-        Wout[i] = q;
-        Vc[i] = vc;
-        d.add(vc, q);
+      T qo[VX];
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        T r = bop2<T, BC, PW>(ps[b], tx * VX + e + 1, ty + 1, gx + e, gy, nx, ny, (T)rc.k[e]);
+        if (BC != GMRF_BC_NEUMANN || z > 0) r += vc[e] - vdn[e];
+        if (BC != GMRF_BC_NEUMANN || z < nz - 1) r += vc[e] - vup[e];
+        if (STEP && j > 0) r -= bprev * rc.vp[e];
+        qo[e] = r;
+        if (STEP) d.add(vc[e], r);
       }
+      vstore<T, VX>(Wout + i, qo);
+      if (STEP) vstore<T, VX>(Vc + i, vc);
     }
-    __syncthreads();
-    vdn = vc;
-    vc = vup;
-    vpc = vpu;
+#pragma unroll
+    for (int e = 0; e < VX; ++e) {
+      vdn[e] = vc[e];
+      vc[e] = vup[e];
+    }
+    rc = r1;
+    r1 = r2;
+    r2 = r3;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      rgw[q] = rgwn[q];
+      rgv[q] = rgvn[q];
+    }
   }
   if (!STEP) return;
   d = block_reduce(d, red);
@@ -305,9 +426,16 @@ __global__ void __launch_bounds__(NT) k_stencil3d(StencilArgs<T> a) {
     finish_step<T>(a.P, j, s, a.partials, nblk, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red, s_int, s_flt);
 }
 
-int nz_chunks(const Grid& g) {
+// cells per thread along x for the 3-D kernel
+int vx3(const Grid& g, bool fp64) {
+  if (!fp64 && g.nx % 4 == 0 && g.nx >= 128) return 4;
+  if (g.nx % 2 == 0 && g.nx >= 64) return 2;
+  return 1;
+}
+
+int nz_chunks(const Grid& g, int vx) {
   if (g.dim != 3) return 1;
-  const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+  const int tiles = ((g.nx + TX * vx - 1) / (TX * vx)) * ((g.ny + TY3 - 1) / TY3);
   int c = 1;
   while (c < g.nz && tiles * c < 4 * 152 && (g.nz + 2 * c - 1) / (2 * c) >= 8) c *= 2;
   return c;
@@ -319,13 +447,24 @@ cudaError_t dispatch(const Grid& g, StencilArgs<T> a, int nvec, cudaStream_t s) 
   dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, nvec);
   if (g.dim == 3) {
     if (g.op != GMRF_OP_SHIFTED_LAPLACIAN) return cudaErrorNotSupported;
-    a.nzc = nz_chunks(g);
-    grd.z = nvec * a.nzc;
+    const int vx = vx3(g, sizeof(T) == 8);
+    a.nzc = nz_chunks(g, vx);
+    blk = dim3(TX, TY3);
+    grd = dim3((g.nx + TX * vx - 1) / (TX * vx), (g.ny + TY3 - 1) / TY3, nvec * a.nzc);
+#define GMRF_L3(BCV, VXV) k_stencil3d<T, BCV, STEP, VXV><<<grd, blk, 0, s>>>(a)
+#define GMRF_L3V(BCV) \
+  do {                \
+    if (vx == 4) GMRF_L3(BCV, 4); \
+    else if (vx == 2) GMRF_L3(BCV, 2); \
+    else GMRF_L3(BCV, 1); \
+  } while (0)
     switch (g.bc) {
-      case GMRF_BC_PERIODIC: k_stencil3d<T, GMRF_BC_PERIODIC, STEP><<<grd, blk, 0, s>>>(a); break;
-      case GMRF_BC_NEUMANN: k_stencil3d<T, GMRF_BC_NEUMANN, STEP><<<grd, blk, 0, s>>>(a); break;
-      default: k_stencil3d<T, GMRF_BC_DIRICHLET, STEP><<<grd, blk, 0, s>>>(a); break;
+      case GMRF_BC_PERIODIC: GMRF_L3V(GMRF_BC_PERIODIC); break;
+      case GMRF_BC_NEUMANN: GMRF_L3V(GMRF_BC_NEUMANN); break;
+      default: GMRF_L3V(GMRF_BC_DIRICHLET); break;
     }
+#undef GMRF_L3V
+#undef GMRF_L3
     return cudaGetLastError();
   }
   a.nzc = 1;
@@ -362,7 +501,11 @@ StencilArgs<T> make_args(const Grid& g, const void* kappa2, double kc) {
 }  // namespace
 
 int stencil_blocks_per_vector(const Grid& g) {
-  return ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * nz_chunks(g);
+  if (g.dim == 3) {
+    // the widest tile (VX = 1) has the most blocks
+    return ((g.nx + TX - 1) / TX) * ((g.ny + TY3 - 1) / TY3) * nz_chunks(g, 1);
+  }
+  return ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
 }
 
 cudaError_t launch_stencil_step(const Grid& g, bool fp64, const void* kappa2, double kappa2_const,

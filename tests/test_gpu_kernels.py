@@ -57,7 +57,9 @@ STENCIL_CASES = [((17, 23), "periodic", "shifted_laplacian"), ((17, 23), "neuman
                  ((17, 23), "dirichlet", "shifted_laplacian"), ((33, 20), "periodic", "spde_squared"),
                  ((33, 20), "neumann", "spde_squared"), ((33, 20), "dirichlet", "spde_squared"),
                  ((5, 7, 9), "periodic", "shifted_laplacian"), ((5, 7, 9), "neumann", "shifted_laplacian"),
-                 ((9, 40, 35), "dirichlet", "shifted_laplacian"), ((3, 2, 70), "periodic", "shifted_laplacian")]
+                 ((9, 40, 35), "dirichlet", "shifted_laplacian"), ((3, 2, 70), "periodic", "shifted_laplacian"),
+                 ((4, 9, 128), "dirichlet", "shifted_laplacian"), ((5, 6, 256), "periodic", "shifted_laplacian"),
+                 ((3, 17, 132), "neumann", "shifted_laplacian"), ((19, 3, 64), "periodic", "shifted_laplacian")]
 
 
 @pytest.mark.parametrize("shape,bc,op", STENCIL_CASES)

@@ -51,7 +51,8 @@ def test_periodic_64x64_fp64_tol1e10(g):
 
 SMALL = [((12, 10), "periodic", "shifted_laplacian"), ((12, 10), "neumann", "spde_squared"),
          ((12, 10), "dirichlet", "spde_squared"), ((11, 13), "neumann", "shifted_laplacian"),
-         ((6, 7, 5), "dirichlet", "shifted_laplacian"), ((6, 7, 5), "periodic", "shifted_laplacian")]
+         ((6, 7, 5), "dirichlet", "shifted_laplacian"), ((6, 7, 5), "periodic", "shifted_laplacian"),
+         ((3, 4, 128), "neumann", "shifted_laplacian")]
 
 
 @pytest.mark.parametrize("shape,bc,op", SMALL)
