@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "stencil_args.h"
 
 namespace gmrf {
 namespace {
@@ -30,28 +31,6 @@ namespace {
 constexpr int TX = 32;
 constexpr int TY = 16;
 constexpr int NT = TX * TY;
-
-template <typename T>
-struct StencilArgs {
-  const T* Win;  // apply mode: v
-  T* Wout;       // apply mode: y
-  T* W0;         // step mode: q ping-pong, W[j & 1] read, W[(j+1) & 1] written
-  T* W1;
-  T* V;  // basis ring base
-  const float* kappa2;
-  T kappa2_const;
-  int nx, ny, nz;
-  size_t n;
-  int nzc;  // z chunks (3-D)
-  StepParams P;
-  VecState* st;
-  double* alpha;
-  double* beta;
-  float* alpha_f;
-  float* beta2_f;
-  Dots<T>* partials;
-  unsigned* counters;
-};
 
 __device__ __forceinline__ int wrapi(int g, int n) {
   g %= n;
@@ -447,6 +426,11 @@ cudaError_t dispatch(const Grid& g, StencilArgs<T> a, int nvec, cudaStream_t s) 
   dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, nvec);
   if (g.dim == 3) {
     if (g.op != GMRF_OP_SHIFTED_LAPLACIAN) return cudaErrorNotSupported;
+    if constexpr (sizeof(T) == 4) {
+      if (stencil3d_tma_eligible(g, false) &&
+          (STEP || stencil3d_tma_pointers_ok(a.Win, a.Wout, a.kappa2)))
+        return launch_stencil3d_tma(g, a, nvec, STEP, s);
+    }
     const int vx = vx3(g, sizeof(T) == 8);
     a.nzc = nz_chunks(g, vx);
     blk = dim3(TX, TY3);
@@ -502,8 +486,10 @@ StencilArgs<T> make_args(const Grid& g, const void* kappa2, double kc) {
 
 int stencil_blocks_per_vector(const Grid& g) {
   if (g.dim == 3) {
-    // the widest tile (VX = 1) has the most blocks
-    return ((g.nx + TX - 1) / TX) * ((g.ny + TY3 - 1) / TY3) * nz_chunks(g, 1);
+    // the widest tile (VX = 1) has the most blocks; the TMA kernel's items
+    const int r = ((g.nx + TX - 1) / TX) * ((g.ny + TY3 - 1) / TY3) * nz_chunks(g, 1);
+    const int t = stencil3d_tma_eligible(g, false) ? stencil3d_tma_items_per_vector(g) : 0;
+    return r > t ? r : t;
   }
   return ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
 }

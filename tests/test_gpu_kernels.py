@@ -59,7 +59,8 @@ STENCIL_CASES = [((17, 23), "periodic", "shifted_laplacian"), ((17, 23), "neuman
                  ((5, 7, 9), "periodic", "shifted_laplacian"), ((5, 7, 9), "neumann", "shifted_laplacian"),
                  ((9, 40, 35), "dirichlet", "shifted_laplacian"), ((3, 2, 70), "periodic", "shifted_laplacian"),
                  ((4, 9, 128), "dirichlet", "shifted_laplacian"), ((5, 6, 256), "periodic", "shifted_laplacian"),
-                 ((3, 17, 132), "neumann", "shifted_laplacian"), ((19, 3, 64), "periodic", "shifted_laplacian")]
+                 ((3, 17, 132), "neumann", "shifted_laplacian"), ((19, 3, 64), "periodic", "shifted_laplacian"),
+                 ((70, 12, 384), "neumann", "shifted_laplacian"), ((37, 29, 256), "dirichlet", "shifted_laplacian")]
 
 
 @pytest.mark.parametrize("shape,bc,op", STENCIL_CASES)
@@ -77,6 +78,22 @@ def test_stencil_apply(g, shape, bc, op, precision):
     for s in range(3):
         ref = Q @ V[s].astype(np.float64)
         assert _rel(Y[s], ref) <= (1e-13 if precision == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_stencil_apply_3d_constant_kappa(g, bc):
+    # 3-D 7-point apply with a constant coefficient (no kappa^2 field), several
+    # z chunks and a ragged tile in y
+    shape = (66, 10, 128)
+    n = int(np.prod(shape))
+    Q = stencil.precision_matrix(shape, bc, "shifted_laplacian", 0.37, tau=1.3)
+    V = inputs.gaussian_vectors(2, n, seed=12, dtype=np.float32)
+    with g.Problem(shape, bc, "shifted_laplacian", kappa2_const=0.37, tau=1.3) as p:
+        y = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+        p.apply(0, _dev(V), y, nvec=2)
+        Y = y.cpu().numpy().reshape(2, n)
+    for s in range(2):
+        assert _rel(Y[s], Q @ V[s].astype(np.float64)) <= 2e-6
 
 
 PRE_CASES = [((8, 8), "periodic"), ((16, 32), "periodic"), ((64, 64), "neumann"), ((32, 16), "neumann"),

@@ -139,6 +139,34 @@ def test_batch_equals_alone(g):
             assert info_1[0].m_used == info_b[s].m_used
 
 
+def test_3d_fp32_vs_dst_spectrum(g):
+    # 3-D Dirichlet 7-point, constant kappa^2, FP32 vectors: several z chunks,
+    # three x tiles and a ragged y tile; exact x = Q^{-1/2} z from the DST-I spectrum
+    shape = (72, 12, 384)
+    n = int(np.prod(shape))
+    Z = inputs.gaussian_vectors(3, n, seed=21, dtype=np.float32)
+    with g.Problem(shape, "dirichlet", "shifted_laplacian", kappa2_const=0.3, tau=1.5) as p:
+        rc, info, X = _sample(g, p, Z, 3e-7, 400, "fp32")
+    assert rc == g.OK
+    for s in range(3):
+        xe = exact.sample_spectral(shape, "dirichlet", "shifted_laplacian", 0.3, 1.5, Z[s].astype(np.float64))
+        assert _rel(X[s], xe) <= 1e-6
+
+
+def test_batch_equals_alone_3d(g):
+    # the 3-D step's partial sums depend only on the grid: batched == alone, bitwise
+    shape = (70, 9, 128)
+    n = int(np.prod(shape))
+    k2 = inputs.kappa2_uniform_field(shape, seed=5)
+    Z = inputs.gaussian_vectors(3, n, seed=10, dtype=np.float32)
+    with g.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=_dev(k2)) as p:
+        _, info_b, Xb = _sample(g, p, Z, 1e-6, 400, "fp32")
+        for s in range(3):
+            _, info_1, X1 = _sample(g, p, Z[s:s + 1], 1e-6, 400, "fp32")
+            np.testing.assert_array_equal(X1[0], Xb[s])
+            assert info_1[0].m_used == info_b[s].m_used
+
+
 def test_device_noise_matches_oracle_generator(g):
     # z from the device Philox stream (no z_in) equals the oracle's generator
     shape = (32, 32)
