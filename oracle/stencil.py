@@ -77,6 +77,52 @@ def precision_matrix(shape, bc: str, op: str, kappa2, tau: float = 1.0) -> sp.cs
     return sp.csr_matrix(float(tau) * Q)
 
 
+def _shifted_rows(shape, bc, kvec_at, rows):
+    """Rows ``rows`` of B = K + L as a sparse (len(rows) x n) matrix, from the
+    1-D Laplacians of each axis (row (c_0..c_{d-1}) of the Kronecker sum is the
+    sum over axes of row c_ax of the 1-D matrix along that axis)."""
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape))
+    rows = np.asarray(rows, dtype=np.int64)
+    strides = [int(np.prod(shape[ax + 1:])) for ax in range(len(shape))]
+    coords = np.stack(np.unravel_index(rows, shape), axis=0)  # [dim][len]
+    r_list, c_list, v_list = [np.arange(len(rows))], [rows], [kvec_at(rows)]
+    for ax, s in enumerate(shape):
+        L1 = laplacian_1d(s, bc).tocsr()
+        for r, c in enumerate(coords[ax]):
+            lo, hi = L1.indptr[c], L1.indptr[c + 1]
+            cols1, vals1 = L1.indices[lo:hi], L1.data[lo:hi]
+            base = rows[r] - c * strides[ax]
+            r_list.append(np.full(len(cols1), r))
+            c_list.append(base + cols1.astype(np.int64) * strides[ax])
+            v_list.append(vals1)
+    R = sp.csr_matrix((np.concatenate(v_list), (np.concatenate(r_list), np.concatenate(c_list))),
+                      shape=(len(rows), n))
+    R.sum_duplicates()
+    return R
+
+
+def precision_rows(shape, bc: str, op: str, kappa2, tau: float = 1.0, rows=()) -> sp.csr_matrix:
+    """Rows ``rows`` of Q without assembling Q (for sampled checks of
+    matrix-free products on grids too large to assemble)."""
+    if op not in OPS:
+        raise ValueError(op)
+    shape = tuple(int(s) for s in shape)
+    k = np.asarray(kappa2, dtype=np.float64)
+    if k.ndim == 0:
+        kvec_at = lambda idx: np.full(len(idx), float(k))  # noqa: E731
+    else:
+        kf = k.reshape(-1)
+        kvec_at = lambda idx: kf[idx].astype(np.float64)  # noqa: E731
+    R = _shifted_rows(shape, bc, kvec_at, rows)
+    if op == "spde_squared":
+        # rows of B B: (row_i of B) applied to the rows of B it touches
+        cols = np.unique(R.indices)
+        Rc = _shifted_rows(shape, bc, kvec_at, cols)
+        R = sp.csr_matrix(R[:, cols] @ Rc)
+    return sp.csr_matrix(float(tau) * R)
+
+
 def precision_matrix_bruteforce(shape, bc: str, op: str, kappa2, tau: float = 1.0) -> np.ndarray:
     """Dense Q built cell by cell from the neighbour definition (pin for the above).
 

@@ -1,0 +1,161 @@
+"""GPU parity at the benchmark sizes, in the launch configurations the bench
+times, against the oracle (Algorithm 1 with full reorthogonalisation in FP64,
+Proposition 1 for the preconditioned case), plus the sample covariance
+against Q^{-1}.
+
+* 1024 x 1024 SPDE, mirror-preconditioned, one FP32 sample at tol 1e-6:
+  whole vector against the oracle's FP64 Lanczos run to 1e-9.
+* 512 x 512 SPDE, 256 samples in one batch: two of the vectors against the
+  oracle; 64 fixed Rademacher probes: two per-probe quadratures.
+* 3-D 7-point at 128^3 (the 256^3 recipe one size down): two of 16 vectors
+  against the oracle.
+* 256^3: the stencil apply on sampled cells against the oracle's rows of Q,
+  and x^T Q x = z^T z for samples of the 16-vector batch (x = Q^{-1/2} z).
+"""
+import numpy as np
+import pytest
+
+from oracle import exact, lanczos as olz, precond, stencil
+from paper_1312_1476_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_1312_1476_gb300 import gmrf
+    assert torch.cuda.is_available()
+    return gmrf
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b))
+
+
+def _spde_oracle_sample(shape, k2, kb, z):
+    Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2.astype(np.float64), 1.0)
+    x, m, est, status = olz.precond_sample(Q, shape, "neumann", "spde_squared", kb, 1.0, z.astype(np.float64),
+                                           1e-9, 400, check_every=1, reorth=True)
+    assert status == "ok"
+    return x
+
+
+def test_headline_1024_mirror_fp32(g):
+    shape = (1024, 1024)
+    n = 1024 * 1024
+    k2 = inputs.kappa2_gp_field(shape, seed=1)
+    kb = precond.kappa2_bar(k2)
+    z = inputs.gaussian_vectors(1, n, seed=2, dtype=np.float32)
+    with g.Problem(shape, "neumann", "spde_squared", kappa2=_dev(k2), precond="mirror", kappa2_precond=kb) as p:
+        x = torch.empty(n, dtype=torch.float32, device="cuda")
+        rc, info = p.sample(x, nsamples=1, tol=1e-6, m_max=2000, z=_dev(z))
+    assert rc == g.OK and info[0].err_est <= 1e-6
+    xe = _spde_oracle_sample(shape, k2, kb, z[0])
+    assert _rel(x.cpu().numpy(), xe) <= 1e-6
+
+
+def test_batched_512_samples_and_logdet_probes(g):
+    shape = (512, 512)
+    n = 512 * 512
+    k2 = inputs.kappa2_gp_field(shape, seed=1, ell=64.0)
+    kb = precond.kappa2_bar(k2)
+    ns = 256
+    Z = inputs.gaussian_vectors(ns, n, seed=2, dtype=np.float32)
+    R = inputs.rademacher_vectors(64, n, seed=3, dtype=np.float32)
+    with g.Problem(shape, "neumann", "spde_squared", kappa2=_dev(k2), precond="mirror", kappa2_precond=kb) as p:
+        x = torch.empty(ns * n, dtype=torch.float32, device="cuda")
+        rc, info = p.sample(x, nsamples=ns, tol=1e-6, m_max=200, z=_dev(Z))
+        assert rc == g.OK
+        X = x.cpu().numpy().reshape(ns, n)
+        ld, se, q, linfo, rc2 = p.logdet(nprobes=64, tol=1e-6, m_max=200, probes=_dev(R))
+        assert rc2 == g.OK
+    for s in (0, ns - 1):
+        assert _rel(X[s], _spde_oracle_sample(shape, k2, kb, Z[s])) <= 1e-6
+    Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2.astype(np.float64), 1.0)
+    A = olz.preconditioned_operator(Q, shape, "neumann", "spde_squared", kb, 1.0)
+    for i in (0, 63):
+        qo, _, st = olz.quadrature_term(A, R[i].astype(np.float64), 1e-9, 400, reorth=True)
+        assert st == "ok"
+        assert abs(q[i] - qo) <= 1e-6 * abs(qo)
+
+
+def test_3d_128_fp32_vs_oracle(g):
+    shape = (128, 128, 128)
+    n = 128 ** 3
+    k3 = inputs.kappa2_uniform_field(shape, seed=1)
+    Z = inputs.gaussian_vectors(16, n, seed=2, dtype=np.float32)
+    with g.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=_dev(k3)) as p:
+        x = torch.empty(16 * n, dtype=torch.float32, device="cuda")
+        rc, info = p.sample(x, nsamples=16, tol=1e-6, m_max=100, z=_dev(Z))
+    assert rc == g.OK
+    X = x.cpu().numpy().reshape(16, n)
+    Q = stencil.precision_matrix(shape, "dirichlet", "shifted_laplacian", k3.astype(np.float64), 1.0)
+    for s in (0, 15):
+        xe, m, est, status = olz.adaptive_sample(lambda v: Q @ v, Z[s].astype(np.float64), 1e-9, 300, reorth=True)
+        assert status == "ok"
+        assert _rel(X[s], xe) <= 1e-6
+
+
+def test_3d_256_rows_and_energy(g):
+    shape = (256, 256, 256)
+    n = 256 ** 3
+    k3 = inputs.kappa2_uniform_field(shape, seed=1)
+    rng = np.random.default_rng(11)
+    rows = rng.choice(n, size=4000, replace=False)
+    # boundary cells of every face are in the sample too
+    face = np.ravel_multi_index((np.array([0, 255, 7, 9, 100, 31]), np.array([5, 9, 0, 255, 17, 44]),
+                                 np.array([3, 77, 12, 200, 0, 255])), shape)
+    rows = np.unique(np.concatenate([rows, face]))
+    Rq = stencil.precision_rows(shape, "dirichlet", "shifted_laplacian", k3, 1.0, rows)
+    V = inputs.gaussian_vectors(2, n, seed=13, dtype=np.float32)
+    Z = inputs.gaussian_vectors(16, n, seed=2, dtype=np.float32)
+    with g.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=_dev(k3)) as p:
+        y = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+        p.apply(0, _dev(V), y, nvec=2)
+        Y = y.cpu().numpy().reshape(2, n)
+        for s in range(2):
+            ref = Rq @ V[s].astype(np.float64)
+            assert np.max(np.abs(Y[s, rows] - ref)) <= 2e-6 * np.max(np.abs(ref))
+        # the 16-sample batch of the bench, then x^T Q x against z^T z
+        x = torch.empty(16 * n, dtype=torch.float32, device="cuda")
+        rc, info = p.sample(x, nsamples=16, tol=1e-6, m_max=100, z=_dev(Z))
+        assert rc == g.OK
+        qx = torch.empty(4 * n, dtype=torch.float32, device="cuda")
+        p.apply(0, x[:4 * n], qx, nvec=4)
+        X = x[:4 * n].cpu().numpy().reshape(4, n).astype(np.float64)
+        QX = qx.cpu().numpy().reshape(4, n).astype(np.float64)
+    for s in range(4):
+        zz = float(np.dot(Z[s].astype(np.float64), Z[s].astype(np.float64)))
+        assert abs(float(np.dot(X[s], QX[s])) - zz) <= 3e-6 * zz
+
+
+@pytest.mark.parametrize("case", ["periodic_unpreconditioned", "neumann_spde_mirror"])
+def test_sample_covariance(g, case):
+    # 2e5 draws on a 16 x 16 grid: every entry of the empirical covariance
+    # within 6 standard errors of Q^{-1}, se_ij^2 = (S_ii S_jj + S_ij^2) / N
+    shape = (16, 16)
+    n = 256
+    N = 200_000
+    if case == "periodic_unpreconditioned":
+        Q = stencil.precision_matrix(shape, "periodic", "shifted_laplacian", 0.5, 1.0)
+        prob = g.Problem(shape, "periodic", "shifted_laplacian", kappa2_const=0.5)
+    else:
+        k2 = inputs.kappa2_gp_field(shape, seed=5, ell=4.0)
+        Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2.astype(np.float64), 2.0)
+        prob = g.Problem(shape, "neumann", "spde_squared", kappa2=_dev(k2), tau=2.0, precond="mirror")
+    with prob as p:
+        x = torch.empty(N * n, dtype=torch.float32, device="cuda")
+        rc, info = p.sample(x, nsamples=N, tol=1e-6, m_max=300, seed=77)
+        assert rc == g.OK
+        X = x.view(N, n).double()
+        C = (X.T @ X / N).cpu().numpy()
+    S = np.linalg.inv(Q.toarray())
+    d = np.diag(S)
+    se = np.sqrt((np.outer(d, d) + S ** 2) / N)
+    assert np.max(np.abs(C - S) / se) <= 6.0

@@ -85,3 +85,17 @@ def test_figure3_matrix_structure():
     lmax = scale ** 2 * (4 - 4 * np.cos(side * h)) ** 2
     ev = np.linalg.eigvalsh(Qm)
     np.testing.assert_allclose([ev[0], ev[-1]], [lmin, lmax], rtol=1e-9)
+
+
+@pytest.mark.parametrize("shape", [(5, 7, 9), (2, 3, 4), (6, 8), (3, 1, 5), (2, 2, 2)])
+@pytest.mark.parametrize("bc", stencil.BCS)
+@pytest.mark.parametrize("op", stencil.OPS)
+def test_precision_rows_match_bruteforce(shape, bc, op):
+    # sampled rows of Q (used for full-size checks) against the cell-by-cell assembly
+    rng = np.random.default_rng(7)
+    k = rng.uniform(0.1, 1.0, size=shape)
+    n = int(np.prod(shape))
+    rows = rng.choice(n, size=min(n, 9), replace=False)
+    Qb = stencil.precision_matrix_bruteforce(shape, bc, op, k, tau=1.3)
+    R = stencil.precision_rows(shape, bc, op, k, 1.3, rows).toarray()
+    np.testing.assert_allclose(R, Qb[rows], rtol=0, atol=1e-12)
