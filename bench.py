@@ -390,6 +390,20 @@ def measure_variants(args, gmrf, torch, flush, peak):
                              "achieved_GBps": ach, "peak_GBps": peak, "frac": ach / peak,
                              "algorithmic_bytes_per_launch": byts / max(st_t, 1),
                              "bytes_rule": "20 n per vector-step (read q_{j-1}, v_{j-1}, kappa^2; write q_j, v_j)"}}
+        # the same 16 samples with a bfloat16 basis for the assembly (half the V_m memory)
+        xb = torch.empty(ns * n, dtype=torch.float32, device="cuda")
+        p.sample(xb, nsamples=ns, tol=TOL, m_max=m3, seed=40, v_storage="bf16")
+        msb, (rcb, infob) = timed(lambda i: p.sample(xb, nsamples=ns, tol=TOL, m_max=m3, seed=40 + i,
+                                                     v_storage="bf16"), 3)
+        p.sample(x, nsamples=ns, tol=TOL, m_max=m3, seed=42)
+        diff = float(torch.linalg.vector_norm((xb - x).view(ns, n).double(), dim=1).max() /
+                     torch.linalg.vector_norm(x.view(ns, n).double(), dim=1).min())
+        out["3d_256_bf16_basis"] = {
+            "workload": "same 256^3 problem and 16 samples, V_m stored in bfloat16 for the assembly",
+            "samples_per_s": ns * 1e3 / msb, "ms_per_call": msb, "status": rcb,
+            "m_mean": float(np.mean([i.m_used for i in infob])),
+            "basis_bytes_per_vector_step": {"fp32": 4 * n, "bf16": 2 * n},
+            "max_rel_diff_vs_fp32_basis": diff}
     out["serving"] = measure_serving()
     return out
 

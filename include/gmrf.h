@@ -103,6 +103,20 @@ typedef struct {
   int32_t reserved;    /* must be 0 */
 } gmrf_desc;
 
+/* Storage of the Lanczos basis V_m that the assembly x_m = ||z|| V_m y reads
+ * (Algorithm 1, last step).
+ *   NATIVE -- the vector precision (FP32 or FP64);
+ *   BF16   -- FP32 problems only: v_j is also rounded to bfloat16 into a
+ *             basis copy of (m_max + 1) * n * 2 bytes per vector, and the
+ *             FP32 basis keeps only v_{j-1} and v_j for the recurrence.  The
+ *             iteration (alpha, beta, m, the stopping rule) is bitwise the
+ *             same as with NATIVE; x_m carries the bfloat16 rounding of V_m,
+ *             about 1e-3 relative, instead of reaching tol.  Halves the
+ *             memory of V_m, so more vectors or larger m fit in HBM.  FP64
+ *             problems return GMRF_ERR_UNSUPPORTED.  The paper stores V_m
+ *             at working precision; this is an option of this library. */
+typedef enum { GMRF_VSTORE_NATIVE = 0, GMRF_VSTORE_BF16 = 1 } gmrf_vstore;
+
 typedef struct {
   double tol;          /* relative tolerance of the Theorem 1 estimate, > 0 */
   int32_t m_max;       /* largest subspace size, >= 1 */
@@ -110,7 +124,7 @@ typedef struct {
   uint64_t seed;       /* Philox-4x32-10 key for z when z_in == NULL */
   const void* z_in;    /* optional [nsamples][n] noise, float (FP32) or double (FP64), host or device */
   int32_t check_every; /* steps between host polls of the convergence flags (<= 0: 16) */
-  int32_t reserved;    /* must be 0 */
+  int32_t v_storage;   /* gmrf_vstore: storage of the basis V_m kept for the assembly */
 } gmrf_sample_opts;
 
 typedef struct {

@@ -11,6 +11,7 @@
 // * Philox-4x32-10 (Salmon et al., SC'11) for z and the Rademacher probes.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -165,7 +166,27 @@ struct StepParams {
   int pad0;
   double tol;     // stopping tolerance on the relative estimate
   double bd_tol;  // breakdown threshold relative to ||T_m||
+  // bfloat16 copy of the basis for the assembly only ([nvec][m_max + 1][n]),
+  // or null.  When set, the FP32 ring above holds just v_{j-1}, v_j (nslots 2),
+  // so the recurrence itself is the same as with an FP32 basis.
+  __nv_bfloat16* vb;
 };
+
+// Stores of v_j into the bfloat16 basis copy (round to nearest even).
+__device__ __forceinline__ __nv_bfloat16* vb_at(const StepParams& P, int s, int j, size_t n, size_t i) {
+  return P.vb + ((size_t)s * (size_t)(P.m_max + 1) + (size_t)j) * n + i;
+}
+__device__ __forceinline__ void vb_store1(__nv_bfloat16* p, float a) { *p = __float2bfloat16_rn(a); }
+__device__ __forceinline__ void vb_store2(__nv_bfloat16* p, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+__device__ __forceinline__ void vb_store4(__nv_bfloat16* p, float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  uint2 u;
+  u.x = *reinterpret_cast<const unsigned*>(&lo);
+  u.y = *reinterpret_cast<const unsigned*>(&hi);
+  *reinterpret_cast<uint2*>(p) = u;
+}
 
 // Count of eigenvalues of T_m below sigma (Sturm sequence of the LDL^T pivots
 // of T_m - sigma I), in FP32 on float copies of alpha and beta^2.

@@ -90,7 +90,7 @@ struct StepGraph {
   GraphTrace tr;
   int nvec = -1, nslots = 0, m_max = 0, c = 0, kernels_per_step = 1;
   double tol = 0.0;
-  const void *W0 = nullptr, *V = nullptr, *st = nullptr, *S = nullptr, *partials = nullptr;
+  const void *W0 = nullptr, *V = nullptr, *Vb = nullptr, *st = nullptr, *S = nullptr, *partials = nullptr;
   bool timed = false;
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -116,7 +116,7 @@ struct gmrf_problem {
   PrecondTables pre;
   // Lanczos workspace (grow-only)
   DevBuf W0, W1, V, st, alpha, beta, alpha_f, beta2_f, partials, counters, y, scratch, nodes, q, out2, stage,
-      stage2, work;
+      stage2, work, Vb;
   VecState* st_host = nullptr;
   int st_host_cap = 0;
 };
@@ -147,7 +147,10 @@ int ensure_host_states(gmrf_problem* p, int nvec) {
 }
 
 // Buffers for a batch of nvec vectors with nslots stored basis vectors each.
-int ensure_lanczos(gmrf_problem* p, int nvec, int nslots, int m_max, bool need_tm, LanczosBufs& b) {
+// bf16_basis: keep a bfloat16 copy of V_m ([nvec][m_max + 1][n]) for the
+// assembly; the FP32 ring then has nslots = 2.
+int ensure_lanczos(gmrf_problem* p, int nvec, int nslots, int m_max, bool need_tm, LanczosBufs& b,
+                   bool bf16_basis = false) {
   const size_t n = p->g.n, es = esize(p);
   CKR(ensure(p->W0, (size_t)nvec * n * es, p->ws));
   CKR(ensure(p->W1, (size_t)nvec * n * es, p->ws));
@@ -171,6 +174,11 @@ int ensure_lanczos(gmrf_problem* p, int nvec, int nslots, int m_max, bool need_t
   b.W[0] = p->W0.p;
   b.W[1] = p->W1.p;
   b.V = p->V.p;
+  b.Vb = nullptr;
+  if (bf16_basis) {
+    CKR(ensure(p->Vb, (size_t)nvec * (size_t)(m_max + 1) * n * sizeof(__nv_bfloat16), p->ws));
+    b.Vb = (__nv_bfloat16*)p->Vb.p;
+  }
   b.st = (VecState*)p->st.p;
   b.alpha = (double*)p->alpha.p;
   b.beta = (double*)p->beta.p;
@@ -193,7 +201,7 @@ int batch_size(gmrf_problem* p, int want, int nslots, int m_max, bool need_tm, s
   }
   // memory already held by this problem's workspace can be reused
   const size_t held = p->W0.bytes + p->W1.bytes + p->V.bytes + p->scratch.bytes + p->stage.bytes +
-                      p->stage2.bytes + p->work.bytes;
+                      p->stage2.bytes + p->work.bytes + p->Vb.bytes;
   const size_t n = p->g.n, es = esize(p);
   size_t per = (size_t)(nslots + 2) * n * es + extra_per_vec + 64 * (size_t)m_max + 4096;
   if (need_tm) per += sizeof(double) * 2 * (size_t)m_max * kMaxNodes;
@@ -233,7 +241,8 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   const bool timed = trace_timing_enabled();
   const void* S = p->precond ? p->pre.S : nullptr;
   if (G.exec && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c && G.tol == P.tol &&
-      G.W0 == b.W[0] && G.V == b.V && G.st == b.st && G.S == S && G.partials == b.partials && G.timed == timed)
+      G.W0 == b.W[0] && G.V == b.V && G.Vb == b.Vb && G.st == b.st && G.S == S && G.partials == b.partials &&
+      G.timed == timed)
     return GMRF_OK;
   G.reset();
   cudaStream_t s = p->ws;
@@ -264,6 +273,7 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   G.tol = P.tol;
   G.W0 = b.W[0];
   G.V = b.V;
+  G.Vb = b.Vb;
   G.st = b.st;
   G.S = S;
   G.partials = b.partials;
@@ -280,6 +290,7 @@ int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, in
   P.nslots = b.nslots;
   P.tol = tol;
   P.bd_tol = p->fp64 ? 1e-13 : 1e-6;
+  P.vb = b.Vb;
   const int c = std::min(check_every > 0 ? check_every : 16, m_max);
   if (p->precond != GMRF_PREC_NONE) CKR(precond_prepare(p->pre, b.nvec, s));
   CKR(capture_steps(p, b, P, c));
@@ -454,7 +465,7 @@ void gmrf_destroy(gmrf_problem* p) {
   p->graph.reset();
   DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,
                     &p->partials, &p->counters, &p->y, &p->scratch, &p->nodes, &p->q, &p->out2, &p->stage,
-                    &p->stage2, &p->work};
+                    &p->stage2, &p->work, &p->Vb};
   for (DevBuf* b : bufs) release(*b, p->ws);
   precond_free(p->pre, p->ws);
   if (p->ws) cudaStreamSynchronize(p->ws);
@@ -468,14 +479,17 @@ void gmrf_destroy(gmrf_problem* p) {
 int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_result_info* info) {
   if (!p || !o || !x_out) return GMRF_ERR_INVALID;
   if (!(o->tol > 0.0) || !std::isfinite(o->tol) || o->m_max < 1 || o->m_max > 8192 || o->nsamples < 1 ||
-      o->reserved != 0)
+      (o->v_storage != GMRF_VSTORE_NATIVE && o->v_storage != GMRF_VSTORE_BF16))
     return GMRF_ERR_INVALID;
+  const bool bf16 = o->v_storage == GMRF_VSTORE_BF16;
+  if (bf16 && p->fp64) return GMRF_ERR_UNSUPPORTED;
   const size_t n = p->g.n, es = esize(p);
   const int m_max = o->m_max;
-  const int nslots = m_max + 1;
+  const int nslots = bf16 ? 2 : m_max + 1;
   const bool x_dev = is_device_ptr(x_out);
   const bool z_dev = o->z_in && is_device_ptr(o->z_in);
-  const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) : 0);
+  const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) : 0) +
+                       (bf16 ? (size_t)(m_max + 1) * n * sizeof(__nv_bfloat16) : 0);
   int chunk = batch_size(p, o->nsamples, nslots, m_max, true, extra);
   if (chunk < 1) return GMRF_ERR_OOM;
   cudaStream_t s = p->ws;
@@ -484,7 +498,7 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
   for (int s0 = 0; s0 < o->nsamples; s0 += chunk) {
     const int c = std::min(chunk, o->nsamples - s0);
     LanczosBufs b;
-    CKR(ensure_lanczos(p, c, nslots, m_max, true, b));
+    CKR(ensure_lanczos(p, c, nslots, m_max, true, b, bf16));
     if (o->z_in) {
       const char* src = (const char*)o->z_in + (size_t)s0 * n * es;
       CK(cudaMemcpyAsync(b.W[0], src, (size_t)c * n * es, z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,

@@ -25,6 +25,7 @@ struct Grid {
 struct LanczosBufs {
   void* W[2];          // q of the previous / current step, [nvec][n]
   void* V;             // basis ring
+  __nv_bfloat16* Vb;   // bfloat16 basis [nvec][m_max + 1][n] for the assembly, or null
   VecState* st;        // [nvec]
   double* alpha;       // [nvec][m_max]
   double* beta;        // [nvec][m_max]

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
       if (j > 0) q -= bprev * Vp[i];
       Wout[i] = q;
       Vc[i] = v;
+      if (a.P.vb) vb_store1(vb_at(a.P, s, j, a.n, i), (float)v);
       d.add(v, q);
     }
   }
@@ -381,7 +382,15 @@ __global__ void __launch_bounds__(NT3) k_stencil3d(StencilArgs<T> a) {
         if (STEP) d.add(vc[e], r);
       }
       vstore<T, VX>(Wout + i, qo);
-      if (STEP) vstore<T, VX>(Vc + i, vc);
+      if (STEP) {
+        vstore<T, VX>(Vc + i, vc);
+        if (a.P.vb) {
+          __nv_bfloat16* pb = vb_at(a.P, s, j, n, i);
+          if (VX == 4) vb_store4(pb, (float)vc[0], (float)vc[1 % VX], (float)vc[2 % VX], (float)vc[3 % VX]);
+          else if (VX == 2) vb_store2(pb, (float)vc[0], (float)vc[1 % VX]);
+          else vb_store1(pb, (float)vc[0]);
+        }
+      }
     }
 #pragma unroll
     for (int e = 0; e < VX; ++e) {

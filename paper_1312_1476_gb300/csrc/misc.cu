@@ -112,8 +112,13 @@ __global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>*
 
 // x[s][i] = scale_s * sum_j V[s][j][i] y[s][j], scale_s = ||z_s|| * extra.
 // FP32: y split into float hi + lo, compensated (Neumaier) accumulation.
-template <typename T>
-__global__ void k_assemble(const T* __restrict__ V, int nslots, size_t n, const VecState* st, const double* y,
+// The basis is read in its storage type S (T, or bfloat16 for T = float).
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ double to_f(double v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T, typename S = T>
+__global__ void k_assemble(const S* __restrict__ V, int nslots, size_t n, const VecState* st, const double* y,
                            int y_stride, double extra, T* x) {
   extern __shared__ unsigned char smem_raw[];
   const int s = blockIdx.y;
@@ -129,7 +134,7 @@ __global__ void k_assemble(const T* __restrict__ V, int nslots, size_t n, const 
   }
   const double scale = v.znorm * extra;
   const double* ys = y + (size_t)s * y_stride;
-  const T* Vs = V + (size_t)s * nslots * n;
+  const S* Vs = V + (size_t)s * nslots * n;
   if (sizeof(T) == 4) {
     float* yh = (float*)smem_raw;
     float* yl = yh + m;
@@ -143,7 +148,7 @@ __global__ void k_assemble(const T* __restrict__ V, int nslots, size_t n, const 
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
       float sum = 0.f, comp = 0.f;
       for (int j = 0; j < m; ++j) {
-        const float vv = (float)Vs[(size_t)j * n + i];
+        const float vv = (float)to_f(Vs[(size_t)j * n + i]);
         const float t = __fmaf_rn(vv, yh[j], __fmul_rn(vv, yl[j]));
         const float s2 = __fadd_rn(sum, t);
         comp = __fadd_rn(comp, fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t)
@@ -158,7 +163,7 @@ __global__ void k_assemble(const T* __restrict__ V, int nslots, size_t n, const 
     __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
       double sum = 0.0;
-      for (int j = 0; j < m; ++j) sum = fma((double)Vs[(size_t)j * n + i], yd[j], sum);
+      for (int j = 0; j < m; ++j) sum = fma((double)to_f(Vs[(size_t)j * n + i]), yd[j], sum);
       xo[i] = (T)sum;
     }
   }
@@ -265,6 +270,12 @@ cudaError_t launch_assemble(bool fp64, size_t n, const LanczosBufs& b, const dou
       cudaFuncSetAttribute(k_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_assemble<double><<<grd, 256, sm, s>>>((const double*)b.V, b.nslots, n, b.st, y, y_stride, extra_scale,
                                             (double*)x);
+  } else if (b.Vb) {
+    // bfloat16 basis copy: m_max + 1 slots per vector
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_assemble<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_assemble<float, __nv_bfloat16><<<grd, 256, sm, s>>>(b.Vb, b.m_max + 1, n, b.st, y, y_stride, extra_scale,
+                                                          (float*)x);
   } else {
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(k_assemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

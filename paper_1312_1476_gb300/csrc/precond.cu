@@ -287,6 +287,7 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
       if (MODE == M_FWD_FORM) {
         v = (j == 0) ? v * inv_b : (v - coef * Vp[i]) * inv_b;
         Vc[i] = v;
+        if (a.P.vb) vb_store1(vb_at(a.P, s, j, n, i), (float)v);
       }
       B0[l * PL + x] = v;
     }

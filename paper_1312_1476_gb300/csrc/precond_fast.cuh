@@ -223,6 +223,18 @@ __device__ __forceinline__ void store_row(const float2* p, float* __restrict__ d
       *reinterpret_cast<float4*>(dst + 4 * (lane + 32 * r)) = make_float4(p[2 * r].x, p[2 * r].y, p[2 * r + 1].x, p[2 * r + 1].y);
   }
 }
+template <int KIND, int E>
+__device__ __forceinline__ void store_row_bf16(const float2* p, __nv_bfloat16* dst) {
+  const int lane = threadIdx.x & 31;
+  if (KIND == GMRF_PREC_CIRCULANT) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) vb_store2(dst + 2 * (lane + 32 * r), p[r].x, p[r].y);
+  } else {
+#pragma unroll
+    for (int r = 0; r < E / 2; ++r)
+      vb_store4(dst + 4 * (lane + 32 * r), p[2 * r].x, p[2 * r].y, p[2 * r + 1].x, p[2 * r + 1].y);
+  }
+}
 // row pairs -> packed complex input of the half-length FFT (strided layout)
 template <int KIND, int E>
 __device__ __forceinline__ void pack_row(const float2* p, float2* v) {
@@ -506,6 +518,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
           for (int r = 0; r < E; ++r) p[g * E + r] = scl2(p[g * E + r], inv_b);
         }
         store_row<KIND, E>(p + g * E, Vc + ro);
+        if (a.P.vb) store_row_bf16<KIND, E>(p + g * E, vb_at(a.P, s, j, n, ro));
       }
     }
     rows_forward<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);

@@ -254,7 +254,10 @@ __global__ void __launch_bounds__(NT, kMinBlocks)
           }
           const size_t i = (size_t)gx + (size_t)nx * gy + plane * z;
           *reinterpret_cast<float4*>(Wout + i) = make_float4(qo[0], qo[1], qo[2], qo[3]);
-          if (STEP) *reinterpret_cast<float4*>(Vc + i) = make_float4(vc[0], vc[1], vc[2], vc[3]);
+          if (STEP) {
+            *reinterpret_cast<float4*>(Vc + i) = make_float4(vc[0], vc[1], vc[2], vc[3]);
+            if (a.P.vb) vb_store4(vb_at(a.P, s, j, n, i), vc[0], vc[1], vc[2], vc[3]);
+          }
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {

@@ -48,7 +48,7 @@ class GmrfDesc(ctypes.Structure):
 class GmrfSampleOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("m_max", ctypes.c_int32), ("nsamples", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("z_in", ctypes.c_void_p), ("check_every", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("v_storage", ctypes.c_int32)]
 
 
 class GmrfResultInfo(ctypes.Structure):
@@ -199,11 +199,13 @@ class Problem:
     def __exit__(self, *exc):
         self.close()
 
-    def sample(self, out, nsamples=1, tol=1e-6, m_max=300, seed=2, z=None, check_every=16, raise_on_error=True):
+    def sample(self, out, nsamples=1, tol=1e-6, m_max=300, seed=2, z=None, check_every=16, raise_on_error=True,
+               v_storage="native"):
         """x ~= Q^{-1/2} z into ``out`` ([nsamples][n], host or device); returns
-        (return code, list of SampleInfo)."""
+        (return code, list of SampleInfo).  v_storage "bf16" keeps the basis
+        for the assembly in bfloat16 (FP32 problems; see include/gmrf.h)."""
         o = GmrfSampleOpts(float(tol), int(m_max), int(nsamples), int(seed) & (2 ** 64 - 1),
-                           _ptr(z) if z is not None else None, int(check_every), 0)
+                           _ptr(z) if z is not None else None, int(check_every), VSTORE[v_storage])
         info = (GmrfResultInfo * int(nsamples))()
         rc = _lib.gmrf_sample(self._h, ctypes.byref(o), _ptr(out), info)
         infos = [SampleInfo(i.m_used, i.status, i.err_est) for i in info]
@@ -249,6 +251,7 @@ def rng(kind, nvec, n, seed, out, precision="fp32", stream=None):
         raise GmrfError(rc, "gmrf_rng")
 
 
+VSTORE = {"native": 0, "bf16": 1}
 KERNEL_CLASSES = {"stencil_step": 0, "pre_row_fwd": 1, "pre_col": 2, "pre_row_mid": 3, "pre_row_last": 4,
                   "init": 5, "rng": 6, "tm": 7, "assemble": 8, "pre_apply": 9, "other": 10}
 

@@ -1,5 +1,7 @@
 """GPU parity of gmrf_sample (Algorithm 1; Proposition 1 when preconditioned)
 against the oracle's exact maps, plus the edge cases of the method."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -165,6 +167,49 @@ def test_batch_equals_alone_3d(g):
             _, info_1, X1 = _sample(g, p, Z[s:s + 1], 1e-6, 400, "fp32")
             np.testing.assert_array_equal(X1[0], Xb[s])
             assert info_1[0].m_used == info_b[s].m_used
+
+
+BF16_CASES = [((24, 20), "neumann", "spde_squared", "none"), ((64, 64), "neumann", "spde_squared", "mirror"),
+              ((128, 128), "dirichlet", "spde_squared", "circulant"), ((70, 9, 128), "dirichlet", "shifted_laplacian",
+                                                                       "none"),
+              ((9, 11, 64), "neumann", "shifted_laplacian", "none"), ((5, 6, 33), "periodic", "shifted_laplacian", "none"),
+              ((128, 256), "neumann", "spde_squared", "mirror")]
+
+
+@pytest.mark.parametrize("shape,bc,op,pre", BF16_CASES)
+def test_bf16_basis(g, shape, bc, op, pre):
+    # bfloat16 V_m for the assembly: the iteration is unchanged (same m per
+    # vector), x differs from the FP32-basis result by the bfloat16 rounding of
+    # V_m only (~1e-3 relative), for every kernel that stores v_j
+    n = int(np.prod(shape))
+    k2 = inputs.kappa2_uniform_field(shape, seed=3, lo=0.1, hi=1.0)
+    Z = inputs.gaussian_vectors(3, n, seed=8, dtype=np.float32)
+    with g.Problem(shape, bc, op, kappa2=_dev(k2), precond=pre) as p:
+        x32 = torch.empty(3 * n, dtype=torch.float32, device="cuda")
+        xbf = torch.empty(3 * n, dtype=torch.float32, device="cuda")
+        rc1, i1 = p.sample(x32, nsamples=3, tol=1e-6, m_max=800, z=_dev(Z))
+        rc2, i2 = p.sample(xbf, nsamples=3, tol=1e-6, m_max=800, z=_dev(Z), v_storage="bf16")
+    assert rc1 == g.OK and rc2 == g.OK
+    X32 = x32.cpu().numpy().reshape(3, n)
+    Xbf = xbf.cpu().numpy().reshape(3, n)
+    for s in range(3):
+        assert i1[s].m_used == i2[s].m_used and i1[s].err_est == i2[s].err_est
+        r = _rel(Xbf[s], X32[s].astype(np.float64))
+        assert 1e-5 < r <= 3e-3
+
+
+def test_bf16_basis_rejected_where_unsupported(g):
+    shape = (16, 16)
+    z = inputs.gaussian_vectors(1, 256, seed=1, dtype=np.float64)
+    with g.Problem(shape, "neumann", "shifted_laplacian", kappa2_const=0.3, precision="fp64") as p:
+        x = torch.empty(256, dtype=torch.float64, device="cuda")
+        rc, _ = p.sample(x, nsamples=1, z=_dev(z), v_storage="bf16", raise_on_error=False)
+        assert rc == g.ERR_UNSUPPORTED
+    o = g.GmrfSampleOpts(1e-6, 50, 1, 1, None, 16, 7)
+    with g.Problem(shape, "neumann", "shifted_laplacian", kappa2_const=0.3) as p:
+        x = torch.empty(256, dtype=torch.float32, device="cuda")
+        info = (g.GmrfResultInfo * 1)()
+        assert g.lib().gmrf_sample(p._h, ctypes.byref(o), ctypes.c_void_p(x.data_ptr()), info) == g.ERR_INVALID
 
 
 def test_device_noise_matches_oracle_generator(g):
