@@ -349,6 +349,7 @@ def measure_variants(args, gmrf, torch, flush, peak):
     with gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond="mirror",
                       stream=stream.cuda_stream) as p:
         ns = 256
+        tune512 = p.autotune(ns)
         x = torch.empty(ns * n, dtype=torch.float32, device="cuda")
         p.sample(x, nsamples=ns, tol=TOL, m_max=M_MAX_512, seed=1)
         gmrf.trace_reset()
@@ -360,7 +361,7 @@ def measure_variants(args, gmrf, torch, flush, peak):
             "samples_per_s": ns * 1e3 / ms, "ms_per_call": ms,
             "m_mean": float(np.mean([i.m_used for i in info])), "status": rc,
             "logdets_per_s": 1e3 / mld, "logdet": ld[0], "logdet_std_err": ld[1],
-            "logdet_m_mean": float(np.mean([i.m_used for i in ld[3]]))}
+            "logdet_m_mean": float(np.mean([i.m_used for i in ld[3]])), "autotune": tune512}
 
     # 3-D 256^3 Dirichlet 7-point, kappa^2 ~ U[0.01, 1], 16 samples; m_max capped
     # so that all 16 Lanczos bases (m_max + 3 vectors each) stay resident in HBM
@@ -369,6 +370,7 @@ def measure_variants(args, gmrf, torch, flush, peak):
     ns, m3 = 16, M_MAX_3D
     k3 = torch.from_numpy(inputs.kappa2_uniform_field(shape, seed=KAPPA_SEED)).cuda()
     with gmrf.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=k3, stream=stream.cuda_stream) as p:
+        tune3 = p.autotune(ns)
         x = torch.empty(ns * n, dtype=torch.float32, device="cuda")
         p.sample(x, nsamples=ns, tol=TOL, m_max=m3, seed=1)
         ms, (rc, info) = timed(lambda i: p.sample(x, nsamples=ns, tol=TOL, m_max=m3, seed=40 + i), 3)
@@ -384,7 +386,7 @@ def measure_variants(args, gmrf, torch, flush, peak):
             "workload": "256^3 Dirichlet, Q = 7-point Laplacian + kappa^2 (i.i.d. U[0.01,1]), 16 samples per "
                         "call, tol 1e-6, m_max %d (all bases resident)" % m3,
             "samples_per_s": ns * 1e3 / ms, "ms_per_call": ms,
-            "m_mean": float(np.mean([i.m_used for i in info])), "status": rc,
+            "m_mean": float(np.mean([i.m_used for i in info])), "status": rc, "autotune": tune3,
             "stencil_step": {"kernel": "k_stencil3d_tma (TMA-staged fused step)",
                              "avg_launch_us": st_ms * 1e3 / max(st_t, 1), "launches": st_t,
                              "achieved_GBps": ach, "peak_GBps": peak, "frac": ach / peak,
@@ -412,8 +414,9 @@ def measure_serving(nreq=32):
     """Poisson request stream of the serving mix (2-D SPDE 128^2..1024^2 with
     the mirror preconditioner, 3-D 7-point 64^3..128^3, tau ~ U[0.5, 5], 1-8
     samples or a log det with 16-64 probes, tol 1e-6), served with continuous
-    admission at 0.5x and 1x the measured saturation rate, against one request
-    at a time in FP64 on the same stream."""
+    admission at 0.5x and 1x the measured saturation rate (block width and
+    3-D z chunk from the library's autotuner per grid shape), against one
+    request and one sample at a time in FP64 on the same stream."""
     from paper_1312_1476_gb300 import serve
 
     def stream(rate):
@@ -434,9 +437,9 @@ def measure_serving(nreq=32):
         srv.prepare(reqs)
         _, met = srv.serve(reqs, realtime=True)
         res["rate_%.1fx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
-    base = serve.Server(max_inflight=1, precision="fp64")
+    base = serve.Server(max_inflight=1, precision="fp64", block_width=1)
     reqs = stream(0.5 * sat_rate)
-    base.prepare(reqs)
+    base.prepare(reqs, tune=False)
     base.serve(reqs[:2], realtime=False)
     _, met = base.serve(reqs, realtime=True)
     res["fp64_one_at_a_time_rate_0.5x"] = dict(met, rate_req_per_s=0.5 * sat_rate)

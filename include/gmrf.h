@@ -224,6 +224,40 @@ int gmrf_trace(int32_t op, int32_t kclass, double* total_ms, int64_t* launches, 
 #define GMRF_NOALLOC_SCRATCH_BYTES (32 << 20)
 int gmrf_apply_inv_sqrt_noalloc(gmrf_problem* p, int64_t nvec, const void* v, void* y);
 
+/* Tuning of the batched Lanczos launches (a facility of this library, not
+ * part of the paper's method).
+ *   block_width -- vectors per Lanczos launch (one batch of the SpMM-like
+ *                  step); 0 = as many as fit in free HBM;
+ *   zchunk      -- 3-D FP32 Dirichlet / zero-Neumann grids without a
+ *                  preconditioner: z planes per work item of the TMA-staged
+ *                  stencil step; 0 = the default for the grid; ignored
+ *                  elsewhere.
+ * A zchunk changes how the step's dot products are grouped, so results can
+ * change in the last bits; they stay independent of the batch. */
+typedef struct {
+  int32_t block_width;
+  int32_t zchunk;
+  double vec_steps_per_s; /* gmrf_autotune: measured rate of the chosen configuration */
+  int32_t candidates;     /* gmrf_autotune: configurations timed */
+  int32_t reserved;       /* must be 0 for gmrf_set_tuning */
+} gmrf_tuning;
+
+/* Times short Lanczos runs (8 untimed + 8 timed steps on Rademacher vectors,
+ * CUDA events on the problem's work stream) over the candidate z chunks
+ * (nz, nz/2, ... >= 8 planes) at a block width of min(16, cap), then over
+ * the block widths 1, 2, 4, ... and the largest that fits free HBM
+ * (<= nvec_max), and keeps the smallest block width within 3% of the best
+ * rate.  The choice is stored in the problem (used by later gmrf_sample /
+ * gmrf_logdet calls) and returned in *out.  Synchronises the work stream.
+ * Errors: GMRF_ERR_INVALID (null pointers, nvec_max < 1), GMRF_ERR_OOM,
+ * GMRF_ERR_CUDA. */
+int gmrf_autotune(gmrf_problem* p, int32_t nvec_max, gmrf_tuning* out);
+
+/* Sets the tuning explicitly (e.g. one found by gmrf_autotune on another
+ * problem with the same grid).  GMRF_ERR_INVALID for negative fields or a
+ * non-zero reserved. */
+int gmrf_set_tuning(gmrf_problem* p, const gmrf_tuning* t);
+
 void gmrf_destroy(gmrf_problem* p);
 const char* gmrf_strerror(int code);
 

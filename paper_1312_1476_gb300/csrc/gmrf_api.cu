@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -88,7 +89,7 @@ bool is_device_ptr(const void* p) {
 struct StepGraph {
   cudaGraphExec_t exec = nullptr;
   GraphTrace tr;
-  int nvec = -1, nslots = 0, m_max = 0, c = 0, kernels_per_step = 1;
+  int nvec = -1, nslots = 0, m_max = 0, c = 0, kernels_per_step = 1, zchunk = 0;
   double tol = 0.0;
   const void *W0 = nullptr, *V = nullptr, *Vb = nullptr, *st = nullptr, *S = nullptr, *partials = nullptr;
   bool timed = false;
@@ -119,6 +120,7 @@ struct gmrf_problem {
       stage2, work, Vb;
   VecState* st_host = nullptr;
   int st_host_cap = 0;
+  int tune_bw = 0;  // vectors per Lanczos launch (0: as many as fit)
 };
 
 namespace {
@@ -212,6 +214,11 @@ int batch_size(gmrf_problem* p, int want, int nslots, int m_max, bool need_tm, s
   return (int)c;
 }
 
+// The z chunk is a tunable of the TMA-staged 3-D step only.
+bool tune_zchunk_ok(const gmrf_problem* p) {
+  return p->precond == GMRF_PREC_NONE && stencil3d_tma_eligible(p->g, p->fp64);
+}
+
 int worst_status(const VecState* st, int nvec) {
   int worst = GMRF_OK;
   for (int s = 0; s < nvec; ++s) {
@@ -242,7 +249,7 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   const void* S = p->precond ? p->pre.S : nullptr;
   if (G.exec && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c && G.tol == P.tol &&
       G.W0 == b.W[0] && G.V == b.V && G.Vb == b.Vb && G.st == b.st && G.S == S && G.partials == b.partials &&
-      G.timed == timed)
+      G.timed == timed && G.zchunk == p->g.zchunk)
     return GMRF_OK;
   G.reset();
   cudaStream_t s = p->ws;
@@ -274,6 +281,7 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   G.W0 = b.W[0];
   G.V = b.V;
   G.Vb = b.Vb;
+  G.zchunk = p->g.zchunk;
   G.st = b.st;
   G.S = S;
   G.partials = b.partials;
@@ -491,6 +499,7 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
   const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) : 0) +
                        (bf16 ? (size_t)(m_max + 1) * n * sizeof(__nv_bfloat16) : 0);
   int chunk = batch_size(p, o->nsamples, nslots, m_max, true, extra);
+  if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
   if (chunk < 1) return GMRF_ERR_OOM;
   cudaStream_t s = p->ws;
   CKR(enter(p));
@@ -551,6 +560,7 @@ int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, doub
   const int m_max = o->m_max;
   const bool z_dev = o->probes_in && is_device_ptr(o->probes_in);
   int chunk = batch_size(p, o->nprobes, 2, m_max, false, 0);
+  if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
   if (chunk < 1) return GMRF_ERR_OOM;
   cudaStream_t s = p->ws;
   CKR(enter(p));
@@ -658,6 +668,113 @@ int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t 
     rc = GMRF_ERR_CUDA;
   }
   return rc;
+}
+
+int gmrf_set_tuning(gmrf_problem* p, const gmrf_tuning* t) {
+  if (!p || !t || t->block_width < 0 || t->zchunk < 0 || t->reserved != 0) return GMRF_ERR_INVALID;
+  p->tune_bw = t->block_width;
+  p->g.zchunk = tune_zchunk_ok(p) ? t->zchunk : 0;
+  p->graph.reset();
+  return GMRF_OK;
+}
+
+int gmrf_autotune(gmrf_problem* p, int32_t nvec_max, gmrf_tuning* out) {
+  if (!p || !out || nvec_max < 1) return GMRF_ERR_INVALID;
+  const size_t n = p->g.n, es = esize(p);
+  constexpr int kSteps = 8, kMmax = 64;
+  const size_t extra = p->precond ? precond_extra_bytes(p->pre, es) : 0;
+  int cap = batch_size(p, nvec_max, 2, kMmax, false, extra);
+  if (cap < 1) return GMRF_ERR_OOM;
+  cudaStream_t s = p->ws;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return GMRF_ERR_CUDA;
+  }
+  int ncand = 0;
+  // vector-steps per second of kSteps Lanczos steps (after kSteps untimed
+  // ones) on `bw` Rademacher vectors, with the problem's current tiling
+  auto measure = [&](int bw, double* rate) -> int {
+    LanczosBufs b;
+    CKR(ensure_lanczos(p, bw, 2, kMmax, false, b));
+    CK(launch_rng(1, p->fp64, bw, (int64_t)n, 0x5EEDull, 0, b.W[0], s));
+    CK(launch_lanczos_init(p->fp64, n, b, s));
+    StepParams P{};
+    P.m_max = kMmax;
+    P.nslots = 2;
+    P.tol = 1e-300;  // never met: every vector runs all timed steps
+    P.bd_tol = p->fp64 ? 1e-13 : 1e-6;
+    if (p->precond != GMRF_PREC_NONE) CKR(precond_prepare(p->pre, bw, s));
+    CKR(capture_steps(p, b, P, kSteps));
+    CK(cudaGraphLaunch(p->graph.exec, s));
+    CK(cudaEventRecord(e0, s));
+    CK(cudaGraphLaunch(p->graph.exec, s));
+    CK(cudaEventRecord(e1, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    *rate = ms > 0.f ? (double)bw * kSteps / (ms * 1e-3) : 0.0;
+    ++ncand;
+    return GMRF_OK;
+  };
+  int rc = enter(p);
+  int best_z = 0, best_bw = cap;
+  double best = -1.0;
+  if (rc == GMRF_OK && tune_zchunk_ok(p)) {
+    // z planes per work item of the 3-D step, at a moderate block width
+    const int bw0 = std::min(cap, 16);
+    for (int z = p->g.nz; z >= 8 && rc == GMRF_OK; z /= 2) {
+      p->g.zchunk = z;
+      double r = 0.0;
+      rc = measure(bw0, &r);
+      if (rc == GMRF_OK && r > best) {
+        best = r;
+        best_z = z;
+      }
+    }
+    p->g.zchunk = best_z;
+  }
+  if (rc == GMRF_OK) {
+    // block width: powers of two up to the memory cap, and the cap itself;
+    // the smallest width within 3% of the best rate wins (less memory, less
+    // waiting for a full batch)
+    std::vector<int> cands;
+    for (int w = 1; w < cap; w *= 2) cands.push_back(w);
+    cands.push_back(cap);
+    std::vector<double> rates;
+    for (int w : cands) {
+      double r = 0.0;
+      rc = measure(w, &r);
+      if (rc != GMRF_OK) break;
+      rates.push_back(r);
+    }
+    if (rc == GMRF_OK) {
+      const double top = *std::max_element(rates.begin(), rates.end());
+      for (size_t i = 0; i < cands.size(); ++i)
+        if (rates[i] >= 0.97 * top) {
+          best_bw = cands[i];
+          best = rates[i];
+          break;
+        }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->graph.reset();
+  const int rl = leave(p);
+  if (rc != GMRF_OK) {
+    p->g.zchunk = 0;
+    return rc;
+  }
+  if (rl != GMRF_OK) return rl;
+  p->tune_bw = best_bw;
+  out->block_width = best_bw;
+  out->zchunk = p->g.zchunk;
+  out->vec_steps_per_s = best;
+  out->candidates = ncand;
+  out->reserved = 0;
+  return GMRF_OK;
 }
 
 }  // extern "C"

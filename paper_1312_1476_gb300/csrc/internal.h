@@ -15,8 +15,9 @@ struct Grid {
   int dim;
   int nx, ny, nz;
   size_t n;
-  int bc;   // gmrf_bc
-  int op;   // gmrf_op
+  int bc;      // gmrf_bc
+  int op;      // gmrf_op
+  int zchunk = 0;  // 3-D FP32 stencil step: z planes per work item (0: chosen from the grid)
 };
 
 // Per-batch Lanczos buffers (all device pointers).  Element type T is float
@@ -49,6 +50,13 @@ cudaError_t launch_stencil_step(const Grid& g, bool fp64, const void* kappa2, do
 // y = Q v for nvec vectors (no Lanczos bookkeeping).
 cudaError_t launch_stencil_apply(const Grid& g, bool fp64, const void* kappa2, double kappa2_const,
                                  const void* v, void* y, int nvec, cudaStream_t s);
+
+// stencil3d_tma.cu -------------------------------------------------------------
+// The TMA-staged 3-D 7-point step / apply serves FP32 grids with Dirichlet or
+// zero-Neumann boundaries, nx a multiple of 4 and >= 128.
+bool stencil3d_tma_eligible(const Grid& g, bool fp64);
+// Work items (partial sums) per vector of that kernel.
+int stencil3d_tma_items_per_vector(const Grid& g);
 
 // misc.cu --------------------------------------------------------------------
 cudaError_t launch_rng(int kind, bool fp64, int64_t nvec, int64_t n, uint64_t seed, int64_t soff, void* out,

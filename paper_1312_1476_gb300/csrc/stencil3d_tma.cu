@@ -297,6 +297,7 @@ Items make_items(const Grid& g, int nvec) {
   int c = 1;
   while (it.ntx * it.nty * c < 3 * 152 && g.nz / (2 * c) >= 32) c *= 2;
   it.zper = (g.nz + c - 1) / c;
+  if (g.zchunk > 0) it.zper = g.zchunk < g.nz ? g.zchunk : g.nz;  // tuned
   it.nzc = (g.nz + it.zper - 1) / it.zper;
   it.per_vec = it.ntx * it.nty * it.nzc;
   it.total = it.per_vec * nvec;

@@ -33,13 +33,9 @@ struct StencilArgs {
 
 struct Grid;
 
-// stencil3d_tma.cu: the TMA-staged 3-D 7-point step / apply (FP32, Dirichlet or
-// zero-Neumann, nx a multiple of 4 and >= 128).
-bool stencil3d_tma_eligible(const Grid& g, bool fp64);
+// stencil3d_tma.cu (eligibility and item counts are declared in internal.h)
 // 16-byte alignment of the vector and coefficient pointers the kernel maps.
 bool stencil3d_tma_pointers_ok(const void* win, const void* wout, const float* kappa2);
-// Work items (partial sums) per vector of the TMA kernel.
-int stencil3d_tma_items_per_vector(const Grid& g);
 // step = true: fused Lanczos step on a.W0/W1/V; false: a.Wout = Q a.Win.
 cudaError_t launch_stencil3d_tma(const Grid& g, const StencilArgs<float>& a, int nvec, bool step, cudaStream_t s);
 

@@ -61,6 +61,11 @@ class GmrfLogdetOpts(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class GmrfTuning(ctypes.Structure):
+    _fields_ = [("block_width", ctypes.c_int32), ("zchunk", ctypes.c_int32), ("vec_steps_per_s", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libgmrf.so is not built; run paper_1312_1476_gb300._build.build() "
@@ -79,6 +84,8 @@ def _load():
         "gmrf_trace": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "gmrf_apply_inv_sqrt_noalloc": (ctypes.c_int, [P, ctypes.c_int64, P, P]),
+        "gmrf_autotune": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(GmrfTuning)]),
+        "gmrf_set_tuning": (ctypes.c_int, [P, ctypes.POINTER(GmrfTuning)]),
         "gmrf_destroy": (None, [P]),
         "gmrf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -235,6 +242,23 @@ class Problem:
         rc = _lib.gmrf_apply_inv_sqrt_noalloc(self._h, int(nvec), _ptr(v), _ptr(y))
         if rc != OK:
             raise GmrfError(rc, "gmrf_apply_inv_sqrt_noalloc")
+
+    def autotune(self, nvec_max):
+        """Times candidate block widths (and 3-D z chunks) and keeps the best
+        for later calls; returns the choice as a dict."""
+        t = GmrfTuning()
+        rc = _lib.gmrf_autotune(self._h, int(nvec_max), ctypes.byref(t))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_autotune")
+        return {"block_width": t.block_width, "zchunk": t.zchunk, "vec_steps_per_s": t.vec_steps_per_s,
+                "candidates": t.candidates}
+
+    def set_tuning(self, block_width=0, zchunk=0):
+        """Explicit tuning (0 = library default for either field)."""
+        t = GmrfTuning(int(block_width), int(zchunk), 0.0, 0, 0)
+        rc = _lib.gmrf_set_tuning(self._h, ctypes.byref(t))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_set_tuning")
 
     def apply(self, which, v, y, nvec=1):
         """which 0: y = Q v; 1: y = A v (preconditioned operator); 2: y = M^{-1/2} v."""

@@ -105,7 +105,7 @@ class Server:
     M_MAX_2D = 300
     M_MAX_3D = 300
 
-    def __init__(self, mem_budget=None, max_inflight=16, precision="fp32", chunk_bytes=8 << 30):
+    def __init__(self, mem_budget=None, max_inflight=16, precision="fp32", chunk_bytes=8 << 30, block_width=None):
         import torch
         from . import gmrf
         self.torch = torch
@@ -116,6 +116,8 @@ class Server:
         self.precision = precision
         self.chunk_bytes = chunk_bytes
         self.fields = FieldPool(torch)
+        self.tuning = {}   # grid shape -> block width / z chunk from the library's autotuner
+        self.block_width = block_width  # fixed vectors per launch (e.g. 1: one sample at a time)
         self.used = 0
         self.cv = threading.Condition()
 
@@ -135,7 +137,8 @@ class Server:
 
     def chunk(self, req):
         per = self.vec_bytes(req)
-        return max(1, min(req.count, self.chunk_bytes // per))
+        c = max(1, min(req.count, self.chunk_bytes // per))
+        return min(c, self.block_width) if self.block_width else c
 
     def need(self, req):
         return self.chunk(req) * self.vec_bytes(req) + 8 * int(np.prod(req.shape))
@@ -147,12 +150,12 @@ class Server:
         n = int(np.prod(shape))
         k2 = self.fields.get(shape, req.field_id)
         stream = torch.cuda.Stream()
-        if len(shape) == 2:
-            prob = g.Problem(shape, "neumann", "spde_squared", kappa2=k2, tau=req.tau, precond="mirror",
-                             precision=self.precision, stream=stream.cuda_stream)
-        else:
-            prob = g.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=k2, tau=req.tau,
-                             precision=self.precision, stream=stream.cuda_stream)
+        prob = self._problem(shape, k2, req.tau, stream)
+        if self.block_width:
+            prob.set_tuning(block_width=self.block_width)
+        elif shape in self.tuning:
+            t = self.tuning[shape]
+            prob.set_tuning(block_width=t["block_width"], zchunk=t["zchunk"])
         dt = torch.float64 if self.precision == "fp64" else torch.float32
         res = Result(req.rid, req.kind, shape, req.count, 0.0, 0.0, 0.0, [], 0)
         with prob:
@@ -179,11 +182,32 @@ class Server:
         res.latency_ms = (end - t0 - req.arrival) * 1e3
         return res
 
-    def prepare(self, requests):
+    def _problem(self, shape, k2, tau, stream):
+        g = self.g
+        if len(shape) == 2:
+            return g.Problem(shape, "neumann", "spde_squared", kappa2=k2, tau=tau, precond="mirror",
+                             precision=self.precision, stream=stream.cuda_stream)
+        return g.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=k2, tau=tau,
+                         precision=self.precision, stream=stream.cuda_stream)
+
+    def prepare(self, requests, tune=True):
         """Generates the coefficient fields of `requests` (their inputs) and
-        the library's per-process state before serving starts."""
+        the library's per-process state before serving starts; with `tune`,
+        runs the library's autotuner once per grid shape of the stream (block
+        width up to the largest request count of that shape, 3-D z chunk)."""
         for r in requests:
             self.fields.get(r.shape, r.field_id)
+        if tune:
+            widest = {}
+            for r in requests:
+                widest[r.shape] = max(widest.get(r.shape, 1), r.count)
+            for shape in sorted(widest, key=lambda sh: (len(sh), sh)):
+                if shape in self.tuning:
+                    continue
+                stream = self.torch.cuda.Stream()
+                k2 = self.fields.get(shape, 0)
+                with self._problem(shape, k2, 1.0, stream) as prob:
+                    self.tuning[shape] = prob.autotune(widest[shape])
         self.torch.cuda.synchronize()
 
     def serve(self, requests, realtime=True):

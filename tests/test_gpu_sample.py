@@ -212,6 +212,35 @@ def test_bf16_basis_rejected_where_unsupported(g):
         assert g.lib().gmrf_sample(p._h, ctypes.byref(o), ctypes.c_void_p(x.data_ptr()), info) == g.ERR_INVALID
 
 
+def test_autotune_and_explicit_tuning(g):
+    # the tuner picks a block width and (3-D TMA grids) a z chunk; a tuned
+    # problem still matches the oracle, and the block width (chunking of the
+    # batch) does not change any vector's result
+    shape = (96, 8, 128)
+    n = int(np.prod(shape))
+    Z = inputs.gaussian_vectors(5, n, seed=31, dtype=np.float32)
+    with g.Problem(shape, "dirichlet", "shifted_laplacian", kappa2_const=0.25) as p:
+        t = p.autotune(8)
+        assert 1 <= t["block_width"] <= 8 and t["candidates"] >= 4 and t["vec_steps_per_s"] > 0
+        assert t["zchunk"] in (96, 48, 24, 12)
+        rc, info, X = _sample(g, p, Z, 3e-7, 300, "fp32")
+        assert rc == g.OK
+        for s in range(5):
+            xe = exact.sample_spectral(shape, "dirichlet", "shifted_laplacian", 0.25, 1.0, Z[s].astype(np.float64))
+            assert _rel(X[s], xe) <= 1e-6
+        for zc, bw in ((12, 2), (96, 0)):
+            p.set_tuning(block_width=bw, zchunk=zc)
+            _, ia, Xa = _sample(g, p, Z, 3e-7, 300, "fp32")
+            p.set_tuning(block_width=0, zchunk=zc)
+            _, ib, Xb = _sample(g, p, Z, 3e-7, 300, "fp32")
+            np.testing.assert_array_equal(Xa, Xb)
+            for s in range(5):
+                assert _rel(Xa[s], X[s].astype(np.float64)) <= 1e-6
+    with pytest.raises(g.GmrfError):
+        with g.Problem((16, 16), "neumann", "shifted_laplacian", kappa2_const=0.3) as p:
+            p.set_tuning(block_width=-1)
+
+
 def test_device_noise_matches_oracle_generator(g):
     # z from the device Philox stream (no z_in) equals the oracle's generator
     shape = (32, 32)

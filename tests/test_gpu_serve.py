@@ -19,15 +19,21 @@ def _mix():
     return reqs
 
 
-def test_alone_equals_mix():
+@pytest.mark.parametrize("tune", [False, True])
+def test_alone_equals_mix(tune):
     torch.cuda.synchronize()
     srv = serve.Server(max_inflight=8)
     reqs = _mix()
+    srv.prepare(reqs, tune=tune)
+    if tune:
+        assert srv.tuning and all(t["block_width"] >= 1 for t in srv.tuning.values())
     mixed, metrics = srv.serve(reqs, realtime=False)
     assert metrics["requests"] == len(reqs)
     assert all(r.status in (0, -3) for r in mixed)
     for target in (0, 5, 11):
-        alone, _ = serve.Server(max_inflight=1).serve([reqs[target]], realtime=False)
+        one = serve.Server(max_inflight=1)
+        one.tuning = dict(srv.tuning)
+        alone, _ = one.serve([reqs[target]], realtime=False)
         a, b = alone[0], mixed[target]
         if a.kind == "sample":
             assert torch.equal(a.x, b.x)
