@@ -355,13 +355,21 @@ def measure_variants(args, gmrf, torch, flush, peak):
         gmrf.trace_reset()
         ms, (rc, info) = timed(lambda i: p.sample(x, nsamples=ns, tol=TOL, m_max=M_MAX_512, seed=20 + i), 3)
         mld, ld = timed(lambda i: p.logdet(nprobes=64, tol=TOL, m_max=M_MAX_512, seed=30 + i), 3)
+        # coloured Hutchinson (Section 6.1) at the same number of quadratures
+        # (about 64): draws x (p + 1)^2 colour classes
+        coloured = {}
+        for pd, nd in ((1, 16), (2, 7), (3, 4)):
+            mc, lc = timed(lambda i: p.logdet(nprobes=nd, tol=TOL, m_max=M_MAX_512, seed=30 + i, colour_dist=pd), 2)
+            coloured["p%d" % pd] = {"draws": nd, "quadratures": nd * (pd + 1) ** 2, "logdet": lc[0],
+                                    "std_err": lc[1], "logdets_per_s": 1e3 / mc}
         out["batched_512"] = {
             "workload": "512x512 SPDE (same recipe, ell 64), mirror M, 256 samples per call (m_max %d, one "
                         "batch); log det with 64 Rademacher probes per call" % M_MAX_512,
             "samples_per_s": ns * 1e3 / ms, "ms_per_call": ms,
             "m_mean": float(np.mean([i.m_used for i in info])), "status": rc,
             "logdets_per_s": 1e3 / mld, "logdet": ld[0], "logdet_std_err": ld[1],
-            "logdet_m_mean": float(np.mean([i.m_used for i in ld[3]])), "autotune": tune512}
+            "logdet_m_mean": float(np.mean([i.m_used for i in ld[3]])), "autotune": tune512,
+            "logdet_coloured": coloured}
 
     # 3-D 256^3 Dirichlet 7-point, kappa^2 ~ U[0.01, 1], 16 samples; m_max capped
     # so that all 16 Lanczos bases (m_max + 3 vectors each) stay resident in HBM

@@ -138,9 +138,11 @@ typedef struct {
   int32_t m_max;
   int32_t nprobes;     /* N >= 1 (>= 2 for a standard error) */
   uint64_t seed;       /* Philox key of the Rademacher probes when probes_in == NULL */
-  const void* probes_in; /* optional [nprobes][n] probes (float / double by precision) */
+  const void* probes_in; /* optional probes (float / double by precision): [nprobes * ncolours][n] */
   int32_t check_every;
-  int32_t reserved;
+  int32_t colour_dist;  /* p >= 0: coloured Hutchinson estimator (Section 6.1) over the distance-p
+                           lattice colouring colour = coords mod (p + 1), ncolours = (p + 1)^dim;
+                           0 = plain Hutchinson (one colour) */
 } gmrf_logdet_opts;
 
 /* Section 2 / 5.1: build a problem.  Validates the descriptor, copies kappa2,
@@ -156,11 +158,17 @@ int gmrf_size(const gmrf_problem* p, int64_t* n);
  * info [nsamples] (host, may be NULL).  Returns the worst per-vector status. */
 int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* opts, void* x_out, gmrf_result_info* info);
 
-/* Section 6 (+ Section 6.2 when preconditioned): *logdet = mean_i q_i +
- * log det M + n log tau, *std_err = sd(q_i)/sqrt(N) (NaN for N == 1),
- * q_out [nprobes] (host, may be NULL) = the per-probe terms
- * ||v_i||^2 e_1^T log(T_m) e_1 of the (preconditioned) operator, info as for
- * gmrf_sample.  logdet and std_err are host pointers. */
+/* Section 6 (+ Section 6.2 when preconditioned): N = nprobes Rademacher
+ * draws v_d.  With colour_dist = p > 0 (Section 6.1) each draw is split over
+ * the ncolours colour classes c, v_dc = v_d on c and 0 elsewhere (the
+ * device stream of draw d is the one of plain probe d), so the library runs
+ * N * ncolours Lanczos quadratures, ordered draw-major.  With
+ * Q_d = sum_c q_dc (Q_d = q_d for p = 0):
+ * *logdet = mean_d Q_d + log det M + n log tau, *std_err = sd(Q_d)/sqrt(N)
+ * (NaN for N == 1), q_out [N * ncolours] (host, may be NULL) = the terms
+ * q_dc = ||v_dc||^2 e_1^T log(T_m) e_1 of the (preconditioned) operator,
+ * info [N * ncolours] as for gmrf_sample.  logdet and std_err are host
+ * pointers.  GMRF_ERR_INVALID for colour_dist < 0 or > 15. */
 int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* opts, double* logdet, double* std_err,
                 double* q_out, gmrf_result_info* info);
 

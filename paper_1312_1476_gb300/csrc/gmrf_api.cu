@@ -554,27 +554,38 @@ int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, doub
                 gmrf_result_info* info) {
   if (!p || !o || !logdet || !std_err) return GMRF_ERR_INVALID;
   if (!(o->tol > 0.0) || !std::isfinite(o->tol) || o->m_max < 1 || o->m_max > 8192 || o->nprobes < 1 ||
-      o->reserved != 0)
+      o->colour_dist < 0 || o->colour_dist > 15)
     return GMRF_ERR_INVALID;
   const size_t n = p->g.n, es = esize(p);
   const int m_max = o->m_max;
   const bool z_dev = o->probes_in && is_device_ptr(o->probes_in);
-  int chunk = batch_size(p, o->nprobes, 2, m_max, false, 0);
+  // coloured estimator (Section 6.1): ncol probe vectors per draw
+  const int P = o->colour_dist + 1;
+  int ncol = 1;
+  for (int d = 0; d < p->g.dim; ++d) ncol *= P;
+  const int64_t nq64 = (int64_t)o->nprobes * ncol;
+  if (nq64 > (1 << 24)) return GMRF_ERR_INVALID;
+  const int nq = (int)nq64;
+  int chunk = batch_size(p, nq, 2, m_max, false, 0);
   if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
   if (chunk < 1) return GMRF_ERR_OOM;
   cudaStream_t s = p->ws;
   CKR(enter(p));
-  CKR(ensure(p->stage2, sizeof(double) * (o->nprobes + 2), p->ws));
+  CKR(ensure(p->stage2, sizeof(double) * (nq + 2), p->ws));
   double* qall = (double*)p->stage2.p;
-  std::vector<VecState> all((size_t)o->nprobes);
-  for (int s0 = 0; s0 < o->nprobes; s0 += chunk) {
-    const int c = std::min(chunk, o->nprobes - s0);
+  std::vector<VecState> all((size_t)nq);
+  for (int s0 = 0; s0 < nq; s0 += chunk) {
+    const int c = std::min(chunk, nq - s0);
     LanczosBufs b;
     CKR(ensure_lanczos(p, c, 2, m_max, false, b));
     if (o->probes_in) {
       const char* src = (const char*)o->probes_in + (size_t)s0 * n * es;
       CK(cudaMemcpyAsync(b.W[0], src, (size_t)c * n * es, z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          s));
+    } else if (ncol > 1) {
+      CK(traced(KC_RNG, s, 1, [&] {
+        return launch_rng_coloured(p->fp64, c, (int64_t)n, o->seed, s0, p->g.nx, p->g.ny, P, ncol, b.W[0], s);
+      }));
     } else {
       CK(traced(KC_RNG, s, 1, [&] { return launch_rng(1, p->fp64, c, (int64_t)n, o->seed, s0, b.W[0], s); }));
     }
@@ -586,17 +597,17 @@ int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, doub
   }
   // log det Q = mean q_i + log det M(tau-free) + n log tau   (Section 6.2, plus sign)
   const double shift = p->logdet_M + (double)n * std::log(p->tau);
-  CK(traced(KC_TM, s, 1, [&] { return launch_logdet_reduce(qall, o->nprobes, shift, qall + o->nprobes, s); }));
+  CK(traced(KC_TM, s, 1, [&] { return launch_logdet_reduce(qall, nq, ncol, shift, qall + nq, s); }));
   double res[2];
-  CK(cudaMemcpyAsync(res, qall + o->nprobes, sizeof(res), cudaMemcpyDeviceToHost, s));
-  if (q_out) CK(cudaMemcpyAsync(q_out, qall, sizeof(double) * o->nprobes, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(res, qall + nq, sizeof(res), cudaMemcpyDeviceToHost, s));
+  if (q_out) CK(cudaMemcpyAsync(q_out, qall, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   trace_collect();
   CKR(leave(p));
   *logdet = res[0];
   *std_err = res[1];
-  fill_info(all.data(), o->nprobes, info);
-  return worst_status(all.data(), o->nprobes);
+  fill_info(all.data(), nq, info);
+  return worst_status(all.data(), nq);
 }
 
 int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void* y) {

@@ -61,6 +61,11 @@ int stencil3d_tma_items_per_vector(const Grid& g);
 // misc.cu --------------------------------------------------------------------
 cudaError_t launch_rng(int kind, bool fp64, int64_t nvec, int64_t n, uint64_t seed, int64_t soff, void* out,
                        cudaStream_t s);
+// Coloured Rademacher probes of the distance-(P-1) lattice colouring (ncol
+// colours): vector soff + s of the output is draw (soff + s) / ncol restricted
+// to colour (soff + s) % ncol.
+cudaError_t launch_rng_coloured(bool fp64, int64_t nvec, int64_t n, uint64_t seed, int64_t soff, int nx, int ny,
+                                int P, int ncol, void* out, cudaStream_t s);
 // out4[0] = #(kappa2 < 0 or not finite), [1] = #zeros, [2] = sum log kappa2 over positives.
 // out4 must have kFieldStatsBytes of device memory (results + per-block parts).
 constexpr size_t kFieldStatsBytes = 4 * sizeof(double) + 256 * sizeof(Dots<float>);
@@ -88,6 +93,8 @@ cudaError_t launch_tm_inv_sqrt(const LanczosBufs& b, bool fp64, TmNodes* nodes, 
 // q[s] = ||v_s||^2 e_1^T log(T_m) e_1 (Gauss quadrature, rational form).
 cudaError_t launch_tm_log(const LanczosBufs& b, bool fp64, TmNodes* nodes, double* q, cudaStream_t s);
 // out[0] = mean(q) + shift, out[1] = sd(q)/sqrt(N) (one block).
-cudaError_t launch_logdet_reduce(const double* q, int nq, double shift, double* out, cudaStream_t s);
+// out[0] = mean over draws of the sums of `group` consecutive q + shift,
+// out[1] = standard error of that mean.
+cudaError_t launch_logdet_reduce(const double* q, int nq, int group, double shift, double* out, cudaStream_t s);
 
 }  // namespace gmrf

@@ -78,6 +78,36 @@ __global__ void k_rng_rademacher(T* out, int64_t nvec, int64_t n, uint32_t k0, u
   }
 }
 
+// Coloured Rademacher probes (Section 6.1): probe k = d * ncol + c is the
+// Rademacher vector of draw d (the stream of k_rng_rademacher for vector d)
+// restricted to colour class c of the distance-p lattice colouring
+// colour(x, y, z) = ((z mod P) P + (y mod P)) P + (x mod P), P = p + 1.
+template <typename T>
+__global__ void k_rng_coloured(T* out, int64_t nvec, int64_t n, uint32_t k0, uint32_t k1, int64_t soff, int nx,
+                               int ny, int P, int ncol) {
+  const int64_t nw = (n + 31) / 32;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nvec * nw;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx / nw, w = idx - s * nw;
+    const int64_t k = s + soff;
+    const int64_t d = k / ncol;
+    const int c = (int)(k - d * ncol);
+    uint32_t ctr[4] = {(uint32_t)(w / 4), (uint32_t)d, 1u, 0u};
+    philox4x32_10(ctr, k0, k1);
+    const uint32_t word = ctr[w & 3];
+    T* o = out + s * n + 32 * w;
+    for (int b = 0; b < 32 && 32 * w + b < n; ++b) {
+      const int64_t i = 32 * w + b;
+      const int64_t row = i / nx;
+      const int x = (int)(i - row * nx);
+      const int y = (int)(row % ny);
+      const int z = (int)(row / ny);
+      const int col = ((z % P) * P + (y % P)) * P + (x % P);
+      o[b] = col != c ? (T)0 : (((word >> b) & 1u) ? (T)1 : (T)-1);
+    }
+  }
+}
+
 // ||z|| per vector and state reset.  grid (nblk, nvec).
 template <typename T>
 __global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>* partials, unsigned* counters) {
@@ -238,6 +268,15 @@ cudaError_t launch_rng(int kind, bool fp64, int64_t nvec, int64_t n, uint64_t se
     const int grid = grid_for((size_t)nvec * ((n + 3) / 4), 256);
     k_rng_words<<<grid, 256, 0, s>>>((uint32_t*)out, nvec, n, k0, k1, soff);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rng_coloured(bool fp64, int64_t nvec, int64_t n, uint64_t seed, int64_t soff, int nx, int ny,
+                                int P, int ncol, void* out, cudaStream_t s) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int grid = grid_for((size_t)nvec * ((n + 31) / 32), 256);
+  if (fp64) k_rng_coloured<double><<<grid, 256, 0, s>>>((double*)out, nvec, n, k0, k1, soff, nx, ny, P, ncol);
+  else k_rng_coloured<float><<<grid, 256, 0, s>>>((float*)out, nvec, n, k0, k1, soff, nx, ny, P, ncol);
   return cudaGetLastError();
 }
 

@@ -185,22 +185,34 @@ __global__ void k_log(const VecState* st, const double* alpha, const double* bet
   if (threadIdx.x == 0) q[s] = v.znorm * v.znorm * acc.v;
 }
 
-__global__ void k_logdet_reduce(const double* q, int nq, double shift, double* out) {
+// Estimate and standard error over ng = nq / group draws, draw d being the sum
+// of q[d * group .. d * group + group - 1] (group > 1: the colour classes of
+// the coloured estimator, Section 6.1).
+__global__ void k_logdet_reduce(const double* q, int nq, int group, double shift, double* out) {
   __shared__ DSum red[8];
+  const int ng = nq / group;
   DSum s1;
   s1.zero();
-  for (int i = threadIdx.x; i < nq; i += blockDim.x) s1.v += q[i];
+  for (int d = threadIdx.x; d < ng; d += blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < group; ++c) t += q[(size_t)d * group + c];
+    s1.v += t;
+  }
   s1 = block_reduce(s1, red);
   __shared__ double mean;
-  if (threadIdx.x == 0) mean = s1.v / nq;
+  if (threadIdx.x == 0) mean = s1.v / ng;
   __syncthreads();
   DSum s2;
   s2.zero();
-  for (int i = threadIdx.x; i < nq; i += blockDim.x) s2.v += (q[i] - mean) * (q[i] - mean);
+  for (int d = threadIdx.x; d < ng; d += blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < group; ++c) t += q[(size_t)d * group + c];
+    s2.v += (t - mean) * (t - mean);
+  }
   s2 = block_reduce(s2, red);
   if (threadIdx.x == 0) {
     out[0] = mean + shift;
-    out[1] = nq > 1 ? sqrt(s2.v / (nq - 1) / nq) : NAN;
+    out[1] = ng > 1 ? sqrt(s2.v / (ng - 1) / ng) : NAN;
   }
 }
 
@@ -224,8 +236,8 @@ cudaError_t launch_tm_log(const LanczosBufs& b, bool fp64, TmNodes* nodes, doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_logdet_reduce(const double* q, int nq, double shift, double* out, cudaStream_t s) {
-  k_logdet_reduce<<<1, 256, 0, s>>>(q, nq, shift, out);
+cudaError_t launch_logdet_reduce(const double* q, int nq, int group, double shift, double* out, cudaStream_t s) {
+  k_logdet_reduce<<<1, 256, 0, s>>>(q, nq, group, shift, out);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ class GmrfResultInfo(ctypes.Structure):
 class GmrfLogdetOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("m_max", ctypes.c_int32), ("nprobes", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("probes_in", ctypes.c_void_p), ("check_every", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("colour_dist", ctypes.c_int32)]
 
 
 class GmrfTuning(ctypes.Structure):
@@ -220,15 +220,19 @@ class Problem:
             raise GmrfError(rc, "gmrf_sample")
         return rc, infos
 
-    def logdet(self, nprobes=16, tol=1e-6, m_max=300, seed=3, probes=None, check_every=16, raise_on_error=True):
+    def logdet(self, nprobes=16, tol=1e-6, m_max=300, seed=3, probes=None, check_every=16, raise_on_error=True,
+               colour_dist=0):
         """Hutchinson / Lanczos-quadrature log det Q; returns
-        (logdet, std_err, q_i array, list of SampleInfo, return code)."""
+        (logdet, std_err, q array, list of SampleInfo, return code).  With
+        colour_dist p > 0 the coloured estimator runs (p + 1)^dim quadratures
+        per draw; q and the infos then have nprobes * (p + 1)^dim entries."""
         o = GmrfLogdetOpts(float(tol), int(m_max), int(nprobes), int(seed) & (2 ** 64 - 1),
-                           _ptr(probes) if probes is not None else None, int(check_every), 0)
+                           _ptr(probes) if probes is not None else None, int(check_every), int(colour_dist))
         ld = ctypes.c_double()
         se = ctypes.c_double()
-        q = np.zeros(int(nprobes), dtype=np.float64)
-        info = (GmrfResultInfo * int(nprobes))()
+        nq = int(nprobes) * (int(colour_dist) + 1) ** len(self.shape)
+        q = np.zeros(nq, dtype=np.float64)
+        info = (GmrfResultInfo * nq)()
         rc = _lib.gmrf_logdet(self._h, ctypes.byref(o), ctypes.byref(ld), ctypes.byref(se),
                               ctypes.c_void_p(q.ctypes.data), info)
         infos = [SampleInfo(i.m_used, i.status, i.err_est) for i in info]

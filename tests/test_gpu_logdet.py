@@ -77,3 +77,43 @@ def test_device_probes_unbiased(g):
     V = philox.rademacher(2000, 64, 11)
     np.testing.assert_allclose(q, exact.quadform_log_dense(Q, V), rtol=1e-7, atol=1e-7)
     assert abs(ld - exact.logdet_cholesky(Q)) <= 4 * se
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("p_dist", [1, 2])
+def test_coloured_estimator_matches_oracle(g, precision, p_dist):
+    # coloured Hutchinson (Section 6.1) with device probes: each colour-class
+    # quadrature against the oracle's estimator on its restated Philox draws
+    from oracle import philox
+    shape = (24, 24)
+    n = 576
+    Q = stencil.precision_matrix(shape, "periodic", "shifted_laplacian", 0.3, 1.0)
+    ndraw, seed = 3, 4242
+    with g.Problem(shape, "periodic", "shifted_laplacian", kappa2_const=0.3, precision=precision) as p:
+        tol = 1e-10 if precision == "fp64" else 1e-6
+        ld, se, q, info, rc = p.logdet(nprobes=ndraw, tol=tol, m_max=n, seed=seed, colour_dist=p_dist)
+    assert rc == g.OK
+    ncol = (p_dist + 1) ** 2
+    assert len(q) == ndraw * ncol
+    draws = philox.rademacher(ndraw, n, seed).astype(np.float64)
+    est, se_o, qo = olz.coloured_hutchinson_logdet(lambda v: Q @ v, shape, p_dist, draws, 1e-11, n, reorth=True)
+    rtol = 1e-8 if precision == "fp64" else 2e-6
+    np.testing.assert_allclose(q.reshape(ndraw, ncol), qo, rtol=rtol, atol=rtol * np.abs(qo).max())
+    assert abs(ld - est) <= rtol * abs(est)
+    assert abs(se - se_o) <= 1e-6 * se_o + rtol * abs(est)
+
+
+def test_coloured_estimator_unbiased_and_lower_variance(g):
+    # same device draws, plain vs coloured (p = 1, 2): both within 4 standard
+    # errors of the exact log det, and the coloured one has the smaller spread
+    shape = (32, 32)
+    Q = stencil.precision_matrix(shape, "periodic", "shifted_laplacian", 0.2, 1.0)
+    ld_exact = exact.logdet_spectral(shape, "periodic", "shifted_laplacian", 0.2, 1.0)
+    ses = []
+    with g.Problem(shape, "periodic", "shifted_laplacian", kappa2_const=0.2, precision="fp64") as p:
+        for pd in (0, 1, 2):
+            ld, se, q, info, rc = p.logdet(nprobes=200, tol=1e-9, m_max=400, seed=99, colour_dist=pd)
+            assert rc == g.OK
+            assert abs(ld - ld_exact) <= 4 * se
+            ses.append(se)
+    assert ses[1] < 0.7 * ses[0] and ses[2] < ses[1]

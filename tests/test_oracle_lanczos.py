@@ -169,3 +169,41 @@ def test_coloured_masks_partition_and_distance(p):
         d = np.abs(ys[:, None] - ys[None, :]) + np.abs(xs[:, None] - xs[None, :])
         np.fill_diagonal(d, 10 ** 6)
         assert d.min() > p
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_coloured_estimator_exact_mean_and_variance(p):
+    # all 2^9 sign patterns on a 3 x 3 grid: the coloured estimator
+    # sum_c v_c^T log(Q) v_c has mean log det Q exactly and variance
+    # 2 sum_c sum_{i != j in c} B_ij^2, B = log Q (Section 6.1 with the
+    # factor 2 of Rademacher quadratic forms)
+    shape = (3, 3)
+    Q = stencil.precision_matrix(shape, "neumann", "spde_squared", 0.7, 1.3).toarray()
+    ld = exact.logdet_cholesky(Q)
+    masks = lanczos.coloured_probe_masks(shape, p)
+    signs = np.array([[1.0 if (k >> b) & 1 else -1.0 for b in range(9)] for k in range(2 ** 9)])
+    vals = np.zeros(len(signs))
+    for mk in masks:
+        vals += exact.quadform_log_dense(Q, np.where(mk[None, :], signs, 0.0))
+    assert abs(vals.mean() - ld) <= 1e-10 * abs(ld)
+    lam, U = exact.dense_eigh(Q)
+    B = (U * np.log(lam)) @ U.T
+    var = 0.0
+    for mk in masks:
+        Bc = B[np.ix_(mk, mk)]
+        var += 2 * (np.sum(Bc ** 2) - np.sum(np.diag(Bc) ** 2))
+    assert abs(vals.var() - var) <= 1e-10 * max(var, 1e-300) + 1e-14
+
+
+def test_coloured_lanczos_quadrature_matches_dense():
+    # the Lanczos-quadrature coloured estimator against dense quadratic forms
+    shape = (8, 8)
+    Q = stencil.precision_matrix(shape, "periodic", "shifted_laplacian", 0.3, 1.0)
+    draws = inputs.rademacher_vectors(3, 64, seed=21, dtype=np.float64)
+    est, se, q = lanczos.coloured_hutchinson_logdet(lambda v: Q @ v, shape, 1, draws, 1e-12, 64, reorth=True)
+    masks = lanczos.coloured_probe_masks(shape, 1)
+    for d in range(3):
+        for c, mk in enumerate(masks):
+            ref = exact.quadform_log_dense(Q.toarray(), np.where(mk, draws[d], 0.0)[None, :])[0]
+            assert abs(q[d, c] - ref) <= 1e-9 * abs(ref) + 1e-9
+    assert abs(est - q.sum(axis=1).mean()) <= 1e-12 * abs(est)
