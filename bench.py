@@ -122,6 +122,20 @@ def algorithmic_bytes(kclass, n, nx, ny, kind):
     }.get(kclass)
 
 
+KERNEL_SOURCES = ("common.cuh", "fft.cuh", "precond.h", "precond_fast.h", "precond_fast.cuh",
+                  "precond_fast_mirror.cu", "precond_fast_circ.cu", "precond.cu")
+
+
+def kernel_sources_sha1():
+    """SHA-1 over the sources of the preconditioned step kernels (the traffic
+    figures in profiles/ncu_traffic.json are valid only for this source)."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1312_1476_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_from_profile(kclass):
     """DRAM bytes per launch from the committed ncu summary, if it matches the
     current kernel source; else None."""
@@ -130,9 +144,7 @@ def traffic_from_profile(kclass):
         return None
     try:
         d = json.load(open(p))
-        import hashlib
-        src = open(os.path.join(ROOT, "paper_1312_1476_gb300", "csrc", "precond.cu"), "rb").read()
-        if d.get("precond_cu_sha1") != hashlib.sha1(src).hexdigest():
+        if d.get("kernel_sources_sha1") != kernel_sources_sha1():
             return None
         return d.get("bytes_per_launch", {}).get(kclass)
     except (OSError, ValueError):

@@ -1,0 +1,60 @@
+"""Bounded runs of the library's hot path for profiler captures.
+
+    python -m paper_1312_1476_gb300.profile_case <case> [--nsamples N] [--steps M]
+
+Each case builds one benchmark configuration on its synthetic inputs, runs
+one sample call capped at M Lanczos steps (so it ends after M steps whatever
+the tolerance) and exits.  The sizes keep a capture small: one or a few
+vectors, a few GB of device memory at most.
+
+Cases:
+  headline_1024  1024 x 1024 SPDE, zero-Neumann, mirror preconditioner, FP32
+  batched_512    512 x 512 SPDE, mirror preconditioner, FP32, N vectors per launch
+  3d_256         256^3 Dirichlet 7-point, kappa^2 i.i.d. U[0.01, 1], FP32
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+
+def run(case: str, nsamples: int, steps: int) -> dict:
+    import torch
+    from . import gmrf, inputs
+    if case == "headline_1024":
+        shape = (1024, 1024)
+        k2 = torch.from_numpy(inputs.kappa2_gp_field(shape, seed=1)).cuda()
+        prob = gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond="mirror")
+    elif case == "batched_512":
+        shape = (512, 512)
+        k2 = torch.from_numpy(inputs.kappa2_gp_field(shape, seed=1, ell=64.0)).cuda()
+        prob = gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond="mirror")
+    elif case == "3d_256":
+        shape = (256, 256, 256)
+        k2 = torch.from_numpy(inputs.kappa2_uniform_field(shape, seed=1)).cuda()
+        prob = gmrf.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=k2)
+    else:
+        raise ValueError("unknown case %r" % case)
+    n = int(np.prod(shape))
+    with prob:
+        x = torch.empty(nsamples * n, dtype=torch.float32, device="cuda")
+        rc, info = prob.sample(x, nsamples=nsamples, tol=1e-6, m_max=steps, seed=2, check_every=8,
+                               raise_on_error=False)
+        torch.cuda.synchronize()
+    if rc not in (gmrf.OK, gmrf.ERR_NOT_CONVERGED):
+        raise gmrf.GmrfError(rc, "profile case " + case)
+    return {"case": case, "nsamples": nsamples, "m_used": [i.m_used for i in info], "rc": rc}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("case", choices=["headline_1024", "batched_512", "3d_256"])
+    ap.add_argument("--nsamples", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=24)
+    a = ap.parse_args(argv)
+    print(run(a.case, a.nsamples, a.steps))
+
+
+if __name__ == "__main__":
+    main()
