@@ -37,7 +37,12 @@
 namespace gmrf {
 namespace {
 
-enum { M_FWD_PLAIN = 0, M_FWD_FORM = 1, M_INV_PLAIN = 2, M_MID = 3, M_LAST = 4, M_LAST_PLAIN = 5 };
+// M_MID does the middle pass in one kernel (no y-boundary terms of R);
+// with them, M_MIDW writes w = B_bar^{-1} v of its rows to a global buffer and
+// M_MIDG reads w of its rows and of their y-partners from it, so no block
+// reads spectrum rows that another block of the same launch rewrites.
+enum { M_FWD_PLAIN = 0, M_FWD_FORM = 1, M_INV_PLAIN = 2, M_MID = 3, M_LAST = 4, M_LAST_PLAIN = 5, M_MIDW = 6,
+       M_MIDG = 7 };
 
 template <typename R>
 struct PArgs {
@@ -53,6 +58,7 @@ struct PArgs {
   R* S;
   size_t sstride;  // per-vector stride of S in R units
   R* G;            // per-vector stride n
+  R* Wg;           // w rows between M_MIDW and M_MIDG, per-vector stride n
   const R* in;     // plain input rows (FWD_PLAIN, MID/LAST_PLAIN v)
   R* out;          // plain output rows
   const float* kappa2;
@@ -207,7 +213,8 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
   __shared__ float s_flt[4];
   typedef typename Cplx<R>::T C;
   const int s = blockIdx.y;
-  const bool step = (MODE == M_FWD_FORM || MODE == M_LAST || (MODE == M_MID && a.in == nullptr));
+  const bool step = (MODE == M_FWD_FORM || MODE == M_LAST ||
+                     ((MODE == M_MID || MODE == M_MIDW || MODE == M_MIDG) && a.in == nullptr));
   int j = 0;
   if (step) {
     if (a.st[s].status != VS_RUNNING) return;
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
       rows[l] = y0 + l;
       partner[l] = -1;
     }
-    if (MODE == M_MID && has_edge_terms<KIND>(a.bc)) {
+    if ((MODE == M_MID || MODE == M_MIDG) && has_edge_terms<KIND>(a.bc)) {
       int extra = rb;
       const bool has0 = y0 == 0, hasN = y0 + rb == ny;
       if (has0) {
@@ -296,7 +303,26 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
     return;
   }
 
-  R* W = row_inverse<R, KIND>(a, B0, B1, B2, PL, nl, rows, Sv);
+  R* W = B0;
+  if (MODE == M_MIDG) {
+    // w of the block's rows and their y-partners, written by M_MIDW
+    const R* wg = a.Wg + (size_t)s * n;
+    for (int idx = tid; idx < nl * nx; idx += nt) {
+      const int l = idx / nx, x = idx - l * nx;
+      B0[l * PL + x] = wg[(size_t)rows[l] * nx + x];
+    }
+    __syncthreads();
+  } else {
+    W = row_inverse<R, KIND>(a, B0, B1, B2, PL, nl, rows, Sv);
+  }
+  if (MODE == M_MIDW) {
+    R* wg = a.Wg + (size_t)s * n;
+    for (int idx = tid; idx < rb * nx; idx += nt) {
+      const int l = idx / nx, x = idx - l * nx;
+      wg[(size_t)(y0 + l) * nx + x] = W[l * PL + x];
+    }
+    return;
+  }
 
   if (MODE == M_INV_PLAIN) {
     R* o = a.out + (size_t)s * n;
@@ -310,7 +336,7 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
   // v: the caller's input (plain operator) or the basis vector v_j (step)
   const R* vsrc = a.in ? a.in + (size_t)s * n : a.V + ((size_t)s * a.P.nslots + (size_t)(j % a.P.nslots)) * n;
 
-  if (MODE == M_MID) {
+  if (MODE == M_MID || MODE == M_MIDG) {
     R* F = B2;                     // r lines (forward-transform input)
     R* T2 = (W == B0) ? B1 : B0;   // scratch for the forward transform
     R* base = W;                   // lines R is applied to
@@ -536,6 +562,7 @@ PArgs<R> base_args(const PrecondTables& t, const Grid& g, const void* kappa2, do
   a.S = (R*)t.S;
   a.sstride = (size_t)t.ny * (t.nx + 2);
   a.G = (R*)t.G;
+  a.Wg = (R*)t.Wg;
   a.kappa2 = (const float*)kappa2;
   a.kappa2_const = (R)kc;
   a.n = g.n;
@@ -582,7 +609,7 @@ int ensure_ws(PrecondTables& t, int nvec, cudaStream_t st) {
     t.G_bytes = gb;
   }
   const bool edges = t.kind == GMRF_PREC_CIRCULANT ? t.bc != GMRF_BC_PERIODIC : t.bc != GMRF_BC_NEUMANN;
-  const size_t wb = (t.fast && edges) ? (size_t)nvec * t.nx * t.ny * es : 16;
+  const size_t wb = edges ? (size_t)nvec * t.nx * t.ny * es : 16;
   if (t.Wg_bytes < wb) {
     if (t.Wg) cudaFreeAsync(t.Wg, st);
     t.Wg = nullptr;
@@ -591,6 +618,12 @@ int ensure_ws(PrecondTables& t, int nvec, cudaStream_t st) {
     t.Wg_bytes = wb;
   }
   return 0;
+}
+
+// R has y-boundary terms (the boundaries of M and Q differ): the middle pass
+// needs the w rows of other blocks (M_MIDW + M_MIDG).
+bool generic_edges(const PrecondTables& t) {
+  return t.kind == GMRF_PREC_CIRCULANT ? t.bc != GMRF_BC_PERIODIC : t.bc != GMRF_BC_NEUMANN;
 }
 
 fast::Args fast_args(const PrecondTables& t, const Grid& g, const void* kappa2, double kc) {
@@ -723,7 +756,12 @@ cudaError_t run_step(PrecondTables& t, const Grid& g, const void* kappa2, double
   a.in = nullptr;
   CKE((row_launch<R, KIND, M_FWD_FORM>(t, a, b.nvec, s, KC_PRE_ROW_FWD)));
   CKE((col_launch<R, KIND>(t, a, b.nvec, 1, s, KC_PRE_COL)));
-  CKE((row_launch<R, KIND, M_MID>(t, a, b.nvec, s, KC_PRE_ROW_MID)));
+  if (generic_edges(t)) {
+    CKE((row_launch<R, KIND, M_MIDW>(t, a, b.nvec, s, KC_PRE_ROW_MID)));
+    CKE((row_launch<R, KIND, M_MIDG>(t, a, b.nvec, s, KC_PRE_ROW_MID)));
+  } else {
+    CKE((row_launch<R, KIND, M_MID>(t, a, b.nvec, s, KC_PRE_ROW_MID)));
+  }
   CKE((col_launch<R, KIND>(t, a, b.nvec, 1, s, KC_PRE_COL)));
   CKE((row_launch<R, KIND, M_LAST>(t, a, b.nvec, s, KC_PRE_ROW_LAST)));
   return cudaSuccess;
@@ -769,7 +807,12 @@ cudaError_t run_operator(PrecondTables& t, const Grid& g, const void* kappa2, do
   a.out = (R*)y;
   CKE((row_launch<R, KIND, M_FWD_PLAIN>(t, a, nvec, s, KC_PRE_APPLY)));
   CKE((col_launch<R, KIND>(t, a, nvec, 0, s, KC_PRE_APPLY)));
-  CKE((row_launch<R, KIND, M_MID>(t, a, nvec, s, KC_PRE_APPLY)));
+  if (generic_edges(t)) {
+    CKE((row_launch<R, KIND, M_MIDW>(t, a, nvec, s, KC_PRE_APPLY)));
+    CKE((row_launch<R, KIND, M_MIDG>(t, a, nvec, s, KC_PRE_APPLY)));
+  } else {
+    CKE((row_launch<R, KIND, M_MID>(t, a, nvec, s, KC_PRE_APPLY)));
+  }
   CKE((col_launch<R, KIND>(t, a, nvec, 0, s, KC_PRE_APPLY)));
   CKE((row_launch<R, KIND, M_LAST_PLAIN>(t, a, nvec, s, KC_PRE_APPLY)));
   return cudaSuccess;
@@ -782,6 +825,8 @@ cudaError_t set_attrs() {
   if ((e = row_attr<R, KIND, M_FWD_FORM>()) != cudaSuccess) return e;
   if ((e = row_attr<R, KIND, M_INV_PLAIN>()) != cudaSuccess) return e;
   if ((e = row_attr<R, KIND, M_MID>()) != cudaSuccess) return e;
+  if ((e = row_attr<R, KIND, M_MIDW>()) != cudaSuccess) return e;
+  if ((e = row_attr<R, KIND, M_MIDG>()) != cudaSuccess) return e;
   if ((e = row_attr<R, KIND, M_LAST>()) != cudaSuccess) return e;
   if ((e = row_attr<R, KIND, M_LAST_PLAIN>()) != cudaSuccess) return e;
   return col_attr<R, KIND>();
@@ -913,7 +958,9 @@ int precond_prepare(PrecondTables& t, int nvec, cudaStream_t s) {
 }
 
 size_t precond_extra_bytes(const PrecondTables& t, size_t es) {
-  return (size_t)t.ny * (t.nx + 2) * es + (size_t)t.nx * t.ny * es;
+  // spectrum, g = C v, and w when R has y-boundary terms
+  return (size_t)t.ny * (t.nx + 2) * es + (size_t)t.nx * t.ny * es +
+         (generic_edges(t) ? (size_t)t.nx * t.ny * es : 0);
 }
 
 cudaError_t launch_precond_step(PrecondTables& t, const Grid& g, bool fp64, const void* kappa2, double kappa2_const,

@@ -3,7 +3,8 @@
 //
 // A line of L = 32 E complex values (E = 2..32) is split over the 32 lanes of
 // a warp: lane l holds x[l + 32 r], r < E, for G = 32 / E lines at a time (32
-// complex values per lane).  Forward FFT: E-point DFTs in registers,
+// complex values per lane); lines of L = 512 go one per warp (16 values per
+// lane, lfft16_*) so that a single 1024 x 1024 vector occupies more warps.  Forward FFT: E-point DFTs in registers,
 // twiddles W_L^{l k1}, one 32x33 shared-memory transpose, 32-point DFTs in
 // registers; the result X[k1 + E k2] sits in lane (g, k1) register k2
 // ("digit-reversed" layout).  The inverse runs the same steps backwards and
@@ -135,13 +136,90 @@ __device__ __forceinline__ void wfft_inv(float2 (&v)[32], float2* sm, const floa
   for (int g = 0; g < G; ++g) reg_fft<E, true>(v + g * E);
 }
 
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return f2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// One line of L = 512 complex values per warp, 16 per lane: L = 16 x 32 with
+// the 32-point DFTs split over lane pairs.  Forward: in v[r] = z[lane + 32 r];
+// 16-point DFTs over r, twiddles W_L^{lane k1}, a 16 x 33 shared transpose so
+// that lane 2 k1 + h holds the entries l = 2 a + h of DFT k1, 16-point DFTs
+// over a, twiddles W_32^j on the odd half and a radix-2 butterfly between the
+// two lanes of a pair.  Out ("split layout"): lane 2 k1 + h, register j holds
+// Z[k1 + 16 j + 256 h].  tw[t] = exp(-2 pi i t / TN), TN = tws * L; sc: this
+// warp's 16 x 33 scratch.
+__device__ __forceinline__ int split_index(int lane, int j) { return (lane >> 1) + 16 * j + 256 * (lane & 1); }
+
+__device__ __forceinline__ void lfft16_fwd(float2 (&v)[16], float2* sc, const float2* __restrict__ tw, int tws) {
+  const int lane = threadIdx.x & 31;
+  reg_fft<16, false>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) v[k1] = mul2(v[k1], tw[lane * k1 * tws]);
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) sc[k1 * 33 + lane] = v[k1];
+  __syncwarp();
+  const int k1 = lane >> 1, h = lane & 1;
+#pragma unroll
+  for (int a = 0; a < 16; ++a) v[a] = sc[k1 * 33 + 2 * a + h];
+  reg_fft<16, false>(v);
+  if (h) {
+#pragma unroll
+    for (int j = 1; j < 16; ++j) v[j] = mul2(v[j], c_w32[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float2 t = shfl_xor2(v[j], 1);
+    v[j] = h ? sub2(t, v[j]) : add2(v[j], t);
+  }
+}
+
+// Inverse (unnormalised) of lfft16_fwd: split layout in, v[r] = L z[lane + 32 r] out.
+__device__ __forceinline__ void lfft16_inv(float2 (&v)[16], float2* sc, const float2* __restrict__ tw, int tws) {
+  const int lane = threadIdx.x & 31;
+  const int k1 = lane >> 1, h = lane & 1;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float2 t = shfl_xor2(v[j], 1);
+    v[j] = h ? sub2(t, v[j]) : add2(v[j], t);
+  }
+  if (h) {
+#pragma unroll
+    for (int j = 1; j < 16; ++j) v[j] = mulc2(v[j], c_w32[j]);
+  }
+  reg_fft<16, true>(v);
+  __syncwarp();
+#pragma unroll
+  for (int a = 0; a < 16; ++a) sc[k1 * 33 + 2 * a + h] = v[a];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = sc[k * 33 + lane];
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = mulc2(v[k], tw[lane * k * tws]);
+  reg_fft<16, true>(v);
+}
+
 enum { R_FWD = 0, R_INV = 1, R_MID = 2, R_MIDW = 3, R_MIDG = 4, R_LAST = 5 };
+
+// Lines per warp and complex values per lane.  Lines of L = 512 (1024-point
+// real rows / columns) go one per warp with 16 values per lane (lfft16_*), so
+// a single large vector spreads over twice as many warps; other lengths put
+// 32 / E lines in a warp with 32 values per lane (wfft_*).
+template <int LOGL>
+__host__ __device__ constexpr bool one_line() { return LOGL == 9; }
+template <int LOGL>
+__host__ __device__ constexpr int lpw() { return one_line<LOGL>() ? 1 : 32 / ((1 << LOGL) / 32); }
+template <int LOGL>
+__host__ __device__ constexpr int vpl() { return one_line<LOGL>() ? (1 << LOGL) / 32 : 32; }
+// per-warp shared scratch (float2): transposes, then one natural-order line per line of the warp
+template <int LOGL>
+__host__ __device__ constexpr int scratch_f2() { return one_line<LOGL>() ? 16 * 33 : 32 * 33; }
 
 template <int KIND>
 __host__ __device__ constexpr int seg_rows() { return KIND == GMRF_PREC_MIRROR ? 8 : 4; }
 template <int KIND, int LOGL>
 __host__ __device__ constexpr int rows_per_block() {
-  return (32 / ((1 << LOGL) / 32)) > seg_rows<KIND>() ? (32 / ((1 << LOGL) / 32)) : seg_rows<KIND>();
+  return lpw<LOGL>() > seg_rows<KIND>() ? lpw<LOGL>() : seg_rows<KIND>();
 }
 template <int KIND, int LOGL>
 __host__ __device__ constexpr int tile_pitch() {  // floats per tile row
@@ -159,18 +237,18 @@ __device__ __forceinline__ void stage_table(float* dst, const float* __restrict_
 constexpr int kColWarps = 4;
 
 // Dynamic shared memory of the row kernel:
-//   tile[RB][TP] floats | per-warp scratch [WPC][32 * 33] float2 | twx[NX] | dctx[NX + 1] (MIRROR only)
+//   tile[RB][TP] floats | per-warp scratch [WPC][scratch_f2] float2 | twx[NX] | dctx[NX + 1] (MIRROR only)
 template <int KIND, int LOGL>
 __host__ __device__ constexpr size_t row_smem_bytes() {
   return (size_t)rows_per_block<KIND, LOGL>() * tile_pitch<KIND, LOGL>() * sizeof(float) +
-         (size_t)(rows_per_block<KIND, LOGL>() / (32 / ((1 << LOGL) / 32))) * 32 * 33 * sizeof(float2) +
+         (size_t)(rows_per_block<KIND, LOGL>() / lpw<LOGL>()) * scratch_f2<LOGL>() * sizeof(float2) +
          (size_t)(2 * (1 << LOGL) + (KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 1 : 0)) * sizeof(float2);
 }
 // Dynamic shared memory of the column kernel:
-//   per-warp scratch [kColWarps][32 * 33] float2 | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny] floats
+//   per-warp scratch [kColWarps][scratch_f2] float2 | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny] floats
 template <int KIND, int LOGL>
 __host__ __device__ constexpr size_t col_smem_bytes() {
-  return (size_t)kColWarps * 32 * 33 * sizeof(float2) +
+  return (size_t)kColWarps * scratch_f2<LOGL>() * sizeof(float2) +
          (size_t)((KIND == GMRF_PREC_CIRCULANT ? (1 << LOGL) : 2 * (1 << LOGL)) +
                   (KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 1 : 0)) * sizeof(float2) +
          (size_t)(KIND == GMRF_PREC_CIRCULANT ? (1 << LOGL) : 2 * (1 << LOGL)) * sizeof(float);
@@ -408,16 +486,21 @@ __device__ __forceinline__ void tile_load_T(const Args& a, float* tile, const fl
 // forward real transform of the warp's G rows held as pairs p[g][E]; spectrum
 // rows written to the tile rows tr0 + g.
 template <int KIND, int LOGL>
-__device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[32], float2* sm, float* tile, int tr0,
-                                             const float2* twx, const float2* dctx) {
-  constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E, TP = tile_pitch<KIND, LOGL>();
+__device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[vpl<LOGL>()], float2* sm, float* tile,
+                                             int tr0, const float2* twx, const float2* dctx) {
+  constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), TP = tile_pitch<KIND, LOGL>();
   const int lane = threadIdx.x & 31;
-  float2 v[32];
+  float2 v[vpl<LOGL>()];
 #pragma unroll
   for (int g = 0; g < G; ++g) pack_row<KIND, E>(p + g * E, v + g * E);
-  wfft_fwd<LOGL>(v, sm, twx, 2);
-  __syncwarp();
-  {
+  if constexpr (one_line<LOGL>()) {
+    lfft16_fwd(v, sm, twx, 2);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sm[split_index(lane, j)] = v[j];
+  } else {
+    wfft_fwd<LOGL>(v, sm, twx, 2);
+    __syncwarp();
     const int g = lane / E, k1 = lane % E;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) sm[g * L + k1 + E * k2] = v[k2];
@@ -433,9 +516,9 @@ __device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[32], flo
 
 // inverse real transform: tile rows tr0 + g -> pairs p[g][E] (times L).
 template <int KIND, int LOGL>
-__device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[32], float2* sm, const float* tile, int tr0,
-                                             const float2* twx, const float2* dctx) {
-  constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E, TP = tile_pitch<KIND, LOGL>();
+__device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[vpl<LOGL>()], float2* sm, const float* tile,
+                                             int tr0, const float2* twx, const float2* dctx) {
+  constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), TP = tile_pitch<KIND, LOGL>();
   const int lane = threadIdx.x & 31;
   constexpr int NP = L / 2 + 1;
   __syncwarp();
@@ -445,21 +528,25 @@ __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[32], flo
     pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, k, twx, dctx, sm + g * L);
   }
   __syncwarp();
-  float2 v[32];
-  {
+  float2 v[vpl<LOGL>()];
+  if constexpr (one_line<LOGL>()) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = sm[split_index(lane, j)];
+    lfft16_inv(v, sm, twx, 2);
+  } else {
     const int g = lane / E, k1 = lane % E;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) v[k2] = sm[g * L + k1 + E * k2];
+    wfft_inv<LOGL>(v, sm, twx, 2);
   }
-  wfft_inv<LOGL>(v, sm, twx, 2);
 #pragma unroll
   for (int g = 0; g < G; ++g) unpack_row<KIND, E>(v + g * E, p + g * E);
 }
 
 template <int KIND, int LOGL, int MODE>
-__global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1 << LOGL) / 32))))
+__global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>()))
     k_row(Args a) {
-  constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E, NX = 2 * L;
+  constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), NX = 2 * L;
   constexpr int RB = rows_per_block<KIND, LOGL>(), TP = tile_pitch<KIND, LOGL>();
   extern __shared__ __align__(16) float smf[];
   __shared__ Dots<float> red[8];
@@ -468,8 +555,8 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
   constexpr int WPC = RB / G;
   float* tile = smf;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* sm = reinterpret_cast<float2*>(smf + RB * TP) + warp * (32 * 33);
-  float2* twx = reinterpret_cast<float2*>(smf + RB * TP) + WPC * (32 * 33);  // [NX] exp(-2 pi i t / NX)
+  float2* sm = reinterpret_cast<float2*>(smf + RB * TP) + warp * scratch_f2<LOGL>();
+  float2* twx = reinterpret_cast<float2*>(smf + RB * TP) + WPC * scratch_f2<LOGL>();  // [NX] exp(-2 pi i t / NX)
   float2* dctx = twx + NX;                                                    // [NX + 1] (MIRROR)
   const int s = blockIdx.y;
   const bool step = (MODE == R_FWD || MODE == R_LAST || MODE == R_MID || MODE == R_MIDW || MODE == R_MIDG) &&
@@ -486,7 +573,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / (32 / ((1
   const int tr0 = warp * G;       // first tile row of this warp
   const size_t n = a.n;
   float* Tv = a.T + (size_t)s * a.tstride;
-  float2 p[32];
+  float2 p[vpl<LOGL>()];
   const size_t slot = (size_t)s * a.P.nslots;
 
   if (MODE == R_FWD) {
@@ -686,15 +773,15 @@ __device__ __forceinline__ float sym(const Args& a, float cx, const float* lamy,
 
 template <int KIND, int LOGL>
 __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
-  constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E;
+  constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), VN = vpl<LOGL>();
   constexpr int NYc = KIND == GMRF_PREC_CIRCULANT ? L : 2 * L;  // ny
   extern __shared__ __align__(16) float smf[];
   const int s = blockIdx.y;
   if (step_mode && a.st[s].status != VS_RUNNING) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* sm = reinterpret_cast<float2*>(smf) + warp * (32 * 33);
+  float2* sm = reinterpret_cast<float2*>(smf) + warp * scratch_f2<LOGL>();
   // layout (must match col_smem_bytes): warp scratch | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny]
-  float2* twy = reinterpret_cast<float2*>(smf) + kColWarps * (32 * 33);
+  float2* twy = reinterpret_cast<float2*>(smf) + kColWarps * scratch_f2<LOGL>();
   float2* dcty = twy + NYc;
   float* lamy = reinterpret_cast<float*>(dcty + (KIND == GMRF_PREC_MIRROR ? NYc + 1 : 0));
   stage_table(twy, a.twy, NYc);
@@ -703,7 +790,7 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
   __syncthreads();
   float* Tv = a.T + (size_t)s * a.tstride;
   const int line0 = (blockIdx.x * kColWarps + warp) * G;
-  float2 v[32];
+  float2 v[VN];
   if (KIND == GMRF_PREC_CIRCULANT) {
     // complex lines kx = 0..nx/2 of length ny = L
     const int ncl = a.nx / 2 + 1;
@@ -714,16 +801,26 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
 #pragma unroll
       for (int r = 0; r < E; ++r) v[g * E + r] = kx < ncl ? src[lane + 32 * r] : f2(0.f, 0.f);
     }
-    wfft_fwd<LOGL>(v, sm, twy, 1);
-    {
-      const int g = lane / E, k1 = lane % E, kx = line0 + g;
-      if (kx < ncl) {
-        const float cx = a.kbar2 + __ldg(a.lamx + kx);
+    if constexpr (one_line<LOGL>()) {
+      lfft16_fwd(v, sm, twy, 1);
+      if (line0 < ncl) {
+        const float cx = a.kbar2 + __ldg(a.lamx + line0);
 #pragma unroll
-        for (int k2 = 0; k2 < 32; ++k2) v[k2] = scl2(v[k2], sym(a, cx, lamy, k1 + E * k2));
+        for (int j = 0; j < 16; ++j) v[j] = scl2(v[j], sym(a, cx, lamy, split_index(lane, j)));
       }
+      lfft16_inv(v, sm, twy, 1);
+    } else {
+      wfft_fwd<LOGL>(v, sm, twy, 1);
+      {
+        const int g = lane / E, k1 = lane % E, kx = line0 + g;
+        if (kx < ncl) {
+          const float cx = a.kbar2 + __ldg(a.lamx + kx);
+#pragma unroll
+          for (int k2 = 0; k2 < 32; ++k2) v[k2] = scl2(v[k2], sym(a, cx, lamy, k1 + E * k2));
+        }
+      }
+      wfft_inv<LOGL>(v, sm, twy, 1);
     }
-    wfft_inv<LOGL>(v, sm, twy, 1);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int kx = line0 + g;
@@ -737,7 +834,7 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
   }
   // MIRROR: real lines kx = 0..nx-1 of length ny = 2L (DCT-II, symbol, inverse)
   constexpr int NY = 2 * L;
-  float2 p[32];
+  float2 p[VN];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     if (line0 + g < a.nx) load_row<KIND, E>(p + g * E, Tv + (size_t)(line0 + g) * NY);
@@ -748,9 +845,14 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
   }
 #pragma unroll
   for (int g = 0; g < G; ++g) pack_row<KIND, E>(p + g * E, v + g * E);
-  wfft_fwd<LOGL>(v, sm, twy, 2);
-  __syncwarp();
-  {
+  if constexpr (one_line<LOGL>()) {
+    lfft16_fwd(v, sm, twy, 2);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sm[split_index(lane, j)] = v[j];
+  } else {
+    wfft_fwd<LOGL>(v, sm, twy, 2);
+    __syncwarp();
     const int g = lane / E, k1 = lane % E;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) sm[g * L + k1 + E * k2] = v[k2];
@@ -823,12 +925,16 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
     }
   }
   __syncwarp();
-  {
+  if constexpr (one_line<LOGL>()) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = sm[split_index(lane, j)];
+    lfft16_inv(v, sm, twy, 2);
+  } else {
     const int g = lane / E, k1 = lane % E;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) v[k2] = sm[g * L + k1 + E * k2];
+    wfft_inv<LOGL>(v, sm, twy, 2);
   }
-  wfft_inv<LOGL>(v, sm, twy, 2);
 #pragma unroll
   for (int g = 0; g < G; ++g) unpack_row<KIND, E>(v + g * E, p + g * E);
 #pragma unroll
@@ -845,7 +951,7 @@ namespace fast {
 // ----------------------------------------------------------------- launchers
 template <int KIND, int LOGL, int MODE>
 cudaError_t row_launch_t(const Args& a, int nvec, cudaStream_t s, int kc) {
-  constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E;
+  constexpr int G = lpw<LOGL>();
   constexpr int RB = rows_per_block<KIND, LOGL>(), TP = tile_pitch<KIND, LOGL>();
   constexpr int WPC = RB / G;
   const size_t sm = row_smem_bytes<KIND, LOGL>();
@@ -876,7 +982,7 @@ cudaError_t row_launch(const Args& a, int nvec, cudaStream_t s, int kc) {
 
 template <int KIND, int LOGL>
 cudaError_t col_launch_t(const Args& a, int nvec, int step_mode, cudaStream_t s, int kc) {
-  constexpr int L = 1 << LOGL, E = L / 32, G = 32 / E;
+  constexpr int G = lpw<LOGL>();
   const int nlines = KIND == GMRF_PREC_CIRCULANT ? a.nx / 2 + 1 : a.nx;
   const int per = kColWarps * G;
   const size_t sm = col_smem_bytes<KIND, LOGL>();

@@ -123,7 +123,12 @@ def test_precond_inv_sqrt(g, shape, kind, op, precision):
 OPER_CASES = [((16, 16), "neumann", "periodic"), ((16, 16), "dirichlet", "periodic"),
               ((16, 16), "periodic", "periodic"), ((32, 16), "neumann", "neumann"),
               ((16, 32), "dirichlet", "neumann"), ((16, 16), "periodic", "neumann"),
-              ((128, 128), "neumann", "periodic"), ((128, 128), "neumann", "neumann")]
+              ((128, 128), "neumann", "periodic"), ((128, 128), "neumann", "neumann"),
+              ((1024, 1024), "neumann", "neumann"), ((512, 1024), "dirichlet", "periodic"),
+              ((1024, 512), "periodic", "neumann"),
+              # several row blocks with y-boundary terms of R (generic path: w rows across blocks)
+              ((64, 32), "dirichlet", "periodic"), ((64, 32), "neumann", "periodic"),
+              ((128, 32), "dirichlet", "neumann")]
 
 
 @pytest.mark.parametrize("shape,bc,kind", OPER_CASES)
