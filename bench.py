@@ -426,8 +426,42 @@ def measure_variants(args, gmrf, torch, flush, peak):
             "m_mean": float(np.mean([i.m_used for i in infob])),
             "basis_bytes_per_vector_step": {"fp32": 4 * n, "bf16": 2 * n},
             "max_rel_diff_vs_fp32_basis": diff}
+    out["table1"] = measure_table1(gmrf, torch)
     out["serving"] = measure_serving()
     return out
+
+
+def measure_table1(gmrf, torch):
+    """Table 1 (Section 5.1): Lanczos steps until the Theorem 1 estimate is
+    below 1e-8 (FP64) for the sMMALA proposal of an LGCP on an N x N lattice of
+    the unit torus, Q = prior + diag(Fisher information), preconditioned by the
+    prior (circulant, applied by FFT) and without preconditioning."""
+    from paper_1312_1476_gb300 import inputs
+    pre, un, ms_sample = {}, {}, {}
+    for N in (16, 32, 64, 128, 256, 512, 1024, 2048):
+        mdl = inputs.lgcp_smmala_model(N)
+        kw = dict(kappa2=torch.from_numpy(mdl["d"]).cuda(), kappa2_const=mdl["kappa2_prior"], tau=mdl["tau"],
+                  precision="fp64")
+        x = torch.empty(N * N, dtype=torch.float64, device="cuda")
+        with gmrf.Problem((N, N), "periodic", "spde_plus_diag", precond="circulant", **kw) as p:
+            p.sample(x, nsamples=1, tol=1e-8, m_max=200, seed=1, check_every=1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, info = p.sample(x, nsamples=1, tol=1e-8, m_max=200, seed=2, check_every=1)
+            torch.cuda.synchronize()
+            ms_sample[N] = round((time.perf_counter() - t0) * 1e3, 3)
+            pre[N] = info[0].m_used if rc == gmrf.OK else None
+        if N <= 128:
+            with gmrf.Problem((N, N), "periodic", "spde_plus_diag", **kw) as p:
+                rc, info = p.sample(x, nsamples=1, tol=1e-8, m_max=8192, seed=2, check_every=16,
+                                    raise_on_error=False)
+                un[N] = info[0].m_used if rc == gmrf.OK else None
+    return {"workload": "LGCP sMMALA proposal on the unit torus (prior h^2 (kappa^2 + L/h^2)^2, kappa 10; "
+                        "Fisher information diag(h^2 exp(x)), mean intensity 2000), FP64, tol 1e-8, one sample",
+            "m_preconditioned": pre, "m_unpreconditioned": un, "ms_per_preconditioned_sample": ms_sample,
+            "paper_table1_context": {"preconditioned": 6, "unpreconditioned": {"16": 102, "32": 286, "64": 790,
+                                                                              "128": 2166},
+                                     "note": "the paper's prior is unspecified; counts are context"}}
 
 
 def measure_serving(nreq=32):

@@ -69,7 +69,16 @@ typedef enum { GMRF_BC_PERIODIC = 0, GMRF_BC_NEUMANN = 1, GMRF_BC_DIRICHLET = 2 
 
 typedef enum {
   GMRF_OP_SHIFTED_LAPLACIAN = 0, /* tau (K + L) */
-  GMRF_OP_SPDE_SQUARED = 1       /* tau (K + L)^2, 2-D only */
+  GMRF_OP_SPDE_SQUARED = 1,      /* tau (K + L)^2, 2-D only */
+  GMRF_OP_SPDE_PLUS_DIAG = 2     /* tau ((kappa_c^2 I + L)^2 + D), 2-D only: a stationary (block-circulant
+                                    on a torus) prior plus a non-negative diagonal, e.g. the Fisher
+                                    information of the LGCP sMMALA proposal (Section 3; Section 5.1,
+                                    Table 1).  kappa_c^2 = kappa2_const (> 0 unless Dirichlet);
+                                    D = diag(kappa2 field), entries >= 0 (NULL: D = 0).
+                                    Preconditioned by the prior itself, M = tau (kappa_c^2 + L)^2, so
+                                    A = I + M^{-1/2} (tau D) M^{-1/2}; that needs matched boundaries
+                                    (PERIODIC with CIRCULANT, NEUMANN with MIRROR) and
+                                    kappa2_precond <= 0 or equal to kappa2_const. */
 } gmrf_op;
 
 /* Preconditioner M (Proposition 1 with F = M^{1/2}; Section 5.1):

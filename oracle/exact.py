@@ -94,21 +94,21 @@ def spectral_coefficients(shape, bc, v):
     return _fwd(bc, np.asarray(v, dtype=np.float64).reshape(shape))
 
 
-def sample_spectral(shape, bc, op, kappa2_const, tau, z):
+def sample_spectral(shape, bc, op, kappa2_const, tau, z, kappa2_prior=None):
     """x = Q^{-1/2} z for constant kappa^2 through the closed-form eigenvalues."""
-    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau)
+    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau, kappa2_prior=kappa2_prior)
     return spectral_apply(shape, bc, 1.0 / np.sqrt(mu), z)
 
 
-def logdet_spectral(shape, bc, op, kappa2_const, tau) -> float:
+def logdet_spectral(shape, bc, op, kappa2_const, tau, kappa2_prior=None) -> float:
     """log det Q = sum of log eigenvalues (constant kappa^2)."""
-    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau)
+    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau, kappa2_prior=kappa2_prior)
     return float(np.sum(np.log(mu)))
 
 
-def quadform_log_spectral(shape, bc, op, kappa2_const, tau, V) -> np.ndarray:
+def quadform_log_spectral(shape, bc, op, kappa2_const, tau, V, kappa2_prior=None) -> np.ndarray:
     """v^T log(Q) v = sum_k |c_k|^2 log mu_k for each row v (constant kappa^2)."""
-    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau)
+    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau, kappa2_prior=kappa2_prior)
     out = []
     for v in np.atleast_2d(V):
         c = spectral_coefficients(shape, bc, v)

@@ -13,7 +13,11 @@ family (its reading of the paper's lattice models, Sections 3 and 5):
 * ``shifted_laplacian``: Q = tau (K + L), K = diag(kappa^2);
 * ``spde_squared``:      Q = tau (K + L)^2  (a 13-point stencil in 2-D; the
   Figure 3 matrix (31^2 poisson(30))^2 of Section 5.2 is this operator with
-  kappa^2 = 0, Dirichlet boundary, tau = 31^4).
+  kappa^2 = 0, Dirichlet boundary, tau = 31^4);
+* ``spde_plus_diag``:    Q = tau ((kp I + L)^2 + D), a stationary prior with
+  constant ``kappa2_prior`` = kp plus the diagonal D = diag(kappa2) (the
+  circulant-plus-diagonal precision of the sMMALA proposal, Sections 3 and
+  5.1).
 
 Grids are given slowest axis first: ``shape = (ny, nx)`` or ``(nz, ny, nx)``;
 cell ``(z, y, x)`` has index ``x + nx*(y + ny*z)`` (C order).
@@ -26,7 +30,7 @@ import numpy as np
 import scipy.sparse as sp
 
 BCS = ("periodic", "neumann", "dirichlet")
-OPS = ("shifted_laplacian", "spde_squared")
+OPS = ("shifted_laplacian", "spde_squared", "spde_plus_diag")
 
 
 def laplacian_1d(n: int, bc: str) -> sp.csr_matrix:
@@ -68,10 +72,13 @@ def _kappa_vector(shape, kappa2):
     return k.reshape(n).astype(np.float64)
 
 
-def precision_matrix(shape, bc: str, op: str, kappa2, tau: float = 1.0) -> sp.csr_matrix:
+def precision_matrix(shape, bc: str, op: str, kappa2, tau: float = 1.0, kappa2_prior=None) -> sp.csr_matrix:
     """Q for the lattice operator family above (sparse, FP64)."""
     if op not in OPS:
         raise ValueError(op)
+    if op == "spde_plus_diag":
+        B = float(kappa2_prior) * sp.identity(int(np.prod(shape))) + laplacian(shape, bc)
+        return sp.csr_matrix(float(tau) * (B @ B + sp.diags(_kappa_vector(shape, kappa2))))
     B = sp.diags(_kappa_vector(shape, kappa2)) + laplacian(shape, bc)
     Q = B if op == "shifted_laplacian" else B @ B
     return sp.csr_matrix(float(tau) * Q)
@@ -102,7 +109,7 @@ def _shifted_rows(shape, bc, kvec_at, rows):
     return R
 
 
-def precision_rows(shape, bc: str, op: str, kappa2, tau: float = 1.0, rows=()) -> sp.csr_matrix:
+def precision_rows(shape, bc: str, op: str, kappa2, tau: float = 1.0, rows=(), kappa2_prior=None) -> sp.csr_matrix:
     """Rows ``rows`` of Q without assembling Q (for sampled checks of
     matrix-free products on grids too large to assemble)."""
     if op not in OPS:
@@ -114,6 +121,15 @@ def precision_rows(shape, bc: str, op: str, kappa2, tau: float = 1.0, rows=()) -
     else:
         kf = k.reshape(-1)
         kvec_at = lambda idx: kf[idx].astype(np.float64)  # noqa: E731
+    if op == "spde_plus_diag":
+        rows = np.asarray(rows, dtype=np.int64)
+        kp_at = lambda idx: np.full(len(idx), float(kappa2_prior))  # noqa: E731
+        R = _shifted_rows(shape, bc, kp_at, rows)
+        cols = np.unique(R.indices)
+        R = sp.csr_matrix(R[:, cols] @ _shifted_rows(shape, bc, kp_at, cols))
+        n = int(np.prod(shape))
+        D = sp.csr_matrix((kvec_at(rows), (np.arange(len(rows)), rows)), shape=(len(rows), n))
+        return sp.csr_matrix(float(tau) * (R + D))
     R = _shifted_rows(shape, bc, kvec_at, rows)
     if op == "spde_squared":
         # rows of B B: (row_i of B) applied to the rows of B it touches
@@ -123,7 +139,7 @@ def precision_rows(shape, bc: str, op: str, kappa2, tau: float = 1.0, rows=()) -
     return sp.csr_matrix(float(tau) * R)
 
 
-def precision_matrix_bruteforce(shape, bc: str, op: str, kappa2, tau: float = 1.0) -> np.ndarray:
+def precision_matrix_bruteforce(shape, bc: str, op: str, kappa2, tau: float = 1.0, kappa2_prior=None) -> np.ndarray:
     """Dense Q built cell by cell from the neighbour definition (pin for the above).
 
     Loops over every cell and every axis direction, adds the edge term
@@ -133,6 +149,9 @@ def precision_matrix_bruteforce(shape, bc: str, op: str, kappa2, tau: float = 1.
     shape = tuple(int(s) for s in shape)
     n = int(np.prod(shape))
     k = _kappa_vector(shape, kappa2)
+    diag = None
+    if op == "spde_plus_diag":
+        diag, k = k, np.full(n, float(kappa2_prior))
     B = np.zeros((n, n))
     strides = [int(np.prod(shape[ax + 1:])) for ax in range(len(shape))]
     for idx in itertools.product(*[range(s) for s in shape]):
@@ -156,6 +175,8 @@ def precision_matrix_bruteforce(shape, bc: str, op: str, kappa2, tau: float = 1.
                 B[i, i] += 1.0
                 B[i, j] -= 1.0
     Q = B if op == "shifted_laplacian" else B @ B
+    if diag is not None:
+        Q = Q + np.diag(diag)
     return float(tau) * Q
 
 
@@ -202,9 +223,15 @@ def laplacian_eigenvalues(shape, bc: str) -> np.ndarray:
     return sum(grids)
 
 
-def operator_eigenvalues(shape, bc: str, op: str, kappa2_const: float, tau: float = 1.0) -> np.ndarray:
+def operator_eigenvalues(shape, bc: str, op: str, kappa2_const: float, tau: float = 1.0,
+                         kappa2_prior=None) -> np.ndarray:
     """Eigenvalues of Q for a constant kappa^2 (array of ``shape``, same ordering
-    as the spectral transforms in ``exact``)."""
+    as the spectral transforms in ``exact``).  For ``spde_plus_diag`` the
+    constant diagonal is ``kappa2_const`` and the prior's constant
+    ``kappa2_prior``."""
+    if op == "spde_plus_diag":
+        lam = float(kappa2_prior) + laplacian_eigenvalues(shape, bc)
+        return float(tau) * (lam * lam + float(kappa2_const))
     lam = float(kappa2_const) + laplacian_eigenvalues(shape, bc)
     if op == "spde_squared":
         lam = lam * lam

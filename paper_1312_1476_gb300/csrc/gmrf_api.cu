@@ -364,7 +364,7 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
   if (!d || !out) return GMRF_ERR_INVALID;
   *out = nullptr;
   if (d->dim != 2 && d->dim != 3) return GMRF_ERR_INVALID;
-  if (d->bc < 0 || d->bc > 2 || d->op < 0 || d->op > 1 || d->precond < 0 || d->precond > 2) return GMRF_ERR_INVALID;
+  if (d->bc < 0 || d->bc > 2 || d->op < 0 || d->op > 2 || d->precond < 0 || d->precond > 2) return GMRF_ERR_INVALID;
   if (d->precision != GMRF_FP32 && d->precision != GMRF_FP64) return GMRF_ERR_INVALID;
   if (d->reserved != 0) return GMRF_ERR_INVALID;
   if (d->nx < 2 || d->ny < 2 || (d->dim == 3 && d->nz < 2)) return GMRF_ERR_INVALID;
@@ -373,14 +373,23 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
   const int64_t nz = d->dim == 3 ? d->nz : 1;
   const double nd = (double)d->nx * (double)d->ny * (double)nz;
   if (nd > 4.0e9) return GMRF_ERR_INVALID;
-  if (!d->kappa2 && (!(d->kappa2_const >= 0.0) || !std::isfinite(d->kappa2_const))) return GMRF_ERR_INVALID;
+  const bool plus_diag = d->op == GMRF_OP_SPDE_PLUS_DIAG;
+  if ((!d->kappa2 || plus_diag) && (!(d->kappa2_const >= 0.0) || !std::isfinite(d->kappa2_const)))
+    return GMRF_ERR_INVALID;
   // a constant kappa^2 = 0 leaves the constant vector in the null space unless the boundary is Dirichlet
-  if (!d->kappa2 && d->bc != GMRF_BC_DIRICHLET && !(d->kappa2_const > 0.0)) return GMRF_ERR_INVALID;
-  if (d->dim == 3 && d->op == GMRF_OP_SPDE_SQUARED) return GMRF_ERR_UNSUPPORTED;
+  if ((!d->kappa2 || plus_diag) && d->bc != GMRF_BC_DIRICHLET && !(d->kappa2_const > 0.0)) return GMRF_ERR_INVALID;
+  if (d->dim == 3 && d->op != GMRF_OP_SHIFTED_LAPLACIAN) return GMRF_ERR_UNSUPPORTED;
   if (d->precond != GMRF_PREC_NONE) {
     if (d->dim != 2) return GMRF_ERR_UNSUPPORTED;
     if (!precond_size_ok(d->nx) || !precond_size_ok(d->ny)) return GMRF_ERR_UNSUPPORTED;
     if (!(d->kappa2_precond <= 0.0 || std::isfinite(d->kappa2_precond))) return GMRF_ERR_INVALID;
+    if (plus_diag) {
+      // M is the prior itself: R = tau D is diagonal only with matched boundaries and kappa_bar = kappa_c
+      const bool matched = (d->precond == GMRF_PREC_CIRCULANT && d->bc == GMRF_BC_PERIODIC) ||
+                           (d->precond == GMRF_PREC_MIRROR && d->bc == GMRF_BC_NEUMANN);
+      if (!matched || (d->kappa2_precond > 0.0 && d->kappa2_precond != d->kappa2_const))
+        return GMRF_ERR_UNSUPPORTED;
+    }
   }
   gmrf_problem* p = new (std::nothrow) gmrf_problem();
   if (!p) return GMRF_ERR_OOM;
@@ -443,14 +452,16 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
     if (h[0] > 0.5) return fail(GMRF_ERR_INVALID);
     nzero = h[1];
     sum_log = h[2];
-    if (d->bc != GMRF_BC_DIRICHLET && nzero > (double)p->g.n - 0.5) return fail(GMRF_ERR_INVALID);
+    // (K + L) with K = 0 is singular without a Dirichlet boundary; the diagonal
+    // of SPDE_PLUS_DIAG may vanish (kappa_c^2 > 0 was checked)
+    if (!plus_diag && d->bc != GMRF_BC_DIRICHLET && nzero > (double)p->g.n - 0.5) return fail(GMRF_ERR_INVALID);
   } else {
     if (d->bc != GMRF_BC_DIRICHLET && !(d->kappa2_const > 0.0)) return fail(GMRF_ERR_INVALID);
     sum_log = d->kappa2_const > 0 ? (double)p->g.n * std::log(d->kappa2_const) : 0.0;
     nzero = d->kappa2_const > 0 ? 0.0 : (double)p->g.n;
   }
   if (d->precond != GMRF_PREC_NONE) {
-    double kb = d->kappa2_precond;
+    double kb = plus_diag ? d->kappa2_const : d->kappa2_precond;
     if (!(kb > 0.0)) {
       const double npos = (double)p->g.n - nzero;
       kb = npos > 0.5 ? std::exp(sum_log / npos) : 0.0;

@@ -57,13 +57,16 @@ __device__ __forceinline__ T bop2(const T* a, int cx, int cy, int gx, int gy, in
 }
 
 // STEP = true: fused Lanczos step.  STEP = false: y = Q v (Win = v, Wout = y).
+// SPDE_PLUS_DIAG: Q v = B(B v) + D v with B = kappa_c^2 I + L (constant
+// coefficient, kappa2_const) and D = diag(kappa2 field, or 0).
 template <typename T, int OP, int BC, bool STEP>
 __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
-  constexpr int H = (OP == GMRF_OP_SPDE_SQUARED) ? 2 : 1;
+  constexpr bool SQ = OP != GMRF_OP_SHIFTED_LAPLACIAN;  // B applied twice
+  constexpr int H = SQ ? 2 : 1;
   constexpr int VW = TX + 2 * H, VH = TY + 2 * H;
   constexpr int GW = TX + 2, GH = TY + 2;
   __shared__ T vs[VH * VW];
-  __shared__ T gs[(OP == GMRF_OP_SPDE_SQUARED) ? GH * GW : 1];
+  __shared__ T gs[SQ ? GH * GW : 1];
   __shared__ Dots<T> red[NT / 32];
   __shared__ int s_int[4];
   __shared__ float s_flt[4];
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
     vs[idx] = val;
   }
   __syncthreads();
-  if (OP == GMRF_OP_SPDE_SQUARED) {
+  if (SQ) {
     for (int idx = tid; idx < GH * GW; idx += NT) {
       const int py = idx / GW, px = idx - py * GW;
       int gx = x0 - 1 + px, gy = y0 - 1 + py;
@@ -129,7 +132,8 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
       }
       T g = 0;
       if (in) {
-        const T kap = kap_at<T>(a.kappa2, a.kappa2_const, (size_t)gx + (size_t)nx * gy);
+        const T kap = OP == GMRF_OP_SPDE_PLUS_DIAG ? a.kappa2_const
+                                                   : kap_at<T>(a.kappa2, a.kappa2_const, (size_t)gx + (size_t)nx * gy);
         g = bop2<T, BC, VW>(vs, px + 1, py + 1, gx, gy, nx, ny, kap);
       }
       gs[idx] = g;
@@ -142,10 +146,11 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
   d.zero();
   if (own) {
     const size_t i = (size_t)gx + (size_t)nx * gy;
-    const T kap = kap_at<T>(a.kappa2, a.kappa2_const, i);
+    const T kap = OP == GMRF_OP_SPDE_PLUS_DIAG ? a.kappa2_const : kap_at<T>(a.kappa2, a.kappa2_const, i);
     T qv;
-    if (OP == GMRF_OP_SPDE_SQUARED) qv = bop2<T, BC, GW>(gs, tx + 1, ty + 1, gx, gy, nx, ny, kap);
+    if (SQ) qv = bop2<T, BC, GW>(gs, tx + 1, ty + 1, gx, gy, nx, ny, kap);
     else qv = bop2<T, BC, VW>(vs, tx + H, ty + H, gx, gy, nx, ny, kap);
+    if (OP == GMRF_OP_SPDE_PLUS_DIAG && a.kappa2) qv += (T)__ldg(a.kappa2 + i) * vs[(ty + H) * VW + tx + H];
     if (!STEP) {
       Wout[i] = qv;
     } else {
@@ -467,6 +472,12 @@ cudaError_t dispatch(const Grid& g, StencilArgs<T> a, int nvec, cudaStream_t s) 
       case GMRF_BC_PERIODIC: GMRF_L2(GMRF_OP_SPDE_SQUARED, GMRF_BC_PERIODIC); break;
       case GMRF_BC_NEUMANN: GMRF_L2(GMRF_OP_SPDE_SQUARED, GMRF_BC_NEUMANN); break;
       default: GMRF_L2(GMRF_OP_SPDE_SQUARED, GMRF_BC_DIRICHLET); break;
+    }
+  } else if (g.op == GMRF_OP_SPDE_PLUS_DIAG) {
+    switch (g.bc) {
+      case GMRF_BC_PERIODIC: GMRF_L2(GMRF_OP_SPDE_PLUS_DIAG, GMRF_BC_PERIODIC); break;
+      case GMRF_BC_NEUMANN: GMRF_L2(GMRF_OP_SPDE_PLUS_DIAG, GMRF_BC_NEUMANN); break;
+      default: GMRF_L2(GMRF_OP_SPDE_PLUS_DIAG, GMRF_BC_DIRICHLET); break;
     }
   } else {
     switch (g.bc) {

@@ -48,7 +48,9 @@ template <typename R>
 struct PArgs {
   typedef typename Cplx<R>::T C;
   int nx, ny, lognx, logny, power, bc, rb, cw;
+  int form;        // FORM_SHIFT / FORM_CTC / FORM_DIAG
   R kbar2, dscale;
+  R roff;          // R = K - roff (kappa_bar^2; 0 for FORM_DIAG, where K is the diagonal D)
   const R* lamx;
   const R* lamy;
   const C* twx;
@@ -194,7 +196,7 @@ __device__ __forceinline__ R kap(const PArgs<R>& a, size_t i) {
 template <typename R, int KIND>
 __device__ __forceinline__ R apply_R(const PArgs<R>& a, const R* Wl, int PL, int li, int lp, int x, int row) {
   const R wi = Wl[li * PL + x];
-  R r = (kap(a, (size_t)row * a.nx + x) - a.kbar2) * wi;
+  R r = (kap(a, (size_t)row * a.nx + x) - a.roff) * wi;
   if (has_edge_terms<KIND>(a.bc)) {
     if (x == 0) r += edge_term<R, KIND>(a.bc, wi, Wl[li * PL + a.nx - 1]);
     if (x == a.nx - 1) r += edge_term<R, KIND>(a.bc, wi, Wl[li * PL]);
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
     R* F = B2;                     // r lines (forward-transform input)
     R* T2 = (W == B0) ? B1 : B0;   // scratch for the forward transform
     R* base = W;                   // lines R is applied to
-    if (a.power == 2) {
+    if (a.form == FORM_CTC) {
       // g = v + R w on all lines (partners included)
       for (int idx = tid; idx < nl * nx; idx += nt) {
         const int l = idx / nx, x = idx - l * nx;
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
   }
 
   // M_LAST / M_LAST_PLAIN: A v = g + h
-  const R* gsrc = (a.power == 2) ? (const R*)(a.G + (size_t)s * n) : vsrc;
+  const R* gsrc = (a.form == FORM_CTC) ? (const R*)(a.G + (size_t)s * n) : vsrc;
   Dots<R> d;
   d.zero();
   if (MODE == M_LAST_PLAIN) {
@@ -548,9 +550,11 @@ PArgs<R> base_args(const PrecondTables& t, const Grid& g, const void* kappa2, do
   a.lognx = t.lognx;
   a.logny = t.logny;
   a.power = t.power;
+  a.form = t.form;
   a.bc = g.bc;
   a.rb = t.rb;
   a.kbar2 = (R)t.kbar2;
+  a.roff = t.form == FORM_DIAG ? (R)0 : (R)t.kbar2;
   const double norm = t.kind == GMRF_PREC_CIRCULANT ? 2.0 / ((double)t.nx * t.ny) : 4.0 / ((double)t.nx * t.ny);
   a.dscale = (R)norm;
   a.lamx = (const R*)t.lamx;
@@ -564,7 +568,7 @@ PArgs<R> base_args(const PrecondTables& t, const Grid& g, const void* kappa2, do
   a.G = (R*)t.G;
   a.Wg = (R*)t.Wg;
   a.kappa2 = (const float*)kappa2;
-  a.kappa2_const = (R)kc;
+  a.kappa2_const = t.form == FORM_DIAG ? (R)0 : (R)kc;  // FORM_DIAG without a field: D = 0
   a.n = g.n;
   return a;
 }
@@ -593,7 +597,7 @@ size_t col_smem(const PrecondTables& t, int cw) {
 int ensure_ws(PrecondTables& t, int nvec, cudaStream_t st) {
   const size_t es = t.fp64 ? 8 : 4;
   const size_t sb = (size_t)nvec * t.ny * (t.nx + 2) * es;
-  const size_t gb = t.power == 2 ? (size_t)nvec * t.nx * t.ny * es : 16;
+  const size_t gb = t.form == FORM_CTC ? (size_t)nvec * t.nx * t.ny * es : 16;
   if (t.S_bytes < sb) {
     if (t.S) cudaFreeAsync(t.S, st);
     t.S = nullptr;
@@ -632,7 +636,9 @@ fast::Args fast_args(const PrecondTables& t, const Grid& g, const void* kappa2, 
   a.ny = t.ny;
   a.bc = g.bc;
   a.power = t.power;
+  a.form = t.form;
   a.kbar2 = (float)t.kbar2;
+  a.roff = t.form == FORM_DIAG ? 0.f : (float)t.kbar2;
   a.dscale = (float)(t.kind == GMRF_PREC_CIRCULANT ? 2.0 / ((double)t.nx * t.ny) : 4.0 / ((double)t.nx * t.ny));
   a.lamx = (const float*)t.lamx;
   a.lamy = (const float*)t.lamy;
@@ -645,7 +651,7 @@ fast::Args fast_args(const PrecondTables& t, const Grid& g, const void* kappa2, 
   a.G = (float*)t.G;
   a.Wg = (float*)t.Wg;
   a.kappa2 = (const float*)kappa2;
-  a.kappa2_const = (float)kc;
+  a.kappa2_const = t.form == FORM_DIAG ? 0.f : (float)kc;  // FORM_DIAG without a field: D = 0
   a.n = g.n;
   return a;
 }
@@ -888,7 +894,8 @@ bool precond_size_ok(int64_t n) {
 int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar2, bool fp64, cudaStream_t s,
                   double* logdet_M) {
   t.kind = kind;
-  t.power = op == GMRF_OP_SPDE_SQUARED ? 2 : 1;
+  t.power = op == GMRF_OP_SHIFTED_LAPLACIAN ? 1 : 2;
+  t.form = op == GMRF_OP_SHIFTED_LAPLACIAN ? FORM_SHIFT : (op == GMRF_OP_SPDE_SQUARED ? FORM_CTC : FORM_DIAG);
   t.nx = g.nx;
   t.ny = g.ny;
   t.lognx = ilog2(g.nx);

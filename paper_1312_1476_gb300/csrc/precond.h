@@ -11,6 +11,12 @@ namespace gmrf {
 
 enum { PRE_INV_SQRT = 0 };
 
+// Form of the preconditioned operator A = M^{-1/2} Q M^{-1/2} (tau-free):
+//   FORM_SHIFT  A = I + P R P, P = B_bar^{-1/2}, R = K - kappa_bar^2 (+ boundary edges)   (shifted Laplacian)
+//   FORM_CTC    A = C^T C, C = I + R B_bar^{-1}, same R                                   (SPDE squared)
+//   FORM_DIAG   A = I + P D P, P = B_bar^{-1}, R = D the diagonal field, no edge terms     (SPDE plus diagonal)
+enum { FORM_SHIFT = 1, FORM_CTC = 2, FORM_DIAG = 3 };
+
 // Tables and workspace of the preconditioner M = tau * B_bar^p with
 // B_bar = kappa_bar^2 I + L_prec (L_prec the torus Laplacian for CIRCULANT,
 // the cell-centred Neumann Laplacian for MIRROR), p = 1 (shifted Laplacian)
@@ -19,7 +25,8 @@ enum { PRE_INV_SQRT = 0 };
 // (kappa_bar^2 + lambda_x + lambda_y)^{-p/2}.
 struct PrecondTables {
   int kind = 0;   // GMRF_PREC_CIRCULANT or GMRF_PREC_MIRROR
-  int power = 1;  // p
+  int power = 1;  // p (symbol exponent)
+  int form = FORM_SHIFT;
   int nx = 0, ny = 0, lognx = 0, logny = 0;
   bool fp64 = false;
   double kbar2 = 0.0;

@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
       const size_t rp = (size_t)((y == 0) ? a.ny - 1 : 0) * NX;
       // partner row's g (needed for the y-term of R g at this row)
       float2 gp[E];
-      if (hy && a.power == 2) {
+      if (hy && a.form == FORM_CTC) {
         float wpf = 0.f, wpl = 0.f;
         float2 wp[E];
         load_row<KIND, E>(wp, wg + rp);
@@ -660,8 +660,8 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
           const size_t o = rp + pair_off<KIND, E>(lane, i);
           const float2 kk = a.kappa2 ? *reinterpret_cast<const float2*>(a.kappa2 + o) : f2(a.kappa2_const, a.kappa2_const);
           const float2 vp = *reinterpret_cast<const float2*>(vsrc + o);
-          float2 t = f2(vp.x + (kk.x - a.kbar2) * wp[i].x + edge_val<KIND>(a.bc, wp[i].x, w[i].x),
-                        vp.y + (kk.y - a.kbar2) * wp[i].y + edge_val<KIND>(a.bc, wp[i].y, w[i].y));
+          float2 t = f2(vp.x + (kk.x - a.roff) * wp[i].x + edge_val<KIND>(a.bc, wp[i].x, w[i].x),
+                        vp.y + (kk.y - a.roff) * wp[i].y + edge_val<KIND>(a.bc, wp[i].y, w[i].y));
           if (lane == 0 && i == 0) t.x += edge_val<KIND>(a.bc, wp[0].x, wpl);
           if (lane == 31 && i == E - 1) t.y += edge_val<KIND>(a.bc, wp[E - 1].y, wpf);
           gp[i] = t;
@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
       for (int i = 0; i < E; ++i) {
         const size_t o = ro + pair_off<KIND, E>(lane, i);
         const float2 kk = a.kappa2 ? *reinterpret_cast<const float2*>(a.kappa2 + o) : f2(a.kappa2_const, a.kappa2_const);
-        float2 t = f2((kk.x - a.kbar2) * w[i].x, (kk.y - a.kbar2) * w[i].y);
+        float2 t = f2((kk.x - a.roff) * w[i].x, (kk.y - a.roff) * w[i].y);
         if (ex && lane == 0 && i == 0) t.x += edge_val<KIND>(a.bc, w[0].x, wl);
         if (ex && lane == 31 && i == E - 1) t.y += edge_val<KIND>(a.bc, w[E - 1].y, wf);
         if (hy) {
@@ -686,13 +686,13 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
           t.x += edge_val<KIND>(a.bc, w[i].x, wq.x);
           t.y += edge_val<KIND>(a.bc, w[i].y, wq.y);
         }
-        if (a.power == 2) {
+        if (a.form == FORM_CTC) {
           const float2 vv = *reinterpret_cast<const float2*>(vsrc + o);
           t = add2(vv, t);
         }
         w[i] = t;
       }
-      if (a.power == 2) {
+      if (a.form == FORM_CTC) {
         store_row<KIND, E>(w, a.G + (size_t)s * n + ro);
         // r = R g (in place)
         float gf = 0.f, gl = 0.f;
@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
         for (int i = 0; i < E; ++i) {
           const size_t o = ro + pair_off<KIND, E>(lane, i);
           const float2 kk = a.kappa2 ? *reinterpret_cast<const float2*>(a.kappa2 + o) : f2(a.kappa2_const, a.kappa2_const);
-          float2 t = f2((kk.x - a.kbar2) * w[i].x, (kk.y - a.kbar2) * w[i].y);
+          float2 t = f2((kk.x - a.roff) * w[i].x, (kk.y - a.roff) * w[i].y);
           if (ex && lane == 0 && i == 0) t.x += edge_val<KIND>(a.bc, w[0].x, gl);
           if (ex && lane == 31 && i == E - 1) t.y += edge_val<KIND>(a.bc, w[E - 1].y, gf);
           if (hy) {
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
     return;
   }
   // R_LAST: A v = g + h
-  const float* gsrc = a.power == 2 ? a.G + (size_t)s * n : vsrc;
+  const float* gsrc = a.form == FORM_CTC ? a.G + (size_t)s * n : vsrc;
   if (a.in) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {

@@ -12,7 +12,9 @@ namespace fast {
 // Arguments of the FP32 register-FFT preconditioner kernels.
 struct Args {
   int nx, ny, bc, power;
+  int form;      // FORM_SHIFT / FORM_CTC / FORM_DIAG (precond.h)
   float kbar2, dscale;
+  float roff;    // R = K - roff
   const float* lamx;
   const float* lamy;
   const float2* twx;   // exp(-2 pi i t / nx)

@@ -32,7 +32,7 @@ ERR_TIMEOUT = -7
 ERR_UNSUPPORTED = -8
 
 BC = {"periodic": 0, "neumann": 1, "dirichlet": 2}
-OP = {"shifted_laplacian": 0, "spde_squared": 1}
+OP = {"shifted_laplacian": 0, "spde_squared": 1, "spde_plus_diag": 2}
 PREC = {"none": 0, "circulant": 1, "mirror": 2}
 PRECISION = {"fp32": 0, "fp64": 1}
 

@@ -1,0 +1,164 @@
+"""GPU parity of the circulant-plus-diagonal operator Q = tau ((kp + L)^2 + D)
+of the sMMALA proposal (Sections 3 and 5.1), preconditioned by the prior
+(Proposition 1), and the Table 1 behaviour: the preconditioned sampler's m
+does not grow with the grid, the unpreconditioned one does."""
+import numpy as np
+import pytest
+
+from oracle import exact, lanczos as olz, precond, stencil
+from paper_1312_1476_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_1312_1476_gb300 import gmrf
+    assert torch.cuda.is_available()
+    return gmrf
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b))
+
+
+def _model_Q(shape, bc, mdl):
+    return stencil.precision_matrix(shape, bc, "spde_plus_diag", mdl["d"].astype(np.float64), mdl["tau"],
+                                    kappa2_prior=mdl["kappa2_prior"])
+
+
+def _problem(g, shape, bc, mdl, precond="none", precision="fp32", diag=True):
+    return g.Problem(shape, bc, "spde_plus_diag", kappa2=_dev(mdl["d"]) if diag else None,
+                     kappa2_const=mdl["kappa2_prior"], tau=mdl["tau"], precond=precond, precision=precision)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("diag", [True, False])
+def test_stencil_apply(g, bc, precision, diag):
+    shape = (40, 24)
+    n = 960
+    # a diagonal comparable to the prior part, so that both terms are checked
+    mdl = {"kappa2_prior": 0.3, "tau": 1.7, "d": inputs.kappa2_uniform_field(shape, seed=4, lo=0.5, hi=3.0)}
+    d = mdl["d"] if diag else np.zeros(shape, dtype=np.float32)
+    Q = stencil.precision_matrix(shape, bc, "spde_plus_diag", d.astype(np.float64), mdl["tau"],
+                                 kappa2_prior=mdl["kappa2_prior"])
+    dt = np.float64 if precision == "fp64" else np.float32
+    V = inputs.gaussian_vectors(2, n, seed=4, dtype=dt)
+    with _problem(g, shape, bc, mdl, precision=precision, diag=diag) as p:
+        y = torch.empty(2 * n, dtype=torch.from_numpy(V).dtype, device="cuda")
+        p.apply(0, _dev(V), y, nvec=2)
+        Y = y.cpu().numpy().reshape(2, n)
+    for s in range(2):
+        assert _rel(Y[s], Q @ V[s].astype(np.float64)) <= (1e-13 if precision == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("N,bc,kind", [(16, "periodic", "circulant"), (32, "neumann", "mirror"),
+                                       (128, "periodic", "circulant"), (128, "neumann", "mirror"),
+                                       (1024, "periodic", "circulant"), (1024, "neumann", "mirror")])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_preconditioned_operator(g, N, bc, kind, precision):
+    shape = (N, N)
+    n = N * N
+    mdl = inputs.lgcp_smmala_model(N)
+    Q = _model_Q(shape, bc, mdl)
+    okind = "periodic" if kind == "circulant" else "neumann"
+    A = olz.preconditioned_operator(Q, shape, okind, "spde_squared", mdl["kappa2_prior"], mdl["tau"])
+    dt = np.float64 if precision == "fp64" else np.float32
+    V = inputs.gaussian_vectors(2, n, seed=6, dtype=dt)
+    with _problem(g, shape, bc, mdl, precond=kind, precision=precision) as p:
+        y = torch.empty(2 * n, dtype=torch.from_numpy(V).dtype, device="cuda")
+        p.apply(1, _dev(V), y, nvec=2)
+        Y = y.cpu().numpy().reshape(2, n)
+    # FP64: rounding of the 2-D transforms grows with log n (1.1e-12 seen at 1024^2)
+    tol64 = 1e-12 if N <= 128 else 5e-12
+    for s in range(2):
+        assert _rel(Y[s], A(V[s].astype(np.float64))) <= (tol64 if precision == "fp64" else 3e-6)
+
+
+@pytest.mark.parametrize("pre", ["none", "circulant"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_sample_vs_dense(g, pre, precision):
+    N = 16
+    shape = (N, N)
+    mdl = inputs.lgcp_smmala_model(N)
+    Q = _model_Q(shape, "periodic", mdl)
+    dt = np.float64 if precision == "fp64" else np.float32
+    Z = inputs.gaussian_vectors(3, N * N, seed=8, dtype=dt)
+    if pre == "none":
+        Xe = exact.sample_dense(Q, Z.astype(np.float64))
+    else:
+        Xe = precond.sample_prop1_dense(Q, shape, "periodic", "spde_squared", mdl["kappa2_prior"], mdl["tau"],
+                                        Z.astype(np.float64))
+    with _problem(g, shape, "periodic", mdl, precond=pre, precision=precision) as p:
+        x = torch.empty(3 * N * N, dtype=torch.from_numpy(Z).dtype, device="cuda")
+        tol = 1e-11 if precision == "fp64" else 1e-6
+        rc, info = p.sample(x, nsamples=3, tol=tol, m_max=4000, z=_dev(Z), check_every=4)
+    assert rc == g.OK
+    X = x.cpu().numpy().reshape(3, N * N)
+    for s in range(3):
+        assert _rel(X[s], Xe[s]) <= (1e-10 if precision == "fp64" else 1e-6)
+
+
+def test_logdet_fixed_probes(g):
+    N = 16
+    shape = (N, N)
+    mdl = inputs.lgcp_smmala_model(N)
+    Q = _model_Q(shape, "periodic", mdl)
+    R = inputs.rademacher_vectors(4, N * N, seed=9, dtype=np.float64)
+    with _problem(g, shape, "periodic", mdl, precond="circulant", precision="fp64") as p:
+        ld, se, q, info, rc = p.logdet(nprobes=4, tol=1e-10, m_max=400, probes=_dev(R))
+    assert rc == g.OK
+    # q_i are the quadratures of log(A); log det Q = mean q_i + log det M (Section 6.2)
+    A, _ = precond.preconditioned_operator_dense(Q, shape, "periodic", "spde_squared", mdl["kappa2_prior"],
+                                                 mdl["tau"])
+    qe = exact.quadform_log_dense(A, R)
+    np.testing.assert_allclose(q, qe, rtol=1e-8, atol=1e-8 * np.abs(qe).max())
+    ldM = precond.logdet(shape, "periodic", "spde_squared", mdl["kappa2_prior"], mdl["tau"])
+    assert abs(ld - (qe.mean() + ldM)) <= 1e-9 * abs(ld)
+
+
+def test_table1_preconditioned_m_flat_unpreconditioned_grows(g):
+    # Table 1 (Section 5.1), tol 1e-8, FP64: m of the prior-preconditioned
+    # sampler against the grid side N, and the unpreconditioned m at small N;
+    # the small sizes also against the oracle's Algorithm 1 with the same rule
+    ms_pre, ms_un = {}, {}
+    for N in (16, 32, 64, 128, 256, 512):
+        mdl = inputs.lgcp_smmala_model(N)
+        z = inputs.gaussian_vectors(1, N * N, seed=2, dtype=np.float64)
+        with _problem(g, (N, N), "periodic", mdl, precond="circulant", precision="fp64") as p:
+            x = torch.empty(N * N, dtype=torch.float64, device="cuda")
+            rc, info = p.sample(x, nsamples=1, tol=1e-8, m_max=200, z=_dev(z), check_every=1)
+            assert rc == g.OK
+            ms_pre[N] = info[0].m_used
+        if N <= 64:
+            with _problem(g, (N, N), "periodic", mdl, precision="fp64") as p:
+                x = torch.empty(N * N, dtype=torch.float64, device="cuda")
+                rc, info = p.sample(x, nsamples=1, tol=1e-8, m_max=8000, z=_dev(z), check_every=1)
+                assert rc == g.OK
+                ms_un[N] = info[0].m_used
+            Q = _model_Q((N, N), "periodic", mdl)
+            A = olz.preconditioned_operator(Q, (N, N), "periodic", "spde_squared", mdl["kappa2_prior"], mdl["tau"])
+            _, m_or, _, st = olz.adaptive_sample(A, z[0], 1e-8, 200)
+            assert st == "ok" and abs(ms_pre[N] - m_or) <= 1
+    assert max(ms_pre.values()) - min(ms_pre.values()) <= 1 and max(ms_pre.values()) <= 12
+    assert ms_un[16] < ms_un[32] < ms_un[64] and ms_un[64] > 50 * max(ms_pre.values())
+
+
+def test_rejects_unmatched_preconditioner(g):
+    mdl = inputs.lgcp_smmala_model(16)
+    with pytest.raises(g.GmrfError):
+        _problem(g, (16, 16), "neumann", mdl, precond="circulant")
+    with pytest.raises(g.GmrfError):
+        _problem(g, (16, 16), "periodic", mdl, precond="mirror")
+    bad = dict(mdl)
+    bad["d"] = mdl["d"].copy()
+    bad["d"][3, 3] = -1.0
+    with pytest.raises(g.GmrfError):
+        _problem(g, (16, 16), "periodic", bad)

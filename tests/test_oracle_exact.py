@@ -9,6 +9,7 @@ from oracle import exact, stencil
 from paper_1312_1476_gb300 import inputs
 
 SHAPES = [(6, 8), (5, 7), (3, 4, 5)]
+KP = 0.45  # the prior's constant of spde_plus_diag (ignored by the other operators)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -17,7 +18,7 @@ SHAPES = [(6, 8), (5, 7), (3, 4, 5)]
 def test_dense_sample_is_principal_inverse_sqrt(shape, bc, op):
     rng = np.random.default_rng(3)
     k2 = rng.uniform(0.05, 1.0, size=shape)
-    Q = stencil.precision_matrix(shape, bc, op, k2, tau=1.3)
+    Q = stencil.precision_matrix(shape, bc, op, k2, tau=1.3, kappa2_prior=KP)
     z = inputs.gaussian_vectors(2, int(np.prod(shape)), seed=5, dtype=np.float64)
     x = exact.sample_dense(Q, z)
     for xi, zi in zip(x, z):
@@ -33,10 +34,10 @@ def test_dense_sample_is_principal_inverse_sqrt(shape, bc, op):
 @pytest.mark.parametrize("bc", stencil.BCS)
 @pytest.mark.parametrize("op", stencil.OPS)
 def test_spectral_sample_matches_dense(shape, bc, op):
-    Q = stencil.precision_matrix(shape, bc, op, 0.2, tau=0.7)
+    Q = stencil.precision_matrix(shape, bc, op, 0.2, tau=0.7, kappa2_prior=KP)
     z = inputs.gaussian_vectors(1, int(np.prod(shape)), seed=11, dtype=np.float64)[0]
     xd = exact.sample_dense(Q, z)[0]
-    xs = exact.sample_spectral(shape, bc, op, 0.2, 0.7, z)
+    xs = exact.sample_spectral(shape, bc, op, 0.2, 0.7, z, kappa2_prior=KP)
     np.testing.assert_allclose(xs, xd, rtol=1e-10, atol=1e-10 * np.linalg.norm(xd))
 
 
@@ -53,9 +54,9 @@ def test_tau_scaling():
 @pytest.mark.parametrize("bc", stencil.BCS)
 @pytest.mark.parametrize("op", stencil.OPS)
 def test_logdet_three_routes(shape, bc, op):
-    Q = stencil.precision_matrix(shape, bc, op, 0.25, tau=1.9)
+    Q = stencil.precision_matrix(shape, bc, op, 0.25, tau=1.9, kappa2_prior=KP)
     ld_chol = exact.logdet_cholesky(Q)
-    ld_spec = exact.logdet_spectral(shape, bc, op, 0.25, 1.9)
+    ld_spec = exact.logdet_spectral(shape, bc, op, 0.25, 1.9, kappa2_prior=KP)
     lu = spla.splu(Q.tocsc())
     ld_lu = float(np.sum(np.log(np.abs(lu.U.diagonal()))))
     assert abs(ld_chol - ld_spec) <= 1e-10 * abs(ld_spec) + 1e-10

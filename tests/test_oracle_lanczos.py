@@ -10,7 +10,7 @@ from paper_1312_1476_gb300 import inputs
 def _problem(shape=(6, 7), bc="neumann", op="spde_squared", seed=4, tau=1.0):
     rng = np.random.default_rng(seed)
     k2 = rng.uniform(0.05, 0.6, size=shape)
-    Q = stencil.precision_matrix(shape, bc, op, k2, tau)
+    Q = stencil.precision_matrix(shape, bc, op, k2, tau, kappa2_prior=0.45)
     return k2, Q
 
 

@@ -16,8 +16,9 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 def test_kronecker_assembly_matches_bruteforce(shape, bc, op):
     rng = np.random.default_rng(7)
     k2 = rng.uniform(0.1, 2.0, size=shape)
-    Q = stencil.precision_matrix(shape, bc, op, k2, tau=1.7).toarray()
-    Qb = stencil.precision_matrix_bruteforce(shape, bc, op, k2, tau=1.7)
+    # kappa2_prior is the prior's constant of spde_plus_diag (ignored by the other operators)
+    Q = stencil.precision_matrix(shape, bc, op, k2, tau=1.7, kappa2_prior=0.6).toarray()
+    Qb = stencil.precision_matrix_bruteforce(shape, bc, op, k2, tau=1.7, kappa2_prior=0.6)
     np.testing.assert_allclose(Q, Qb, rtol=0, atol=1e-12)
     np.testing.assert_allclose(Q, Q.T, atol=0)
 
@@ -35,8 +36,8 @@ def test_1d_closed_form_eigenpairs(n, bc):
 @pytest.mark.parametrize("bc", stencil.BCS)
 @pytest.mark.parametrize("op", stencil.OPS)
 def test_lattice_eigenvalues_match_dense(shape, bc, op):
-    Q = stencil.precision_matrix(shape, bc, op, 0.3, tau=2.0).toarray()
-    lam = np.sort(stencil.operator_eigenvalues(shape, bc, op, 0.3, 2.0).reshape(-1))
+    Q = stencil.precision_matrix(shape, bc, op, 0.3, tau=2.0, kappa2_prior=0.6).toarray()
+    lam = np.sort(stencil.operator_eigenvalues(shape, bc, op, 0.3, 2.0, kappa2_prior=0.6).reshape(-1))
     np.testing.assert_allclose(np.linalg.eigvalsh(Q), lam, rtol=1e-10, atol=1e-10)
 
 
@@ -96,6 +97,18 @@ def test_precision_rows_match_bruteforce(shape, bc, op):
     k = rng.uniform(0.1, 1.0, size=shape)
     n = int(np.prod(shape))
     rows = rng.choice(n, size=min(n, 9), replace=False)
-    Qb = stencil.precision_matrix_bruteforce(shape, bc, op, k, tau=1.3)
-    R = stencil.precision_rows(shape, bc, op, k, 1.3, rows).toarray()
+    Qb = stencil.precision_matrix_bruteforce(shape, bc, op, k, tau=1.3, kappa2_prior=0.45)
+    R = stencil.precision_rows(shape, bc, op, k, 1.3, rows, kappa2_prior=0.45).toarray()
     np.testing.assert_allclose(R, Qb[rows], rtol=0, atol=1e-12)
+
+
+def test_spde_plus_diag_is_prior_plus_diagonal():
+    # Q = tau ((kp + L)^2 + D): the spde_squared matrix with constant kp plus tau D
+    shape = (5, 6)
+    rng = np.random.default_rng(3)
+    d = rng.uniform(0.0, 2.0, size=shape)
+    d[1, 2] = 0.0
+    for bc in stencil.BCS:
+        Q = stencil.precision_matrix_bruteforce(shape, bc, "spde_plus_diag", d, tau=0.7, kappa2_prior=0.4)
+        Qp = stencil.precision_matrix_bruteforce(shape, bc, "spde_squared", 0.4, tau=0.7)
+        np.testing.assert_allclose(Q - Qp, 0.7 * np.diag(d.reshape(-1)), rtol=0, atol=1e-13)
