@@ -22,10 +22,21 @@ bool fast_eligible(int kind, bool fp64, int nx, int ny) {
   return ny >= 128 && ny <= 2048;
 }
 
+// rows per block of the row kernels (the device layout's own rule)
+template <int KIND>
+static int rows_for(int nx) {
+  switch (nx) {
+    case 128: return fast::rows_per_block<KIND, 6>();
+    case 256: return fast::rows_per_block<KIND, 7>();
+    case 512: return fast::rows_per_block<KIND, 8>();
+    case 1024: return fast::rows_per_block<KIND, 9>();
+    case 2048: return fast::rows_per_block<KIND, 10>();
+    default: return 1;
+  }
+}
+
 int fast_rows_per_block(int kind, int nx) {
-  const int L = nx / 2, E = L / 32, G = 32 / E;
-  const int seg = kind == GMRF_PREC_MIRROR ? 8 : 4;
-  return G > seg ? G : seg;
+  return kind == GMRF_PREC_MIRROR ? rows_for<GMRF_PREC_MIRROR>(nx) : rows_for<GMRF_PREC_CIRCULANT>(nx);
 }
 
 }  // namespace gmrf
