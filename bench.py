@@ -426,6 +426,17 @@ def measure_variants(args, gmrf, torch, flush, peak):
             "m_mean": float(np.mean([i.m_used for i in infob])),
             "basis_bytes_per_vector_step": {"fp32": 4 * n, "bf16": 2 * n},
             "max_rel_diff_vs_fp32_basis": diff}
+        # two passes, no basis kept (O(n) memory per vector, twice the steps)
+        p.sample(xb, nsamples=ns, tol=TOL, m_max=m3, seed=40, v_storage="none")
+        mst, (rct, infot) = timed(lambda i: p.sample(xb, nsamples=ns, tol=TOL, m_max=m3, seed=40 + i,
+                                                     v_storage="none"), 3)
+        p.sample(x, nsamples=ns, tol=TOL, m_max=m3, seed=42)
+        out["3d_256_two_pass"] = {
+            "workload": "same 256^3 problem and 16 samples, no basis kept: the iteration runs twice and the "
+                        "second pass adds ||z|| y_j v_j after every step",
+            "samples_per_s": ns * 1e3 / mst, "ms_per_call": mst, "status": rct,
+            "basis_bytes_per_vector": {"stored_fp32": 4 * n * (m3 + 1), "two_pass": 4 * n * 2 + 8 * n},
+            "bitwise_equal_to_stored_basis": bool(torch.equal(xb, x))}
     out["table1"] = measure_table1(gmrf, torch)
     out["serving"] = measure_serving()
     return out

@@ -124,7 +124,14 @@ typedef struct {
  *             memory of V_m, so more vectors or larger m fit in HBM.  FP64
  *             problems return GMRF_ERR_UNSUPPORTED.  The paper stores V_m
  *             at working precision; this is an option of this library. */
-typedef enum { GMRF_VSTORE_NATIVE = 0, GMRF_VSTORE_BF16 = 1 } gmrf_vstore;
+/*   NONE   -- no basis kept: two passes.  The first runs the iteration with
+ *             only v_{j-1}, v_j and finds alpha, beta, m and y; the second
+ *             runs the same iteration again (bitwise the same, from the same
+ *             z) and adds ||z|| y_j v_j to x after every step.  x_m is
+ *             bitwise the one NATIVE returns; device memory per vector is
+ *             O(n) instead of (m_max + 1) n, for twice the steps.  Not in the
+ *             paper; an option of this library. */
+typedef enum { GMRF_VSTORE_NATIVE = 0, GMRF_VSTORE_BF16 = 1, GMRF_VSTORE_NONE = 2 } gmrf_vstore;
 
 typedef struct {
   double tol;          /* relative tolerance of the Theorem 1 estimate, > 0 */

@@ -92,6 +92,8 @@ struct StepGraph {
   int nvec = -1, nslots = 0, m_max = 0, c = 0, kernels_per_step = 1, zchunk = 0;
   double tol = 0.0;
   const void *W0 = nullptr, *V = nullptr, *Vb = nullptr, *st = nullptr, *S = nullptr, *partials = nullptr;
+  const void* Xacc = nullptr;
+  double xscale = 0.0;
   bool timed = false;
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -117,7 +119,7 @@ struct gmrf_problem {
   PrecondTables pre;
   // Lanczos workspace (grow-only)
   DevBuf W0, W1, V, st, alpha, beta, alpha_f, beta2_f, partials, counters, y, scratch, nodes, q, out2, stage,
-      stage2, work, Vb;
+      stage2, work, Vb, xacc, accn;
   VecState* st_host = nullptr;
   int st_host_cap = 0;
   int tune_bw = 0;  // vectors per Lanczos launch (0: as many as fit)
@@ -239,6 +241,7 @@ int launch_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, int
                 [&] { return launch_stencil_step(p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s); }));
     else
       CK(launch_precond_step(p->pre, p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s));
+    if (b.Xacc) CK(traced(KC_ASSEMBLE, s, 1, [&] { return launch_accumulate(p->fp64, p->g.n, b, s); }));
   }
   return GMRF_OK;
 }
@@ -249,7 +252,7 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   const void* S = p->precond ? p->pre.S : nullptr;
   if (G.exec && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c && G.tol == P.tol &&
       G.W0 == b.W[0] && G.V == b.V && G.Vb == b.Vb && G.st == b.st && G.S == S && G.partials == b.partials &&
-      G.timed == timed && G.zchunk == p->g.zchunk)
+      G.timed == timed && G.zchunk == p->g.zchunk && G.Xacc == b.Xacc && G.xscale == b.xscale)
     return GMRF_OK;
   G.reset();
   cudaStream_t s = p->ws;
@@ -282,11 +285,13 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   G.V = b.V;
   G.Vb = b.Vb;
   G.zchunk = p->g.zchunk;
+  G.Xacc = b.Xacc;
+  G.xscale = b.xscale;
   G.st = b.st;
   G.S = S;
   G.partials = b.partials;
   G.timed = timed;
-  G.kernels_per_step = p->precond ? 5 : 1;
+  G.kernels_per_step = (p->precond ? 5 : 1) + (b.Xacc ? 1 : 0);
   return GMRF_OK;
 }
 
@@ -484,7 +489,7 @@ void gmrf_destroy(gmrf_problem* p) {
   p->graph.reset();
   DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,
                     &p->partials, &p->counters, &p->y, &p->scratch, &p->nodes, &p->q, &p->out2, &p->stage,
-                    &p->stage2, &p->work, &p->Vb};
+                    &p->stage2, &p->work, &p->Vb, &p->xacc, &p->accn};
   for (DevBuf* b : bufs) release(*b, p->ws);
   precond_free(p->pre, p->ws);
   if (p->ws) cudaStreamSynchronize(p->ws);
@@ -498,17 +503,20 @@ void gmrf_destroy(gmrf_problem* p) {
 int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_result_info* info) {
   if (!p || !o || !x_out) return GMRF_ERR_INVALID;
   if (!(o->tol > 0.0) || !std::isfinite(o->tol) || o->m_max < 1 || o->m_max > 8192 || o->nsamples < 1 ||
-      (o->v_storage != GMRF_VSTORE_NATIVE && o->v_storage != GMRF_VSTORE_BF16))
+      (o->v_storage != GMRF_VSTORE_NATIVE && o->v_storage != GMRF_VSTORE_BF16 &&
+       o->v_storage != GMRF_VSTORE_NONE))
     return GMRF_ERR_INVALID;
   const bool bf16 = o->v_storage == GMRF_VSTORE_BF16;
+  const bool two_pass = o->v_storage == GMRF_VSTORE_NONE;
   if (bf16 && p->fp64) return GMRF_ERR_UNSUPPORTED;
   const size_t n = p->g.n, es = esize(p);
   const int m_max = o->m_max;
-  const int nslots = bf16 ? 2 : m_max + 1;
+  const int nslots = (bf16 || two_pass) ? 2 : m_max + 1;
   const bool x_dev = is_device_ptr(x_out);
   const bool z_dev = o->z_in && is_device_ptr(o->z_in);
   const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) : 0) +
-                       (bf16 ? (size_t)(m_max + 1) * n * sizeof(__nv_bfloat16) : 0);
+                       (bf16 ? (size_t)(m_max + 1) * n * sizeof(__nv_bfloat16) : 0) +
+                       (two_pass ? 2 * n * sizeof(float) + (p->precond ? n * es : 0) : 0);
   int chunk = batch_size(p, o->nsamples, nslots, m_max, true, extra);
   if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
   if (chunk < 1) return GMRF_ERR_OOM;
@@ -519,31 +527,52 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
     const int c = std::min(chunk, o->nsamples - s0);
     LanczosBufs b;
     CKR(ensure_lanczos(p, c, nslots, m_max, true, b, bf16));
-    if (o->z_in) {
-      const char* src = (const char*)o->z_in + (size_t)s0 * n * es;
-      CK(cudaMemcpyAsync(b.W[0], src, (size_t)c * n * es, z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                         s));
-    } else {
-      CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, c, (int64_t)n, o->seed, s0, b.W[0], s); }));
-    }
+    auto load_z = [&]() -> int {
+      if (o->z_in) {
+        const char* src = (const char*)o->z_in + (size_t)s0 * n * es;
+        CK(cudaMemcpyAsync(b.W[0], src, (size_t)c * n * es,
+                           z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      } else {
+        CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, c, (int64_t)n, o->seed, s0, b.W[0], s); }));
+      }
+      return GMRF_OK;
+    };
+    CKR(load_z());
     CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
     CK(traced(KC_TM, s, 3, [&] {
       return launch_tm_inv_sqrt(b, p->fp64, (TmNodes*)p->nodes.p, (double*)p->scratch.p, (double*)p->y.p, s);
     }));
+    if (two_pass) {
+      // second pass: the same iteration again (bitwise: same z, same kernels),
+      // adding ||z|| y_j v_j to x after every step instead of keeping V_m
+      const size_t xb = (size_t)c * n * (p->fp64 ? sizeof(double) : 2 * sizeof(float));
+      CKR(ensure(p->xacc, xb, p->ws));
+      CKR(ensure(p->accn, sizeof(int) * c, p->ws));
+      CK(cudaMemsetAsync(p->xacc.p, 0, xb, s));
+      CK(cudaMemsetAsync(p->accn.p, 0, sizeof(int) * c, s));
+      b.Xacc = p->xacc.p;
+      b.acc = (int*)p->accn.p;
+      b.y = (const double*)p->y.p;
+      b.xscale = p->precond == GMRF_PREC_NONE ? 1.0 / std::sqrt(p->tau) : 1.0;
+      CKR(load_z());
+      CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
+    }
     void* xdst = (char*)x_out + (size_t)s0 * n * es;
     if (!x_dev) {
       CKR(ensure(p->stage, (size_t)c * n * es, p->ws));
       xdst = p->stage.p;
     }
+    // x_m = ||z|| V_m y (one pass) or the accumulated sum (two passes)
+    auto assemble = [&](double extra, void* dst) -> cudaError_t {
+      return two_pass ? launch_accumulate_finish(p->fp64, n, b, dst, s)
+                      : launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, extra, dst, s);
+    };
     if (p->precond == GMRF_PREC_NONE) {
-      CK(traced(KC_ASSEMBLE, s, 1, [&] {
-        return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0 / std::sqrt(p->tau), xdst, s);
-      }));
+      CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0 / std::sqrt(p->tau), xdst); }));
     } else {
       // u = ||z|| V_m y, then x = M^{-1/2} u = tau^{-1/2} B_bar^{-p/2} u (Proposition 1)
       CKR(ensure(p->work, (size_t)c * n * es, p->ws));
-      CK(traced(KC_ASSEMBLE, s, 1,
-                [&] { return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
+      CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0, p->work.p); }));
       CK(traced(KC_PRE_APPLY, s, 3,
                 [&] { return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, p->work.p, xdst, c, s); }));
       CK(traced(KC_OTHER, s, 1,

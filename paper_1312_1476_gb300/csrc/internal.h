@@ -37,6 +37,13 @@ struct LanczosBufs {
   int nvec;
   int nslots;
   int m_max;
+  // Two-pass sampling (second pass): after each step x += ||z|| extra y_j v_j
+  // into Xacc ([nvec][2][n] float sum/compensation, or [nvec][n] double);
+  // acc[s] counts the basis vectors already added.  Xacc null: no accumulation.
+  void* Xacc = nullptr;
+  int* acc = nullptr;
+  const double* y = nullptr;  // [nvec][m_max] from the first pass
+  double xscale = 1.0;
 };
 
 // lanczos_stencil.cu --------------------------------------------------------
@@ -75,6 +82,11 @@ cudaError_t launch_lanczos_init(bool fp64, size_t n, const LanczosBufs& b, cudaS
 // x[s] = scale[s] * V_m y  (scale = ||z|| * extra), y from tm buffers.
 cudaError_t launch_assemble(bool fp64, size_t n, const LanczosBufs& b, const double* y, int y_stride,
                             double extra_scale, void* x, cudaStream_t s);
+// Two-pass sampling: add the newest basis vector of each vector to Xacc
+// (after a step), and x = Xacc (sum + compensation) at the end; the same
+// arithmetic, in the same order, as launch_assemble.
+cudaError_t launch_accumulate(bool fp64, size_t n, const LanczosBufs& b, cudaStream_t s);
+cudaError_t launch_accumulate_finish(bool fp64, size_t n, const LanczosBufs& b, void* x, cudaStream_t s);
 cudaError_t launch_convert(bool to_fp64, const void* in, void* out, size_t count, cudaStream_t s);
 cudaError_t launch_scale(bool fp64, void* x, size_t count, double a, cudaStream_t s);
 

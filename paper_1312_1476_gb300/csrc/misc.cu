@@ -199,6 +199,63 @@ __global__ void k_assemble(const S* __restrict__ V, int nslots, size_t n, const 
   }
 }
 
+// Two-pass sampling: x += scale_s y_j v_j for the basis vector v_j the step
+// just formed (j = acc[s] if the step ran for vector s), with the arithmetic
+// of k_assemble per element.  acc[s] advances in the vector's last block,
+// after every block has read it.
+template <typename T>
+__global__ void k_accumulate(const T* __restrict__ V, int nslots, size_t n, const VecState* st, const double* y,
+                             int m_max, double extra, void* X, int* acc, unsigned* counters) {
+  __shared__ int s_flag;
+  const int s = blockIdx.y;
+  const VecState v = st[s];
+  const int a = acc[s];
+  const bool work = a < v.m;
+  if (work) {
+    const T* vj = V + ((size_t)s * nslots + (size_t)(a % nslots)) * n;
+    const double yy = y[(size_t)s * m_max + a] * (v.znorm * extra);
+    if (sizeof(T) == 4) {
+      float* xh = (float*)X + (size_t)s * 2 * n;
+      float* xl = xh + n;
+      const float h = (float)yy;
+      const float l = (float)(yy - (double)h);
+      for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float vv = (float)vj[i];
+        const float t = __fmaf_rn(vv, h, __fmul_rn(vv, l));
+        const float sum = xh[i];
+        const float s2 = __fadd_rn(sum, t);
+        xl[i] = __fadd_rn(xl[i], fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t)
+                                                         : __fadd_rn(__fsub_rn(t, s2), sum));
+        xh[i] = s2;
+      }
+    } else {
+      double* xd = (double*)X + (size_t)s * n;
+      for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        xd[i] = fma((double)vj[i], yy, xd[i]);
+    }
+  }
+  if (last_block(counters, s, gridDim.x, &s_flag) && threadIdx.x == 0 && work) acc[s] = a + 1;
+}
+
+// x = sum + compensation (FP32) or the FP64 sum; failures filled as k_assemble does.
+template <typename T>
+__global__ void k_accumulate_finish(const void* X, size_t n, const VecState* st, T* x) {
+  const int s = blockIdx.y;
+  const VecState v = st[s];
+  T* xo = x + (size_t)s * n;
+  const bool bad = !(v.status == VS_DONE || v.status == GMRF_ERR_NOT_CONVERGED);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (bad || v.m == 0) {
+      xo[i] = (bad && v.status != VS_DONE) ? (T)NAN : (T)0;
+    } else if (sizeof(T) == 4) {
+      const float* xh = (const float*)X + (size_t)s * 2 * n;
+      xo[i] = (T)__fadd_rn(xh[i], xh[n + i]);
+    } else {
+      xo[i] = (T)((const double*)X)[(size_t)s * n + i];
+    }
+  }
+}
+
 template <typename A, typename B>
 __global__ void k_convert(const A* in, B* out, size_t count) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
@@ -321,6 +378,28 @@ cudaError_t launch_assemble(bool fp64, size_t n, const LanczosBufs& b, const dou
     k_assemble<float><<<grd, 256, sm, s>>>((const float*)b.V, b.nslots, n, b.st, y, y_stride, extra_scale,
                                            (float*)x);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(bool fp64, size_t n, const LanczosBufs& b, cudaStream_t s) {
+  int nblk = (int)((n + 255) / 256);
+  if (nblk > 2048) nblk = 2048;
+  dim3 grd(nblk, b.nvec);
+  if (fp64)
+    k_accumulate<double><<<grd, 256, 0, s>>>((const double*)b.V, b.nslots, n, b.st, b.y, b.m_max, b.xscale, b.Xacc,
+                                             b.acc, b.counters);
+  else
+    k_accumulate<float><<<grd, 256, 0, s>>>((const float*)b.V, b.nslots, n, b.st, b.y, b.m_max, b.xscale, b.Xacc,
+                                            b.acc, b.counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_finish(bool fp64, size_t n, const LanczosBufs& b, void* x, cudaStream_t s) {
+  int nblk = (int)((n + 255) / 256);
+  if (nblk > 2048) nblk = 2048;
+  dim3 grd(nblk, b.nvec);
+  if (fp64) k_accumulate_finish<double><<<grd, 256, 0, s>>>(b.Xacc, n, b.st, (double*)x);
+  else k_accumulate_finish<float><<<grd, 256, 0, s>>>(b.Xacc, n, b.st, (float*)x);
   return cudaGetLastError();
 }
 

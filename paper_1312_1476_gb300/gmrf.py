@@ -279,7 +279,7 @@ def rng(kind, nvec, n, seed, out, precision="fp32", stream=None):
         raise GmrfError(rc, "gmrf_rng")
 
 
-VSTORE = {"native": 0, "bf16": 1}
+VSTORE = {"native": 0, "bf16": 1, "none": 2}
 KERNEL_CLASSES = {"stencil_step": 0, "pre_row_fwd": 1, "pre_col": 2, "pre_row_mid": 3, "pre_row_last": 4,
                   "init": 5, "rng": 6, "tm": 7, "assemble": 8, "pre_apply": 9, "other": 10}
 

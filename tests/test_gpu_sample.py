@@ -198,6 +198,46 @@ def test_bf16_basis(g, shape, bc, op, pre):
         assert 1e-5 < r <= 3e-3
 
 
+TWO_PASS_CASES = [((24, 20), "neumann", "spde_squared", "none", "fp32"),
+                  ((24, 20), "dirichlet", "shifted_laplacian", "none", "fp64"),
+                  ((64, 64), "neumann", "spde_squared", "mirror", "fp64"),
+                  ((128, 256), "neumann", "spde_squared", "mirror", "fp32"),
+                  ((128, 128), "periodic", "spde_squared", "circulant", "fp32"),
+                  ((70, 9, 128), "dirichlet", "shifted_laplacian", "none", "fp32"),
+                  ((5, 6, 33), "periodic", "shifted_laplacian", "none", "fp32")]
+
+
+@pytest.mark.parametrize("shape,bc,op,pre,precision", TWO_PASS_CASES)
+def test_two_pass_equals_stored_basis(g, shape, bc, op, pre, precision):
+    # basis-free two-pass sampling reruns the same iteration and adds each
+    # basis vector as it appears: same m, same estimate, bitwise the same x
+    n = int(np.prod(shape))
+    k2 = inputs.kappa2_uniform_field(shape, seed=6, lo=0.1, hi=1.0)
+    dt = np.float64 if precision == "fp64" else np.float32
+    Z = inputs.gaussian_vectors(3, n, seed=12, dtype=dt)
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    with g.Problem(shape, bc, op, kappa2=_dev(k2), tau=1.3, precond=pre, precision=precision) as p:
+        tol = 1e-10 if precision == "fp64" else 1e-6
+        xa = torch.empty(3 * n, dtype=tdt, device="cuda")
+        xb = torch.empty(3 * n, dtype=tdt, device="cuda")
+        rc1, i1 = p.sample(xa, nsamples=3, tol=tol, m_max=900, z=_dev(Z))
+        rc2, i2 = p.sample(xb, nsamples=3, tol=tol, m_max=900, z=_dev(Z), v_storage="none")
+        # m_max too small: NOT_CONVERGED, still the same best x
+        xc = torch.empty(3 * n, dtype=tdt, device="cuda")
+        xd = torch.empty(3 * n, dtype=tdt, device="cuda")
+        rc3, i3 = p.sample(xc, nsamples=3, tol=tol, m_max=5, z=_dev(Z), raise_on_error=False)
+        rc4, i4 = p.sample(xd, nsamples=3, tol=tol, m_max=5, z=_dev(Z), v_storage="none", raise_on_error=False)
+        # device noise (regenerated for the second pass)
+        xe = torch.empty(2 * n, dtype=tdt, device="cuda")
+        xf = torch.empty(2 * n, dtype=tdt, device="cuda")
+        p.sample(xe, nsamples=2, tol=tol, m_max=900, seed=77)
+        p.sample(xf, nsamples=2, tol=tol, m_max=900, seed=77, v_storage="none")
+    assert rc1 == rc2 == g.OK and rc3 == rc4 == g.ERR_NOT_CONVERGED
+    for a, b in ((i1, i2), (i3, i4)):
+        assert [x.m_used for x in a] == [x.m_used for x in b] and [x.err_est for x in a] == [x.err_est for x in b]
+    assert torch.equal(xa, xb) and torch.equal(xc, xd) and torch.equal(xe, xf)
+
+
 def test_bf16_basis_rejected_where_unsupported(g):
     shape = (16, 16)
     z = inputs.gaussian_vectors(1, 256, seed=1, dtype=np.float64)
