@@ -2,12 +2,13 @@
 // register FFTs (see precond.cu for the operator they implement).
 //
 // A line of L = 32 E complex values (E = 2..32) is split over the 32 lanes of
-// a warp: lane l holds x[l + 32 r], r < E, for G = 32 / E lines at a time (32
-// complex values per lane); lines of L = 512 go one per warp (16 values per
-// lane, lfft16_*) so that a single 1024 x 1024 vector occupies more warps.  Forward FFT: E-point DFTs in registers,
-// twiddles W_L^{l k1}, one 32x33 shared-memory transpose, 32-point DFTs in
-// registers; the result X[k1 + E k2] sits in lane (g, k1) register k2
-// ("digit-reversed" layout).  The inverse runs the same steps backwards and
+// a warp: lane l holds x[l + 32 r], r < E.  Lines shorter than 1024 complex go
+// one per warp (E values per lane, lfft_*, 32-point stage split over lane
+// groups).  Lines of 1024 (E = 32) use wfft_*, which can also take G = 32 / E
+// lines per warp (32 values per lane): E-point DFTs in registers, twiddles
+// W_L^{l k1}, one 32x33 shared-memory transpose, 32-point DFTs in registers;
+// the result X[k1 + E k2] sits in lane (g, k1) register k2 ("digit-reversed"
+// layout).  The inverse runs the same steps backwards and
 // returns the strided layout, so a forward/inverse pair needs no extra
 // reordering.  Real transforms of length N = 2L use the half-length packing
 // of fft.cuh; the DCT-II packing u[m] = x[2m], u[N-1-m] = x[2m+1] is formed
@@ -140,80 +141,105 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return f2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
-// One line of L = 512 complex values per warp, 16 per lane: L = 16 x 32 with
-// the 32-point DFTs split over lane pairs.  Forward: in v[r] = z[lane + 32 r];
-// 16-point DFTs over r, twiddles W_L^{lane k1}, a 16 x 33 shared transpose so
-// that lane 2 k1 + h holds the entries l = 2 a + h of DFT k1, 16-point DFTs
-// over a, twiddles W_32^j on the odd half and a radix-2 butterfly between the
-// two lanes of a pair.  Out ("split layout"): lane 2 k1 + h, register j holds
-// Z[k1 + 16 j + 256 h].  tw[t] = exp(-2 pi i t / TN), TN = tws * L; sc: this
-// warp's 16 x 33 scratch.
-__device__ __forceinline__ int split_index(int lane, int j) { return (lane >> 1) + 16 * j + 256 * (lane & 1); }
+// One line of L = 32 E complex values per warp, E per lane (E = 2 .. 16):
+// L = E x 32 with each 32-point DFT split over S = 32 / E lanes.  Forward: in
+// v[r] = z[lane + 32 r]; E-point DFTs over r, twiddles W_L^{lane k1}, an
+// E x 33 shared transpose so that lane S k1 + h holds the entries l = S a + h
+// of DFT k1, E-point DFTs over a, twiddles W_32^{h j}, and an S-point DFT over
+// the lanes h (radix-2 stages by shuffle, decimation in frequency).  Out
+// ("split layout"): lane S k1 + h, register j holds Z[k1 + E j + E^2 brev(h)].
+// tw[t] = exp(-2 pi i t / TN), TN = tws * L; sc: this warp's E x 33 scratch.
+template <int E>
+__device__ __forceinline__ int split_index(int lane, int j) {
+  constexpr int S = 32 / E, LS = ilog2_c(S);
+  return lane / S + E * j + E * E * brev_c(lane % S, LS);
+}
 
-__device__ __forceinline__ void lfft16_fwd(float2 (&v)[16], float2* sc, const float2* __restrict__ tw, int tws) {
+template <int E>
+__device__ __forceinline__ void lfft_fwd(float2 (&v)[E], float2* sc, const float2* __restrict__ tw, int tws) {
+  constexpr int S = 32 / E;
   const int lane = threadIdx.x & 31;
-  reg_fft<16, false>(v);
+  reg_fft<E, false>(v);
 #pragma unroll
-  for (int k1 = 1; k1 < 16; ++k1) v[k1] = mul2(v[k1], tw[lane * k1 * tws]);
+  for (int k1 = 1; k1 < E; ++k1) v[k1] = mul2(v[k1], tw[lane * k1 * tws]);
   __syncwarp();
 #pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) sc[k1 * 33 + lane] = v[k1];
+  for (int k1 = 0; k1 < E; ++k1) sc[k1 * 33 + lane] = v[k1];
   __syncwarp();
-  const int k1 = lane >> 1, h = lane & 1;
+  const int k1 = lane / S, h = lane % S;
 #pragma unroll
-  for (int a = 0; a < 16; ++a) v[a] = sc[k1 * 33 + 2 * a + h];
-  reg_fft<16, false>(v);
+  for (int a = 0; a < E; ++a) v[a] = sc[k1 * 33 + S * a + h];
+  reg_fft<E, false>(v);
   if (h) {
 #pragma unroll
-    for (int j = 1; j < 16; ++j) v[j] = mul2(v[j], c_w32[j]);
+    for (int j = 1; j < E; ++j) v[j] = mul2(v[j], c_w32[S == 2 ? j : (h * j) & 31]);
   }
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const float2 t = shfl_xor2(v[j], 1);
-    v[j] = h ? sub2(t, v[j]) : add2(v[j], t);
+  for (int d = S / 2; d >= 1; d >>= 1) {
+    const bool up = (h & d) != 0;
+    const float2 w = c_w32[(h & (d - 1)) * (16 / d)];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const float2 t = shfl_xor2(v[j], d);
+      if (d == 1) v[j] = up ? sub2(t, v[j]) : add2(v[j], t);  // twiddle 1
+      else v[j] = up ? mul2(sub2(t, v[j]), w) : add2(v[j], t);
+    }
   }
 }
 
-// Inverse (unnormalised) of lfft16_fwd: split layout in, v[r] = L z[lane + 32 r] out.
-__device__ __forceinline__ void lfft16_inv(float2 (&v)[16], float2* sc, const float2* __restrict__ tw, int tws) {
+// Inverse (unnormalised) of lfft_fwd: split layout in, v[r] = L z[lane + 32 r] out.
+template <int E>
+__device__ __forceinline__ void lfft_inv(float2 (&v)[E], float2* sc, const float2* __restrict__ tw, int tws) {
+  constexpr int S = 32 / E;
   const int lane = threadIdx.x & 31;
-  const int k1 = lane >> 1, h = lane & 1;
+  const int k1 = lane / S, h = lane % S;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const float2 t = shfl_xor2(v[j], 1);
-    v[j] = h ? sub2(t, v[j]) : add2(v[j], t);
+  for (int d = 1; d < S; d <<= 1) {
+    const bool up = (h & d) != 0;
+    const float2 w = c_w32[(h & (d - 1)) * (16 / d)];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const float2 t = shfl_xor2(v[j], d);
+      if (d == 1) v[j] = up ? sub2(t, v[j]) : add2(v[j], t);  // twiddle 1
+      else v[j] = up ? sub2(t, mulc2(v[j], w)) : add2(v[j], mulc2(t, w));
+    }
   }
   if (h) {
 #pragma unroll
-    for (int j = 1; j < 16; ++j) v[j] = mulc2(v[j], c_w32[j]);
+    for (int j = 1; j < E; ++j) v[j] = mulc2(v[j], c_w32[S == 2 ? j : (h * j) & 31]);
   }
-  reg_fft<16, true>(v);
+  reg_fft<E, true>(v);
   __syncwarp();
 #pragma unroll
-  for (int a = 0; a < 16; ++a) sc[k1 * 33 + 2 * a + h] = v[a];
+  for (int a = 0; a < E; ++a) sc[k1 * 33 + S * a + h] = v[a];
   __syncwarp();
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = sc[k * 33 + lane];
+  for (int k = 0; k < E; ++k) v[k] = sc[k * 33 + lane];
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = mulc2(v[k], tw[lane * k * tws]);
-  reg_fft<16, true>(v);
+  for (int k = 1; k < E; ++k) v[k] = mulc2(v[k], tw[lane * k * tws]);
+  reg_fft<E, true>(v);
 }
 
 enum { R_FWD = 0, R_INV = 1, R_MID = 2, R_MIDW = 3, R_MIDG = 4, R_LAST = 5 };
 
-// Lines per warp and complex values per lane.  Lines of L = 512 (1024-point
-// real rows / columns) go one per warp with 16 values per lane (lfft16_*), so
-// a single large vector spreads over twice as many warps; other lengths put
-// 32 / E lines in a warp with 32 values per lane (wfft_*).
-template <int LOGL>
-__host__ __device__ constexpr bool one_line() { return LOGL == 9; }
-template <int LOGL>
-__host__ __device__ constexpr int lpw() { return one_line<LOGL>() ? 1 : 32 / ((1 << LOGL) / 32); }
-template <int LOGL>
-__host__ __device__ constexpr int vpl() { return one_line<LOGL>() ? (1 << LOGL) / 32 : 32; }
+// Lines per warp and complex values per lane.  Lines of L < 1024 complex go
+// one per warp with E = L / 32 values per lane (lfft_*), so that every line of
+// a vector has its own warp; lines of L = 1024 put 32 values in each lane of
+// one warp (wfft_*).
+// COL: the column kernel, which keeps several lines per warp below L = 512
+// (its DCT pair pass has L / 2 + 1 pairs, one lane-iteration too many for a
+// single short line).
+template <int LOGL, bool COL = false>
+__host__ __device__ constexpr bool one_line() { return COL ? LOGL == 9 : (LOGL >= 6 && LOGL <= 9); }
+template <int LOGL, bool COL = false>
+__host__ __device__ constexpr int lpw() { return one_line<LOGL, COL>() ? 1 : 32 / ((1 << LOGL) / 32); }
+template <int LOGL, bool COL = false>
+__host__ __device__ constexpr int vpl() { return one_line<LOGL, COL>() ? (1 << LOGL) / 32 : 32; }
 // per-warp shared scratch (float2): transposes, then one natural-order line per line of the warp
-template <int LOGL>
-__host__ __device__ constexpr int scratch_f2() { return one_line<LOGL>() ? 16 * 33 : 32 * 33; }
+template <int LOGL, bool COL = false>
+__host__ __device__ constexpr int scratch_f2() {
+  return one_line<LOGL, COL>() ? ((1 << LOGL) / 32) * 33 : 32 * 33;
+}
 
 template <int KIND>
 __host__ __device__ constexpr int seg_rows() { return KIND == GMRF_PREC_MIRROR ? 8 : 4; }
@@ -234,7 +260,9 @@ __device__ __forceinline__ void stage_table(float* dst, const float* __restrict_
   for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
-constexpr int kColWarps = 4;
+// warps per column block: with one line per warp, 8 lines share the staged tables
+template <int LOGL>
+__host__ __device__ constexpr int col_warps() { return one_line<LOGL, true>() ? 8 : 4; }
 
 // Dynamic shared memory of the row kernel:
 //   tile[RB][TP] floats | per-warp scratch [WPC][scratch_f2] float2 | twx[NX] | dctx[NX + 1] (MIRROR only)
@@ -245,10 +273,10 @@ __host__ __device__ constexpr size_t row_smem_bytes() {
          (size_t)(2 * (1 << LOGL) + (KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 1 : 0)) * sizeof(float2);
 }
 // Dynamic shared memory of the column kernel:
-//   per-warp scratch [kColWarps][scratch_f2] float2 | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny] floats
+//   per-warp scratch [col_warps][scratch_f2] float2 | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny] floats
 template <int KIND, int LOGL>
 __host__ __device__ constexpr size_t col_smem_bytes() {
-  return (size_t)kColWarps * scratch_f2<LOGL>() * sizeof(float2) +
+  return (size_t)col_warps<LOGL>() * scratch_f2<LOGL, true>() * sizeof(float2) +
          (size_t)((KIND == GMRF_PREC_CIRCULANT ? (1 << LOGL) : 2 * (1 << LOGL)) +
                   (KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 1 : 0)) * sizeof(float2) +
          (size_t)(KIND == GMRF_PREC_CIRCULANT ? (1 << LOGL) : 2 * (1 << LOGL)) * sizeof(float);
@@ -494,10 +522,10 @@ __device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[vpl<LOGL
 #pragma unroll
   for (int g = 0; g < G; ++g) pack_row<KIND, E>(p + g * E, v + g * E);
   if constexpr (one_line<LOGL>()) {
-    lfft16_fwd(v, sm, twx, 2);
+    lfft_fwd<E>(v, sm, twx, 2);
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sm[split_index(lane, j)] = v[j];
+    for (int j = 0; j < E; ++j) sm[split_index<E>(lane, j)] = v[j];
   } else {
     wfft_fwd<LOGL>(v, sm, twx, 2);
     __syncwarp();
@@ -531,8 +559,9 @@ __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[vpl<LOGL
   float2 v[vpl<LOGL>()];
   if constexpr (one_line<LOGL>()) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = sm[split_index(lane, j)];
-    lfft16_inv(v, sm, twx, 2);
+    for (int j = 0; j < E; ++j) v[j] = sm[split_index<E>(lane, j)];
+    __syncwarp();
+    lfft_inv<E>(v, sm, twx, 2);
   } else {
     const int g = lane / E, k1 = lane % E;
 #pragma unroll
@@ -772,16 +801,16 @@ __device__ __forceinline__ float sym(const Args& a, float cx, const float* lamy,
 }
 
 template <int KIND, int LOGL>
-__global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
-  constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), VN = vpl<LOGL>();
+__global__ void __launch_bounds__(32 * col_warps<LOGL>()) k_col(Args a, int step_mode) {
+  constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL, true>(), VN = vpl<LOGL, true>();
   constexpr int NYc = KIND == GMRF_PREC_CIRCULANT ? L : 2 * L;  // ny
   extern __shared__ __align__(16) float smf[];
   const int s = blockIdx.y;
   if (step_mode && a.st[s].status != VS_RUNNING) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* sm = reinterpret_cast<float2*>(smf) + warp * scratch_f2<LOGL>();
+  float2* sm = reinterpret_cast<float2*>(smf) + warp * scratch_f2<LOGL, true>();
   // layout (must match col_smem_bytes): warp scratch | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny]
-  float2* twy = reinterpret_cast<float2*>(smf) + kColWarps * scratch_f2<LOGL>();
+  float2* twy = reinterpret_cast<float2*>(smf) + col_warps<LOGL>() * scratch_f2<LOGL, true>();
   float2* dcty = twy + NYc;
   float* lamy = reinterpret_cast<float*>(dcty + (KIND == GMRF_PREC_MIRROR ? NYc + 1 : 0));
   stage_table(twy, a.twy, NYc);
@@ -789,7 +818,7 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
   stage_table(lamy, a.lamy, NYc);
   __syncthreads();
   float* Tv = a.T + (size_t)s * a.tstride;
-  const int line0 = (blockIdx.x * kColWarps + warp) * G;
+  const int line0 = (blockIdx.x * col_warps<LOGL>() + warp) * G;
   float2 v[VN];
   if (KIND == GMRF_PREC_CIRCULANT) {
     // complex lines kx = 0..nx/2 of length ny = L
@@ -801,14 +830,14 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
 #pragma unroll
       for (int r = 0; r < E; ++r) v[g * E + r] = kx < ncl ? src[lane + 32 * r] : f2(0.f, 0.f);
     }
-    if constexpr (one_line<LOGL>()) {
-      lfft16_fwd(v, sm, twy, 1);
+    if constexpr (one_line<LOGL, true>()) {
+      lfft_fwd<E>(v, sm, twy, 1);
       if (line0 < ncl) {
         const float cx = a.kbar2 + __ldg(a.lamx + line0);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = scl2(v[j], sym(a, cx, lamy, split_index(lane, j)));
+        for (int j = 0; j < E; ++j) v[j] = scl2(v[j], sym(a, cx, lamy, split_index<E>(lane, j)));
       }
-      lfft16_inv(v, sm, twy, 1);
+      lfft_inv<E>(v, sm, twy, 1);
     } else {
       wfft_fwd<LOGL>(v, sm, twy, 1);
       {
@@ -845,11 +874,11 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
   }
 #pragma unroll
   for (int g = 0; g < G; ++g) pack_row<KIND, E>(p + g * E, v + g * E);
-  if constexpr (one_line<LOGL>()) {
-    lfft16_fwd(v, sm, twy, 2);
+  if constexpr (one_line<LOGL, true>()) {
+    lfft_fwd<E>(v, sm, twy, 2);
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sm[split_index(lane, j)] = v[j];
+    for (int j = 0; j < E; ++j) sm[split_index<E>(lane, j)] = v[j];
   } else {
     wfft_fwd<LOGL>(v, sm, twy, 2);
     __syncwarp();
@@ -925,10 +954,11 @@ __global__ void __launch_bounds__(32 * kColWarps) k_col(Args a, int step_mode) {
     }
   }
   __syncwarp();
-  if constexpr (one_line<LOGL>()) {
+  if constexpr (one_line<LOGL, true>()) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = sm[split_index(lane, j)];
-    lfft16_inv(v, sm, twy, 2);
+    for (int j = 0; j < E; ++j) v[j] = sm[split_index<E>(lane, j)];
+    __syncwarp();
+    lfft_inv<E>(v, sm, twy, 2);
   } else {
     const int g = lane / E, k1 = lane % E;
 #pragma unroll
@@ -982,9 +1012,9 @@ cudaError_t row_launch(const Args& a, int nvec, cudaStream_t s, int kc) {
 
 template <int KIND, int LOGL>
 cudaError_t col_launch_t(const Args& a, int nvec, int step_mode, cudaStream_t s, int kc) {
-  constexpr int G = lpw<LOGL>();
+  constexpr int G = lpw<LOGL, true>();
   const int nlines = KIND == GMRF_PREC_CIRCULANT ? a.nx / 2 + 1 : a.nx;
-  const int per = kColWarps * G;
+  const int per = col_warps<LOGL>() * G;
   const size_t sm = col_smem_bytes<KIND, LOGL>();
   static bool attr = false;
   if (!attr) {
@@ -994,7 +1024,7 @@ cudaError_t col_launch_t(const Args& a, int nvec, int step_mode, cudaStream_t s,
   }
   dim3 grd((nlines + per - 1) / per, nvec);
   trace_begin(kc, s);
-  k_col<KIND, LOGL><<<grd, 32 * kColWarps, sm, s>>>(a, step_mode);
+  k_col<KIND, LOGL><<<grd, 32 * col_warps<LOGL>(), sm, s>>>(a, step_mode);
   trace_end(kc, s);
   return cudaGetLastError();
 }
