@@ -61,7 +61,7 @@ extern "C" {
 #define GMRF_ERR_NUMERIC (-5)       /* NaN or Inf during the iteration */
 #define GMRF_ERR_CUDA (-6)          /* a CUDA runtime call failed */
 #define GMRF_ERR_TIMEOUT (-7)       /* a device-side wait ran out of its iteration budget */
-#define GMRF_ERR_UNSUPPORTED (-8)   /* a valid combination this build does not implement */
+#define GMRF_ERR_UNSUPPORTED (-8)   /* a valid combination this library does not implement */
 
 typedef struct gmrf_problem gmrf_problem; /* opaque, library-owned */
 

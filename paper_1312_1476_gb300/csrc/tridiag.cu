@@ -2,7 +2,7 @@
 //
 // Sample (Algorithm 1, last step): y = T_m^{-1/2} e_1.  The algorithm's
 // caption notes that the square root of T_m may be replaced by a rational
-// approximation; this build uses one.  From
+// approximation; this library uses one.  From
 //   t^{-1/2} = (2/pi) int_0^inf ds / (t + s^2) = (2/pi) int_R e^u / (t + e^{2u}) du,
 // whose integrand is sech(u - log(t)/2) / (2 sqrt t), the trapezoid rule with
 // step h on [u_lo, u_hi] gives
