@@ -13,7 +13,7 @@ The oracle is written for a reader checking it against the paper
 from massive Gaussian random vectors"):
 
 * ``stencil``  -- the precision matrices Q (Section 2: matrix-free structured Q;
-  the build's lattice operators), assembled from Kronecker sums of 1-D graph
+  the library's lattice operators), assembled from Kronecker sums of 1-D graph
   Laplacians, plus a per-cell brute-force assembly used to pin them.
 * ``exact``    -- the plain definitions the method converges to: x = Q^{-1/2} z
   (Section 4, principal square root) by dense eigendecomposition or by the

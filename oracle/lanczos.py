@@ -13,7 +13,7 @@ Theorem 1: ||x - x_m|| <= lambda_min^{-1/2} ||r_m|| with r_m the m-th conjugate
 gradient residual for Q y = z (a posteriori), and the a-priori bound
 2 lambda_min^{-1/2} sqrt(kappa) ((sqrt(kappa)-1)/(sqrt(kappa)+1))^m ||z||.
 
-Stopping rule (the build's reading; the paper gives only the bound, and says it
+Stopping rule (the reading used here; the paper gives only the bound, and says it
 is the practical convergence check): after step m compute
 est_m = theta_min(T_m)^{-1/2} ||r_m|| / ||x_m||, with theta_min the smallest
 Ritz value standing in for the unknown lambda_min, ||r_m|| = ||z|| beta_m

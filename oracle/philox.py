@@ -9,7 +9,7 @@ Definition (per round, with key (k0, k1)):
 and between rounds the key advances by the Weyl constants
     (k0, k1) <- (k0 + 0x9E3779B9, k1 + 0xBB67AE85)   (mod 2^32); 10 rounds.
 
-Counter layout of the build (both sides):
+Counter layout used on both sides:
 * Gaussian element e of vector s: one Philox call per group g = e // 4 with
   counter (g, s, 0, 0), key (seed mod 2^32, seed >> 32); words (w0, w1) give
   elements 4g, 4g+1 and (w2, w3) give 4g+2, 4g+3 by Box-Muller:

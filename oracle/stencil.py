@@ -1,7 +1,7 @@
 """Lattice precision matrices Q, assembled explicitly (oracle side).
 
 Section 2 of the paper: the methods only need a cheap product Q v; for a GMRF
-on a lattice Q is sparse and the product costs O(n).  The build's operator
+on a lattice Q is sparse and the product costs O(n).  The library's operator
 family (its reading of the paper's lattice models, Sections 3 and 5):
 
 * graph Laplacian L with unit spacing: (L v)_i = sum over lattice neighbours j
