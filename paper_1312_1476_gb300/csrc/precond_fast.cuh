@@ -534,11 +534,14 @@ __device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[vpl<LOGL
     for (int k2 = 0; k2 < 32; ++k2) sm[g * L + k1 + E * k2] = v[k2];
   }
   __syncwarp();
-  constexpr int NP = L / 2 + 1;
-  for (int idx = lane; idx < G * NP; idx += 32) {
-    const int g = idx / NP, k = idx - g * NP;
+  // pairs (k, L - k), k = 0 .. L/2; the lane with k = 0 also takes the cheap
+  // k = L/2 item, so the L/2 + 1 items fill whole lane-iterations
+  constexpr int HP = L / 2;
+  for (int idx = lane; idx < G * HP; idx += 32) {
+    const int g = idx / HP, k = idx - g * HP;
     float* trow = tile + (tr0 + g) * TP;
     post_pair<KIND, L>(sm + g * L, k, twx, dctx, reinterpret_cast<float2*>(trow), trow);
+    if (k == 0) post_pair<KIND, L>(sm + g * L, HP, twx, dctx, reinterpret_cast<float2*>(trow), trow);
   }
 }
 
@@ -548,12 +551,13 @@ __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[vpl<LOGL
                                              int tr0, const float2* twx, const float2* dctx) {
   constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), TP = tile_pitch<KIND, LOGL>();
   const int lane = threadIdx.x & 31;
-  constexpr int NP = L / 2 + 1;
+  constexpr int HP = L / 2;  // k = 0 and k = L/2 go to one lane (see rows_forward)
   __syncwarp();
-  for (int idx = lane; idx < G * NP; idx += 32) {
-    const int g = idx / NP, k = idx - g * NP;
+  for (int idx = lane; idx < G * HP; idx += 32) {
+    const int g = idx / HP, k = idx - g * HP;
     const float* trow = tile + (tr0 + g) * TP;
     pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, k, twx, dctx, sm + g * L);
+    if (k == 0) pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, HP, twx, dctx, sm + g * L);
   }
   __syncwarp();
   float2 v[vpl<LOGL>()];
@@ -890,9 +894,9 @@ __global__ void __launch_bounds__(32 * col_warps<LOGL>()) k_col(Args a, int step
 #pragma unroll
   for (int g = 0; g < G; ++g) cxl[g] = line0 + g < a.nx ? a.kbar2 + __ldg(a.lamx + line0 + g) : 1.f;
   __syncwarp();
-  constexpr int NP = L / 2 + 1;
-  for (int idx = lane; idx < G * NP; idx += 32) {
-    const int g = idx / NP, k = idx - g * NP;
+  // pairs (k, L - k), k = 0 .. L/2; the lane with k = 0 also takes k = L/2
+  constexpr int HP = L / 2;
+  auto pair = [&](int g, int k) {
     const int kx = line0 + g;
     float cx = cxl[0];
 #pragma unroll
@@ -952,6 +956,11 @@ __global__ void __launch_bounds__(32 * col_warps<LOGL>()) k_col(Args a, int step
       const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), twy[kp]);
       zl[kp] = f2(Ev.x - O.y, Ev.y + O.x);
     }
+  };
+  for (int idx = lane; idx < G * HP; idx += 32) {
+    const int g = idx / HP, k = idx - g * HP;
+    pair(g, k);
+    if (k == 0) pair(g, HP);
   }
   __syncwarp();
   if constexpr (one_line<LOGL, true>()) {
