@@ -68,6 +68,21 @@ struct Dots<float> {
     s2 = df_add(s2, two_prod(q, q));
     s3 = df_add(s3, two_prod(v, v));
   }
+  // Dot2 of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 2005): exact product
+  // (TwoProd), TwoSum into hi, the rounding errors summed into lo without
+  // renormalising; as accurate as summing in twice the working precision.
+  __device__ __forceinline__ static void dot2(df& a, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);
+    const df t = two_sum(a.hi, p);
+    a.hi = t.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(t.lo, pe));
+  }
+  __device__ __forceinline__ void add_dot2(float v, float q) {
+    dot2(s1, v, q);
+    dot2(s2, q, q);
+    dot2(s3, v, v);
+  }
   __device__ __forceinline__ void merge(const Dots& o) {
     s1 = df_add(s1, o.s1);
     s2 = df_add(s2, o.s2);

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks)
             if (BC != GMRF_BC_NEUMANN || z < nz - 1) r += c - vup[e];
             if (STEP && j > 0) r -= bprev * vpc[e];
             qo[e] = r;
-            if (STEP) d.add(c, r);
+            if (STEP) d.add_dot2(c, r);
           }
           const size_t i = (size_t)gx + (size_t)nx * gy + plane * z;
           *reinterpret_cast<float4*>(Wout + i) = make_float4(qo[0], qo[1], qo[2], qo[3]);
