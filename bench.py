@@ -437,9 +437,77 @@ def measure_variants(args, gmrf, torch, flush, peak):
             "samples_per_s": ns * 1e3 / mst, "ms_per_call": mst, "status": rct,
             "basis_bytes_per_vector": {"stored_fp32": 4 * n * (m3 + 1), "two_pass": 4 * n * 2 + 8 * n},
             "bitwise_equal_to_stored_basis": bool(torch.equal(xb, x))}
+    out["cfg1_64x64_periodic_fp64"] = measure_cfg1(gmrf, torch, timed)
+    if not getattr(args, "no_cpu_baseline", False):
+        # the oracle beside the batched and 3-D workloads (bounded samples on the host cores)
+        out["batched_512"]["cpu_oracle"] = cpu_oracle_rate("batched_512", out["batched_512"]["m_mean"])
+        out["3d_256"]["cpu_oracle"] = cpu_oracle_rate("3d_128", out["3d_256"]["m_mean"])
     out["table1"] = measure_table1(gmrf, torch)
     out["serving"] = measure_serving()
     return out
+
+
+def measure_cfg1(gmrf, torch, timed):
+    """64 x 64 periodic, Q = 0.1 I + 5-point Laplacian, FP64, tol 1e-10, m <= 300
+    (the smallest configuration): one sample per call and 256 per call, with
+    the oracle's Algorithm 1 on the host beside it."""
+    from oracle import lanczos as olz, stencil
+    from paper_1312_1476_gb300 import inputs
+    shape, n = (64, 64), 4096
+    res = {"workload": "64x64 periodic, Q = 0.1 I + 5-point Laplacian, FP64, tol 1e-10, m_max 300"}
+    with gmrf.Problem(shape, "periodic", "shifted_laplacian", kappa2_const=0.1, precision="fp64") as p:
+        x1 = torch.empty(n, dtype=torch.float64, device="cuda")
+        xb = torch.empty(256 * n, dtype=torch.float64, device="cuda")
+        p.sample(x1, nsamples=1, tol=1e-10, m_max=300, seed=1)
+        p.sample(xb, nsamples=256, tol=1e-10, m_max=300, seed=1)
+        ms1, (rc1, info1) = timed(lambda i: p.sample(x1, nsamples=1, tol=1e-10, m_max=300, seed=5 + i), 5)
+        msb, (rcb, infob) = timed(lambda i: p.sample(xb, nsamples=256, tol=1e-10, m_max=300, seed=5 + i), 3)
+    res.update({"samples_per_s_one_per_call": 1e3 / ms1, "ms_per_sample": ms1, "m_used": info1[0].m_used,
+                "samples_per_s_256_per_call": 256e3 / msb, "status": max(rc1, rcb)})
+    Q = stencil.precision_matrix(shape, "periodic", "shifted_laplacian", 0.1)
+    z = inputs.gaussian_vectors(1, n, seed=2, dtype=np.float64)[0]
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 2.0:
+        olz.adaptive_sample(lambda v: Q @ v, z, 1e-10, 300)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    res["cpu_oracle"] = {"value": 1.0 / dt, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                         "sample": "%d full samples (oracle Algorithm 1, sparse matvec, FP64)" % reps}
+    return res
+
+
+def cpu_oracle_rate(which, m_mean):
+    """The oracle on the host cores: a few Lanczos steps of one vector of the
+    workload, scaled to its mean m (a bounded sample, labelled)."""
+    import scipy.fft
+    from oracle import lanczos as olz, precond as opre, stencil
+    from paper_1312_1476_gb300 import inputs
+    cores = os.cpu_count() or 1
+    k_steps = 6
+    with scipy.fft.set_workers(cores):
+        if which == "batched_512":
+            shape = (512, 512)
+            k2 = inputs.kappa2_gp_field(shape, seed=KAPPA_SEED, ell=64.0).astype(np.float64)
+            Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2, 1.0)
+            A = olz.preconditioned_operator(Q, shape, "neumann", "spde_squared", opre.kappa2_bar(k2), 1.0)
+            label = "512x512 SPDE, mirror M"
+        else:
+            shape = (128, 128, 128)
+            k3 = inputs.kappa2_uniform_field(shape, seed=KAPPA_SEED).astype(np.float64)
+            Q = stencil.precision_matrix(shape, "dirichlet", "shifted_laplacian", k3, 1.0)
+            A = lambda v: Q @ v  # noqa: E731
+            label = "128^3 Dirichlet 7-point (the 256^3 recipe one size down; 256^3 does not fit a bounded sample)"
+        z = inputs.gaussian_vectors(1, int(np.prod(shape)), seed=2, dtype=np.float64)[0]
+        t0 = time.perf_counter()
+        done = 0
+        for st in olz.lanczos_steps(A, z):
+            done += 1
+            if done >= k_steps or st["breakdown"]:
+                break
+        per_step = (time.perf_counter() - t0) / done
+    return {"value": 1.0 / (per_step * m_mean), "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": "%d Lanczos steps of one vector of %s (FP64), scaled to m = %.1f" % (done, label, m_mean)}
 
 
 def measure_table1(gmrf, torch):
