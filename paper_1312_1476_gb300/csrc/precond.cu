@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <atomic>
 #include <vector>
 
 #include "fft.cuh"
@@ -657,38 +658,38 @@ fast::Args fast_args(const PrecondTables& t, const Grid& g, const void* kappa2, 
 }
 
 int smem_optin() {
-  static int v = 0;
-  if (!v) {
-    int dev = 0;
+  static const int v = [] {  // thread-safe one-time initialisation
+    int dev = 0, r = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    if (cudaDeviceGetAttribute(&r, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
       cudaGetLastError();
-      v = 48 * 1024;
+      r = 48 * 1024;
     }
-  }
+    return r;
+  }();
   return v;
 }
 
 // Raise the dynamic shared memory limit of a kernel once per process.
 template <typename K>
-cudaError_t allow_smem(K* k, bool& done) {
-  if (done) return cudaSuccess;
+cudaError_t allow_smem(K* k, std::atomic<bool>& done) {
+  if (done.load(std::memory_order_acquire)) return cudaSuccess;
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, k);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin() - (int)fa.sharedSizeBytes);
-  if (e == cudaSuccess) done = true;
+  if (e == cudaSuccess) done.store(true, std::memory_order_release);
   return e;
 }
 
 template <typename R, int KIND, int MODE>
 cudaError_t row_attr() {
-  static bool done = false;
+  static std::atomic<bool> done{false};
   return allow_smem(k_prow<R, KIND, MODE>, done);
 }
 template <typename R, int KIND>
 cudaError_t col_attr() {
-  static bool done = false;
+  static std::atomic<bool> done{false};
   return allow_smem(k_pcol<R, KIND>, done);
 }
 

@@ -22,6 +22,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "fft.cuh"
 #include "precond.h"
 #include "precond_fast.h"
@@ -994,11 +996,11 @@ cudaError_t row_launch_t(const Args& a, int nvec, cudaStream_t s, int kc) {
   constexpr int RB = rows_per_block<KIND, LOGL>(), TP = tile_pitch<KIND, LOGL>();
   constexpr int WPC = RB / G;
   const size_t sm = row_smem_bytes<KIND, LOGL>();
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // several host threads may launch at once
+  if (!attr.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(k_row<KIND, LOGL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   dim3 grd(a.ny / RB, nvec);
   trace_begin(kc, s);
@@ -1025,11 +1027,11 @@ cudaError_t col_launch_t(const Args& a, int nvec, int step_mode, cudaStream_t s,
   const int nlines = KIND == GMRF_PREC_CIRCULANT ? a.nx / 2 + 1 : a.nx;
   const int per = col_warps<LOGL>() * G;
   const size_t sm = col_smem_bytes<KIND, LOGL>();
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // several host threads may launch at once
+  if (!attr.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(k_col<KIND, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   dim3 grd((nlines + per - 1) / per, nvec);
   trace_begin(kc, s);
