@@ -601,15 +601,18 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
     if (a.st[s].status != VS_RUNNING) return;
     j = a.st[s].m;
   }
-  stage_table(twx, a.twx, NX);
-  if (KIND == GMRF_PREC_MIRROR) stage_table(dctx, a.dctx, NX + 1);
-  __syncthreads();
   const int y0 = blockIdx.x * RB;
   const int tr0 = warp * G;       // first tile row of this warp
   const size_t n = a.n;
   float* Tv = a.T + (size_t)s * a.tstride;
   float2 p[vpl<LOGL>()];
   const size_t slot = (size_t)s * a.P.nslots;
+  // the transform tables are staged behind the block's first global loads,
+  // so that both latencies overlap (one barrier)
+  auto stage_tables = [&]() {
+    stage_table(twx, a.twx, NX);
+    if (KIND == GMRF_PREC_MIRROR) stage_table(dctx, a.dctx, NX + 1);
+  };
 
   if (MODE == R_FWD) {
     const float* Win = a.in ? a.in + (size_t)s * n : (((j & 1) ? a.W1 : a.W0) + (size_t)s * n);
@@ -624,14 +627,21 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
         inv_b = (float)(1.0 / a.beta[mo]);
       }
     }
+    float2 qv[vpl<LOGL>()];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const size_t ro = (size_t)(y0 + tr0 + g) * NX;
       load_row<KIND, E>(p + g * E, Win + ro);
+      if (Vp) load_row<KIND, E>(qv + g * E, Vp + ro);
+    }
+    stage_tables();
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const size_t ro = (size_t)(y0 + tr0 + g) * NX;
       if (!a.in) {
         if (j > 0) {
-          float2 q[E];
-          load_row<KIND, E>(q, Vp + ro);
+          const float2* q = qv + g * E;
 #pragma unroll
           for (int r = 0; r < E; ++r)
             p[g * E + r] = f2((p[g * E + r].x - coef * q[r].x) * inv_b, (p[g * E + r].y - coef * q[r].y) * inv_b);
@@ -650,11 +660,10 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
   }
 
   // inverse transform of the block's rows
-  if (MODE != R_MIDG) {
-    tile_load_T<KIND, LOGL>(a, tile, Tv, y0);
-    __syncthreads();
-    rows_inverse<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);
-  }
+  stage_tables();
+  if (MODE != R_MIDG) tile_load_T<KIND, LOGL>(a, tile, Tv, y0);
+  __syncthreads();
+  if (MODE != R_MIDG) rows_inverse<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);
   if (MODE == R_INV) {
 #pragma unroll
     for (int g = 0; g < G; ++g) store_row<KIND, E>(p + g * E, a.out + (size_t)s * n + (size_t)(y0 + tr0 + g) * NX);
@@ -819,10 +828,13 @@ __global__ void __launch_bounds__(32 * col_warps<LOGL>()) k_col(Args a, int step
   float2* twy = reinterpret_cast<float2*>(smf) + col_warps<LOGL>() * scratch_f2<LOGL, true>();
   float2* dcty = twy + NYc;
   float* lamy = reinterpret_cast<float*>(dcty + (KIND == GMRF_PREC_MIRROR ? NYc + 1 : 0));
-  stage_table(twy, a.twy, NYc);
-  if (KIND == GMRF_PREC_MIRROR) stage_table(dcty, a.dcty, NYc + 1);
-  stage_table(lamy, a.lamy, NYc);
-  __syncthreads();
+  // the tables are staged after the warp's line loads are issued (one barrier)
+  auto stage_tables = [&]() {
+    stage_table(twy, a.twy, NYc);
+    if (KIND == GMRF_PREC_MIRROR) stage_table(dcty, a.dcty, NYc + 1);
+    stage_table(lamy, a.lamy, NYc);
+    __syncthreads();
+  };
   float* Tv = a.T + (size_t)s * a.tstride;
   const int line0 = (blockIdx.x * col_warps<LOGL>() + warp) * G;
   float2 v[VN];
@@ -836,6 +848,7 @@ __global__ void __launch_bounds__(32 * col_warps<LOGL>()) k_col(Args a, int step
 #pragma unroll
       for (int r = 0; r < E; ++r) v[g * E + r] = kx < ncl ? src[lane + 32 * r] : f2(0.f, 0.f);
     }
+    stage_tables();
     if constexpr (one_line<LOGL, true>()) {
       lfft_fwd<E>(v, sm, twy, 1);
       if (line0 < ncl) {
@@ -878,6 +891,7 @@ __global__ void __launch_bounds__(32 * col_warps<LOGL>()) k_col(Args a, int step
       for (int r = 0; r < E; ++r) p[g * E + r] = f2(0.f, 0.f);
     }
   }
+  stage_tables();
 #pragma unroll
   for (int g = 0; g < G; ++g) pack_row<KIND, E>(p + g * E, v + g * E);
   if constexpr (one_line<LOGL, true>()) {
