@@ -168,7 +168,7 @@ struct VecState {
   double amax;    // max |alpha_i|
   double bmax;    // max beta_i
   double beta_last;  // beta_{m-1}
-  double pad;
+  double vscale;     // 1 / ||z|| at m = 0, then 1 / beta_{m-1}: the scale of v_m (one division per step)
 };
 
 // Loop-invariant parameters of the Lanczos steps.  The step index j (the
@@ -318,6 +318,7 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
     }
     v.m = j + 1;
     v.beta_last = b;
+    v.vscale = b > 0.0 ? 1.0 / b : 0.0;
     v.amax = fmax(v.amax, fabs(a));
     v.bmax = fmax(v.bmax, b);
     int need = 0;

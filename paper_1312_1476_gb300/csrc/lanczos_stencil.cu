@@ -90,13 +90,13 @@ __global__ void __launch_bounds__(NT) k_stencil2d(StencilArgs<T> a) {
     const size_t base = (size_t)s * a.P.nslots;
     Vc = a.V + (base + (size_t)(j % a.P.nslots)) * n;
     if (j == 0) {
-      inv_b = (T)(1.0 / a.st[s].znorm);
+      inv_b = (T)a.st[s].vscale;
     } else {
       Vp = a.V + (base + (size_t)((j - 1) % a.P.nslots)) * n;
       const size_t mo = (size_t)s * a.P.m_max + (j - 1);
       coef = (T)a.alpha[mo];
       bprev = (T)a.beta[mo];
-      inv_b = (T)(1.0 / a.beta[mo]);
+      inv_b = (T)a.st[s].vscale;
     }
   }
   // ---- load v_j on tile + halo
@@ -248,13 +248,13 @@ __global__ void __launch_bounds__(NT3) k_stencil3d(StencilArgs<T> a) {
     const size_t base = (size_t)s * a.P.nslots;
     Vc = a.V + (base + (size_t)(j % a.P.nslots)) * n;
     if (j == 0) {
-      inv_b = (T)(1.0 / a.st[s].znorm);
+      inv_b = (T)a.st[s].vscale;
     } else {
       Vp = a.V + (base + (size_t)((j - 1) % a.P.nslots)) * n;
       const size_t mo = (size_t)s * a.P.m_max + (j - 1);
       coef = (T)a.alpha[mo];
       bprev = (T)a.beta[mo];
-      inv_b = (T)(1.0 / a.beta[mo]);
+      inv_b = (T)a.st[s].vscale;
     }
   }
   auto fv = [&](T w, T vp) -> T {

@@ -132,6 +132,7 @@ __global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>*
     acc.get(s1, s2, s3);
     VecState v = {};
     v.znorm = sqrt(s3);
+    v.vscale = v.znorm > 0.0 ? 1.0 / v.znorm : 0.0;
     v.m = 0;
     if (!isfinite(v.znorm)) v.status = GMRF_ERR_NUMERIC;
     else if (v.znorm == 0.0) v.status = VS_DONE;

@@ -280,12 +280,12 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
       Win = ((j & 1) ? a.W1 : a.W0) + (size_t)s * n;
       Vc = a.V + (base + (size_t)(j % a.P.nslots)) * n;
       if (j == 0) {
-        inv_b = (R)(1.0 / a.st[s].znorm);
+        inv_b = (R)a.st[s].vscale;
       } else {
         Vp = a.V + (base + (size_t)((j - 1) % a.P.nslots)) * n;
         const size_t mo = (size_t)s * a.P.m_max + (j - 1);
         coef = (R)a.alpha[mo];
-        inv_b = (R)(1.0 / a.beta[mo]);
+        inv_b = (R)a.st[s].vscale;
       }
     } else {
       Win = a.in + (size_t)s * n;

@@ -579,7 +579,7 @@ __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[vpl<LOGL
 }
 
 template <int KIND, int LOGL, int MODE>
-__global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>()))
+__global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>()), LOGL == 9 ? 1 : 0)
     k_row(Args a) {
   constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), NX = 2 * L;
   constexpr int RB = rows_per_block<KIND, LOGL>(), TP = tile_pitch<KIND, LOGL>();
@@ -620,11 +620,11 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
     const float* Vp = (!a.in && j > 0) ? a.V + (slot + (size_t)((j - 1) % a.P.nslots)) * n : nullptr;
     float coef = 0.f, inv_b = 1.f;
     if (!a.in) {
-      if (j == 0) inv_b = (float)(1.0 / a.st[s].znorm);
+      if (j == 0) inv_b = (float)a.st[s].vscale;
       else {
         const size_t mo = (size_t)s * a.P.m_max + (j - 1);
         coef = (float)a.alpha[mo];
-        inv_b = (float)(1.0 / a.beta[mo]);
+        inv_b = (float)a.st[s].vscale;
       }
     }
     float2 qv[vpl<LOGL>()];
@@ -660,6 +660,27 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
   }
 
   // inverse transform of the block's rows
+  const float* vsrc = a.in ? a.in + (size_t)s * n : a.V + (slot + (size_t)(j % a.P.nslots)) * n;
+  const float* gsrc = a.form == FORM_CTC ? a.G + (size_t)s * n : vsrc;
+  // Rows of 1024 (one per warp, one block per SM at one vector): the arrays
+  // the elementwise part reads after the inverse transform are loaded before
+  // it, so that their latency overlaps the table staging and the transform
+  // (pa, pb, pc: kappa^2 and v for R_MID; g, v and v_{j-1} for R_LAST).
+  constexpr bool PF = LOGL == 9 && G == 1 && (MODE == R_MID || MODE == R_LAST);
+  float2 pa[PF ? E : 1], pb[PF ? E : 1], pc[PF ? E : 1];
+  if constexpr (PF) {
+    const size_t ro = (size_t)(y0 + tr0) * NX;
+    if (MODE == R_MID) {
+      load_kap<KIND, E>(a, ro, pa);
+      if (a.form == FORM_CTC) load_row<KIND, E>(pb, vsrc + ro);
+    } else {
+      load_row<KIND, E>(pa, gsrc + ro);
+      if (!a.in) {
+        load_row<KIND, E>(pb, vsrc + ro);
+        if (j > 0) load_row<KIND, E>(pc, a.V + (slot + (size_t)((j - 1) % a.P.nslots)) * n + ro);
+      }
+    }
+  }
   stage_tables();
   if (MODE != R_MIDG) tile_load_T<KIND, LOGL>(a, tile, Tv, y0);
   __syncthreads();
@@ -669,7 +690,6 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
     for (int g = 0; g < G; ++g) store_row<KIND, E>(p + g * E, a.out + (size_t)s * n + (size_t)(y0 + tr0 + g) * NX);
     return;
   }
-  const float* vsrc = a.in ? a.in + (size_t)s * n : a.V + (slot + (size_t)(j % a.P.nslots)) * n;
   if (MODE == R_MIDW) {
     float* wg = a.Wg + (size_t)s * n;
 #pragma unroll
@@ -720,7 +740,9 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const size_t o = ro + pair_off<KIND, E>(lane, i);
-        const float2 kk = a.kappa2 ? *reinterpret_cast<const float2*>(a.kappa2 + o) : f2(a.kappa2_const, a.kappa2_const);
+        float2 kk;
+        if constexpr (PF) kk = pa[i];
+        else kk = a.kappa2 ? *reinterpret_cast<const float2*>(a.kappa2 + o) : f2(a.kappa2_const, a.kappa2_const);
         float2 t = f2((kk.x - a.roff) * w[i].x, (kk.y - a.roff) * w[i].y);
         if (ex && lane == 0 && i == 0) t.x += edge_val<KIND>(a.bc, w[0].x, wl);
         if (ex && lane == 31 && i == E - 1) t.y += edge_val<KIND>(a.bc, w[E - 1].y, wf);
@@ -731,7 +753,9 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
           t.y += edge_val<KIND>(a.bc, w[i].y, wq.y);
         }
         if (a.form == FORM_CTC) {
-          const float2 vv = *reinterpret_cast<const float2*>(vsrc + o);
+          float2 vv;
+          if constexpr (PF) vv = pb[i];
+          else vv = *reinterpret_cast<const float2*>(vsrc + o);
           t = add2(vv, t);
         }
         w[i] = t;
@@ -747,7 +771,9 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           const size_t o = ro + pair_off<KIND, E>(lane, i);
-          const float2 kk = a.kappa2 ? *reinterpret_cast<const float2*>(a.kappa2 + o) : f2(a.kappa2_const, a.kappa2_const);
+          float2 kk;
+          if constexpr (PF) kk = pa[i];
+          else kk = a.kappa2 ? *reinterpret_cast<const float2*>(a.kappa2 + o) : f2(a.kappa2_const, a.kappa2_const);
           float2 t = f2((kk.x - a.roff) * w[i].x, (kk.y - a.roff) * w[i].y);
           if (ex && lane == 0 && i == 0) t.x += edge_val<KIND>(a.bc, w[0].x, gl);
           if (ex && lane == 31 && i == E - 1) t.y += edge_val<KIND>(a.bc, w[E - 1].y, gf);
@@ -766,13 +792,17 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
     return;
   }
   // R_LAST: A v = g + h
-  const float* gsrc = a.form == FORM_CTC ? a.G + (size_t)s * n : vsrc;
   if (a.in) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const size_t ro = (size_t)(y0 + tr0 + g) * NX;
       float2 gg[E];
-      load_row<KIND, E>(gg, gsrc + ro);
+      if constexpr (PF) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) gg[i] = pa[i];
+      } else {
+        load_row<KIND, E>(gg, gsrc + ro);
+      }
 #pragma unroll
       for (int i = 0; i < E; ++i) gg[i] = add2(gg[i], p[g * E + i]);
       store_row<KIND, E>(gg, a.out + (size_t)s * n + ro);
@@ -788,9 +818,18 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
   for (int g = 0; g < G; ++g) {
     const size_t ro = (size_t)(y0 + tr0 + g) * NX;
     float2 gg[E], vv[E], q[E];
-    load_row<KIND, E>(gg, gsrc + ro);
-    load_row<KIND, E>(vv, vsrc + ro);
-    if (j > 0) load_row<KIND, E>(q, Vp + ro);
+    if constexpr (PF) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        gg[i] = pa[i];
+        vv[i] = pb[i];
+        q[i] = pc[i];
+      }
+    } else {
+      load_row<KIND, E>(gg, gsrc + ro);
+      load_row<KIND, E>(vv, vsrc + ro);
+      if (j > 0) load_row<KIND, E>(q, Vp + ro);
+    }
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       float2 t = add2(gg[i], p[g * E + i]);

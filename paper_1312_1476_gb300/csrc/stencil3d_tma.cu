@@ -149,13 +149,13 @@ __global__ void __launch_bounds__(NT, kMinBlocks)
       const size_t base = (size_t)s * a.P.nslots;
       Vc = a.V + (base + (size_t)(j % a.P.nslots)) * n;
       if (j == 0) {
-        inv_b = (float)(1.0 / a.st[s].znorm);
+        inv_b = (float)a.st[s].vscale;
       } else {
         vrow = (int)(base + (size_t)((j - 1) % a.P.nslots));
         const size_t mo = (size_t)s * a.P.m_max + (j - 1);
         coef = (float)a.alpha[mo];
         bprev = (float)a.beta[mo];
-        inv_b = (float)(1.0 / a.beta[mo]);
+        inv_b = (float)a.st[s].vscale;
       }
     }
     // v_j from the staged q_{j-1} and v_{j-1}
