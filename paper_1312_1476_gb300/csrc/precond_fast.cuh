@@ -850,8 +850,8 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
 // ----------------------------------------------------------------- columns
 // symbol of B_bar^{-p/2} (times the transform normalisation); cx = kappa_bar^2 + lambda_x
 __device__ __forceinline__ float sym(const Args& a, float cx, const float* lamy, int ky) {
-  const float lam = cx + lamy[ky];
-  return (a.power == 2 ? 1.f / lam : rsqrtf(lam)) * a.dscale;
+  const float r = rsqrtf(cx + lamy[ky]);  // lam^{-1/2}; lam^{-1} = r^2 (a few ulp, no division)
+  return (a.power == 2 ? r * r : r) * a.dscale;
 }
 
 template <int KIND, int LOGL>
