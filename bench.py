@@ -354,6 +354,38 @@ def measure_variants(args, gmrf, torch, flush, peak):
         out["circulant"] = {"workload": "same input, plain-torus circulant M", "samples_per_s": 1e3 / ms,
                             "ms_per_sample": ms, "m_used": info[0].m_used, "status": rc}
 
+    # Section 5.1: the linear solve x = Q^{-1} b on the headline problem (the
+    # sampler's iteration and preconditioner, T_m^{-1} in place of T_m^{-1/2})
+    with gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond="mirror",
+                      stream=stream.cuda_stream) as p:
+        b = torch.from_numpy(inputs.gaussian_vectors(1, n, seed=7, dtype=np.float32)).cuda()
+        x = torch.empty(n, dtype=torch.float32, device="cuda")
+        p.solve(b, x, nrhs=1, tol=TOL, m_max=M_MAX)
+        ms, (rc, info) = timed(lambda i: p.solve(b, x, nrhs=1, tol=TOL, m_max=M_MAX), 3)
+        out["solve_1024"] = {"workload": "headline problem, x = Q^{-1} b (Section 5.1 solve), mirror M, FP32, "
+                                         "relative residual of the preconditioned system 1e-6, one right-hand side",
+                             "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "m_used": info[0].m_used,
+                             "status": rc}
+    # the sMMALA proposal of Section 3 at 1024^2 (LGCP recipe of Table 1, FP32,
+    # tol 1e-6): one mean solve (Q + H)^{-1} grad and one sample, both with the
+    # prior as the preconditioner
+    mdl = inputs.lgcp_smmala_model(GRID)
+    with gmrf.Problem(shape, "periodic", "spde_plus_diag", kappa2=torch.from_numpy(mdl["d"]).cuda(),
+                      kappa2_const=mdl["kappa2_prior"], tau=mdl["tau"], precond="circulant",
+                      stream=stream.cuda_stream) as p:
+        gb = torch.from_numpy(inputs.lgcp_gradient(GRID).astype(np.float32)).cuda()
+        xm = torch.empty(n, dtype=torch.float32, device="cuda")
+        xs = torch.empty(n, dtype=torch.float32, device="cuda")
+        p.solve(gb, xm, nrhs=1, tol=TOL, m_max=200)
+        p.sample(xs, nsamples=1, tol=TOL, m_max=200, seed=1)
+        mss, (rcs, infs) = timed(lambda i: p.solve(gb, xm, nrhs=1, tol=TOL, m_max=200), 3)
+        msp, (rcp, infp) = timed(lambda i: p.sample(xs, nsamples=1, tol=TOL, m_max=200, seed=50 + i), 3)
+        out["smmala_proposal_1024"] = {
+            "workload": "LGCP sMMALA proposal on a 1024^2 torus (Table 1 recipe), FP32, tol 1e-6: mean solve "
+                        "(Q + H)^{-1} grad log pi(y|x) plus one sample, prior (circulant) preconditioner",
+            "proposals_per_s": 1e3 / (mss + msp), "ms_solve": mss, "ms_sample": msp,
+            "m_solve": infs[0].m_used, "m_sample": infp[0].m_used, "status": [rcs, rcp]}
+
     # batched 512^2: 256 samples + log det with 64 Rademacher probes in one call each
     shape = (512, 512)
     n = 512 * 512
@@ -516,7 +548,7 @@ def measure_table1(gmrf, torch):
     the unit torus, Q = prior + diag(Fisher information), preconditioned by the
     prior (circulant, applied by FFT) and without preconditioning."""
     from paper_1312_1476_gb300 import inputs
-    pre, un, ms_sample = {}, {}, {}
+    pre, un, ms_sample, pre_solve = {}, {}, {}, {}
     for N in (16, 32, 64, 128, 256, 512, 1024, 2048):
         mdl = inputs.lgcp_smmala_model(N)
         kw = dict(kappa2=torch.from_numpy(mdl["d"]).cuda(), kappa2_const=mdl["kappa2_prior"], tau=mdl["tau"],
@@ -530,6 +562,10 @@ def measure_table1(gmrf, torch):
             torch.cuda.synchronize()
             ms_sample[N] = round((time.perf_counter() - t0) * 1e3, 3)
             pre[N] = info[0].m_used if rc == gmrf.OK else None
+            # the proposal mean's solve with the same preconditioner (Section 5.1)
+            gb = torch.from_numpy(inputs.lgcp_gradient(N)).cuda()
+            rcs, infs = p.solve(gb, x, nrhs=1, tol=1e-8, m_max=200, check_every=1)
+            pre_solve[N] = infs[0].m_used if rcs == gmrf.OK else None
         if N <= 128:
             with gmrf.Problem((N, N), "periodic", "spde_plus_diag", **kw) as p:
                 rc, info = p.sample(x, nsamples=1, tol=1e-8, m_max=8192, seed=2, check_every=16,
@@ -538,6 +574,7 @@ def measure_table1(gmrf, torch):
     return {"workload": "LGCP sMMALA proposal on the unit torus (prior h^2 (kappa^2 + L/h^2)^2, kappa 10; "
                         "Fisher information diag(h^2 exp(x)), mean intensity 2000), FP64, tol 1e-8, one sample",
             "m_preconditioned": pre, "m_unpreconditioned": un, "ms_per_preconditioned_sample": ms_sample,
+            "m_mean_solve_preconditioned": pre_solve,
             "paper_table1_context": {"preconditioned": 6, "unpreconditioned": {"16": 102, "32": 286, "64": 790,
                                                                               "128": 2166},
                                      "note": "the paper's prior is unspecified; counts are context"}}

@@ -188,6 +188,40 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* opts, void* x_out, gmrf
 int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* opts, double* logdet, double* std_err,
                 double* q_out, gmrf_result_info* info);
 
+typedef struct {
+  double tol;          /* relative residual at which an iteration stops, > 0 (see gmrf_solve) */
+  int32_t m_max;       /* largest subspace size (CG steps), 1 .. 8192 */
+  int32_t nrhs;        /* number of right-hand sides (>= 1) */
+  int32_t check_every; /* steps between host polls of the convergence flags (<= 0: 16) */
+  int32_t reserved;    /* must be 0 */
+} gmrf_solve_opts;
+
+/* Section 5.1: x = Q^{-1} b, the linear solve of the sMMALA proposal mean
+ * (Q + H)^{-1} grad log pi(y | x), run by the same Lanczos iteration and
+ * the same preconditioner as the sampler ("one preconditioner ... both
+ * problems").  The iteration is the Lanczos form of conjugate gradients:
+ * from v_1 = b / ||b|| it builds V_m and T_m exactly as Algorithm 1 and
+ * returns x_m = ||b|| V_m T_m^{-1} e_1 (T_m^{-1} in place of T_m^{-1/2}).
+ * With a preconditioner M = tau B_bar^p (Proposition 1's factor
+ * F = M^{1/2}) it solves A u = M^{-1/2} b with A = M^{-1/2} Q M^{-1/2} and
+ * returns x = M^{-1/2} u.
+ *
+ * Stopping rule: the relative residual of the iterated system,
+ * ||r_m|| / ||b~|| = beta_m |e_m^T T_m^{-1} e_1| <= tol, with b~ = b
+ * (no preconditioner; r_m = b - Q x_m scaled by 1/tau) or
+ * b~ = M^{-1/2} b (r_m the residual of A u = b~), from the LDL^T recurrence
+ * of the stopping rule of gmrf_sample.  info[k].err_est is that relative
+ * residual; info[k].m_used the number of steps.
+ *
+ * b and x: [nrhs][n] of the problem's precision (float for FP32, double for
+ * FP64), host or device, must not overlap; b is not modified.  info [nrhs]
+ * (host, may be NULL).  Returns the worst per-right-hand-side status
+ * (GMRF_OK, GMRF_ERR_NOT_CONVERGED with x_m at m_max written,
+ * GMRF_ERR_NOT_SPD, GMRF_ERR_NUMERIC); GMRF_ERR_INVALID for a bad option;
+ * GMRF_ERR_OOM when one right-hand side does not fit in device memory.
+ * A zero right-hand side gives x = 0 with status GMRF_OK and m_used = 0. */
+int gmrf_solve(gmrf_problem* p, const gmrf_solve_opts* opts, const void* b, void* x, gmrf_result_info* info);
+
 /* Matrix-free operator applies on nvec vectors of the problem's precision
  * (Section 2's "routine that computes the matrix-vector product"), for
  * testing and for callers composing their own solvers:

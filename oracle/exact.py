@@ -8,6 +8,7 @@
   the cell-centred Neumann lattice with the DCT-II and for Dirichlet with the
   DST-I (constant kappa^2 only).
 * Section 6: the Hutchinson terms v^T log(Q) v.
+* Section 5.1: the linear solve x = Q^{-1} b of the sMMALA proposal mean.
 
 Everything here is FP64.  Pins: tests/test_oracle_exact.py.
 """
@@ -114,3 +115,19 @@ def quadform_log_spectral(shape, bc, op, kappa2_const, tau, V, kappa2_prior=None
         c = spectral_coefficients(shape, bc, v)
         out.append(float(np.sum(np.abs(c) ** 2 * np.log(mu))))
     return np.array(out)
+
+
+# ---------------------------------------------------------------- linear solves (Section 5.1)
+def solve_sparse(Q, B):
+    """x = Q^{-1} b for each row b of B (the sMMALA mean's system, Section 5.1),
+    by a sparse LU factorisation of Q (SuperLU)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    lu = spla.splu(sp.csc_matrix(Q))
+    return np.array([lu.solve(np.asarray(b, dtype=np.float64).reshape(-1)) for b in np.atleast_2d(B)])
+
+
+def solve_spectral(shape, bc, op, kappa2_const, tau, b, kappa2_prior=None):
+    """x = Q^{-1} b for constant kappa^2 through the closed-form eigenvalues."""
+    mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau, kappa2_prior=kappa2_prior)
+    return spectral_apply(shape, bc, 1.0 / mu, b)

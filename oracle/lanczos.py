@@ -150,6 +150,34 @@ def cg_residual_direct(apply_A, z, run, m=None) -> float:
     return float(np.linalg.norm(np.asarray(z).reshape(-1) - apply_A(y)))
 
 
+def cg_solve(apply_A, b, tol, m_max):
+    """Conjugate gradients (Hestenes and Stiefel) for A x = b from x_0 = 0:
+    r_0 = p_0 = b; a_k = r_k^T r_k / p_k^T A p_k; x_{k+1} = x_k + a_k p_k;
+    r_{k+1} = r_k - a_k A p_k; p_{k+1} = r_{k+1} + (r_{k+1}^T r_{k+1} / r_k^T r_k) p_k.
+    Stops at the first k with ||r_k|| <= tol ||b|| (k <= m_max).  Its iterates
+    are the Lanczos ones, x_k = ||b|| V_k T_k^{-1} e_1 (the link Theorem 1's
+    residual r_m rests on).  Returns (x, k, status in {'ok', 'not_converged'})."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    x = np.zeros_like(b)
+    r = b.copy()
+    bn = float(np.linalg.norm(b))
+    if bn == 0.0:
+        return x, 0, "ok"
+    p = r.copy()
+    rr = float(r @ r)
+    for k in range(1, m_max + 1):
+        Ap = apply_A(p)
+        a = rr / float(p @ Ap)
+        x = x + a * p
+        r = r - a * Ap
+        rr_new = float(r @ r)
+        if np.sqrt(rr_new) <= tol * bn:
+            return x, k, "ok"
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, m_max, "not_converged"
+
+
 def posterior_bound(lam_min, res_norm) -> float:
     """Theorem 1, eq. (krylov_bound): lambda_min^{-1/2} ||r_m||."""
     return float(res_norm / np.sqrt(lam_min))

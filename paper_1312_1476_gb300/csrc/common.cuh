@@ -178,7 +178,7 @@ struct VecState {
 struct StepParams {
   int m_max;      // largest subspace size
   int nslots;     // ring size of the stored basis (m_max + 1, or 2 when V_m is not kept)
-  int pad0;
+  int solve;      // 1: the iteration solves A u = z (stopping rule on the CG residual), 0: sampling / quadrature
   double tol;     // stopping tolerance on the relative estimate
   double bd_tol;  // breakdown threshold relative to ||T_m||
   // bfloat16 copy of the basis for the assembly only ([nvec][m_max + 1][n]),
@@ -334,7 +334,14 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
       if (b <= P.bd_tol * (v.amax + v.bmax)) {
         v.status = VS_DONE;  // invariant Krylov subspace: x_m is exact
         v.err_est = 0.0;
-        need = 1;            // theta still wanted for the T_m function
+        need = !P.solve;     // theta still wanted for the T_m function of a sample
+      } else if (P.solve) {
+        // linear solve: x_m = ||z|| V_m T_m^{-1} e_1 is the CG iterate, with
+        // relative residual ||r_m|| / ||z|| = beta_m |e_m^T T_m^{-1} e_1|
+        const double rres = b * fabs(u / d);
+        v.err_est = rres;
+        if (rres <= P.tol) v.status = VS_DONE;
+        else if (j + 1 >= P.m_max) v.status = GMRF_ERR_NOT_CONVERGED;
       } else {
         double est_lb = pfac / sqrt(v.theta);  // theta >= theta_min(T_m): a lower bound of est
         v.err_est = est_lb;

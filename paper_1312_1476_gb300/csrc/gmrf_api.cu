@@ -89,7 +89,7 @@ bool is_device_ptr(const void* p) {
 struct StepGraph {
   cudaGraphExec_t exec = nullptr;
   GraphTrace tr;
-  int nvec = -1, nslots = 0, m_max = 0, c = 0, kernels_per_step = 1, zchunk = 0;
+  int nvec = -1, nslots = 0, m_max = 0, c = 0, kernels_per_step = 1, zchunk = 0, solve = 0;
   double tol = 0.0;
   const void *W0 = nullptr, *V = nullptr, *Vb = nullptr, *st = nullptr, *S = nullptr, *partials = nullptr;
   const void* Xacc = nullptr;
@@ -119,7 +119,7 @@ struct gmrf_problem {
   PrecondTables pre;
   // Lanczos workspace (grow-only)
   DevBuf W0, W1, V, st, alpha, beta, alpha_f, beta2_f, partials, counters, y, scratch, nodes, q, out2, stage,
-      stage2, work, Vb, xacc, accn;
+      stage2, work, Vb, xacc, accn, solvew;
   VecState* st_host = nullptr;
   int st_host_cap = 0;
   int tune_bw = 0;  // vectors per Lanczos launch (0: as many as fit)
@@ -252,7 +252,8 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   const void* S = p->precond ? p->pre.S : nullptr;
   if (G.exec && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c && G.tol == P.tol &&
       G.W0 == b.W[0] && G.V == b.V && G.Vb == b.Vb && G.st == b.st && G.S == S && G.partials == b.partials &&
-      G.timed == timed && G.zchunk == p->g.zchunk && G.Xacc == b.Xacc && G.xscale == b.xscale)
+      G.timed == timed && G.zchunk == p->g.zchunk && G.Xacc == b.Xacc && G.xscale == b.xscale &&
+      G.solve == P.solve)
     return GMRF_OK;
   G.reset();
   cudaStream_t s = p->ws;
@@ -281,6 +282,7 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   G.m_max = P.m_max;
   G.c = c;
   G.tol = P.tol;
+  G.solve = P.solve;
   G.W0 = b.W[0];
   G.V = b.V;
   G.Vb = b.Vb;
@@ -295,12 +297,14 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   return GMRF_OK;
 }
 
-int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, int check_every) {
+int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, int check_every,
+                bool solve = false) {
   cudaStream_t s = p->ws;
   CK(traced(KC_INIT, s, 1, [&] { return launch_lanczos_init(p->fp64, p->g.n, b, s); }));
   StepParams P{};
   P.m_max = m_max;
   P.nslots = b.nslots;
+  P.solve = solve ? 1 : 0;
   P.tol = tol;
   P.bd_tol = p->fp64 ? 1e-13 : 1e-6;
   P.vb = b.Vb;
@@ -489,7 +493,7 @@ void gmrf_destroy(gmrf_problem* p) {
   p->graph.reset();
   DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,
                     &p->partials, &p->counters, &p->y, &p->scratch, &p->nodes, &p->q, &p->out2, &p->stage,
-                    &p->stage2, &p->work, &p->Vb, &p->xacc, &p->accn};
+                    &p->stage2, &p->work, &p->Vb, &p->xacc, &p->accn, &p->solvew};
   for (DevBuf* b : bufs) release(*b, p->ws);
   precond_free(p->pre, p->ws);
   if (p->ws) cudaStreamSynchronize(p->ws);
@@ -588,6 +592,77 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
   CKR(leave(p));
   fill_info(all.data(), o->nsamples, info);
   return worst_status(all.data(), o->nsamples);
+}
+
+int gmrf_solve(gmrf_problem* p, const gmrf_solve_opts* o, const void* b_in, void* x_out, gmrf_result_info* info) {
+  if (!p || !o || !b_in || !x_out) return GMRF_ERR_INVALID;
+  if (!(o->tol > 0.0) || !std::isfinite(o->tol) || o->m_max < 1 || o->m_max > 8192 || o->nrhs < 1 ||
+      o->reserved != 0)
+    return GMRF_ERR_INVALID;
+  const size_t n = p->g.n, es = esize(p);
+  const int m_max = o->m_max;
+  const int nslots = m_max + 1;
+  const bool x_dev = is_device_ptr(x_out);
+  const bool b_dev = is_device_ptr(b_in);
+  const size_t extra = (x_dev ? 0 : n * es) + (b_dev ? 0 : n * es) +
+                       (p->precond ? precond_extra_bytes(p->pre, es) + n * es : 0) + sizeof(double) * m_max;
+  int chunk = batch_size(p, o->nrhs, nslots, m_max, false, extra);
+  if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
+  if (chunk < 1) return GMRF_ERR_OOM;
+  cudaStream_t s = p->ws;
+  CKR(enter(p));
+  std::vector<VecState> all((size_t)o->nrhs);
+  for (int s0 = 0; s0 < o->nrhs; s0 += chunk) {
+    const int c = std::min(chunk, o->nrhs - s0);
+    LanczosBufs b;
+    CKR(ensure_lanczos(p, c, nslots, m_max, false, b));
+    CKR(ensure(p->solvew, sizeof(double) * (size_t)c * m_max, p->ws));
+    const char* bsrc = (const char*)b_in + (size_t)s0 * n * es;
+    // start vector: b (no preconditioner) or B_bar^{-p/2} b, normalised by the first step
+    if (p->precond == GMRF_PREC_NONE) {
+      CK(cudaMemcpyAsync(b.W[0], bsrc, (size_t)c * n * es, b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         s));
+    } else {
+      const void* dsrc = bsrc;
+      if (!b_dev) {
+        CKR(ensure(p->stage2, (size_t)c * n * es, p->ws));
+        CK(cudaMemcpyAsync(p->stage2.p, bsrc, (size_t)c * n * es, cudaMemcpyHostToDevice, s));
+        dsrc = p->stage2.p;
+      }
+      CK(traced(KC_PRE_APPLY, s, 3,
+                [&] { return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, dsrc, b.W[0], c, s); }));
+    }
+    CKR(run_lanczos(p, b, o->tol, m_max, o->check_every, true));
+    CK(traced(KC_TM, s, 1, [&] { return launch_tm_inv(b, (double*)p->solvew.p, (double*)p->y.p, s); }));
+    void* xdst = (char*)x_out + (size_t)s0 * n * es;
+    if (!x_dev) {
+      CKR(ensure(p->stage, (size_t)c * n * es, p->ws));
+      xdst = p->stage.p;
+    }
+    // x_m = ||b~|| V_m T_m^{-1} e_1; Q = tau Q~ (the steps run on Q~ or A, both tau-free)
+    if (p->precond == GMRF_PREC_NONE) {
+      CK(traced(KC_ASSEMBLE, s, 1, [&] {
+        return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0 / p->tau, xdst, s);
+      }));
+    } else {
+      // u = ||b~|| V_m T_m^{-1} e_1 = A^{-1} b~, then x = tau^{-1} B_bar^{-p/2} u
+      CKR(ensure(p->work, (size_t)c * n * es, p->ws));
+      CK(traced(KC_ASSEMBLE, s, 1,
+                [&] { return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
+      CK(traced(KC_PRE_APPLY, s, 3,
+                [&] { return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, p->work.p, xdst, c, s); }));
+      CK(traced(KC_OTHER, s, 1, [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / p->tau, s); }));
+    }
+    if (!x_dev)
+      CK(cudaMemcpyAsync((char*)x_out + (size_t)s0 * n * es, xdst, (size_t)c * n * es, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * c, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    trace_collect();
+    std::memcpy(all.data() + s0, p->st_host, sizeof(VecState) * c);
+  }
+  CKR(leave(p));
+  fill_info(all.data(), o->nrhs, info);
+  return worst_status(all.data(), o->nrhs);
 }
 
 int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, double* std_err, double* q_out,

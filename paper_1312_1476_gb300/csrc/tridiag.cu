@@ -216,7 +216,40 @@ __global__ void k_logdet_reduce(const double* q, int nq, int group, double shift
   }
 }
 
+// y = T_m^{-1} e_1 (the CG coefficients of a linear solve) by the LDL^T
+// factorisation that the stopping rule also runs: d_0 = a_0,
+// d_i = a_i - b_{i-1}^2 / d_{i-1}, l_i = b_{i-1} / d_{i-1}; L w = e_1 gives
+// w_i = -l_i w_{i-1}; then y = L^{-T} D^{-1} w.  One thread per vector.
+__global__ void k_tm_inv(const VecState* st, const double* alpha, const double* beta, int m_max, int nvec,
+                         double* dwork, double* y) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nvec) return;
+  const VecState v = st[s];
+  if (!usable(v)) return;
+  const int m = v.m;
+  const double* a = alpha + (size_t)s * m_max;
+  const double* b = beta + (size_t)s * m_max;
+  double* d = dwork + (size_t)s * m_max;
+  double* ys = y + (size_t)s * m_max;
+  double dp = a[0], w = 1.0;
+  d[0] = dp;
+  ys[0] = w / dp;  // z_i = w_i / d_i
+  for (int i = 1; i < m; ++i) {
+    const double l = b[i - 1] / dp;
+    dp = a[i] - l * b[i - 1];
+    w = -l * w;
+    d[i] = dp;
+    ys[i] = w / dp;
+  }
+  for (int i = m - 2; i >= 0; --i) ys[i] -= (b[i] / d[i]) * ys[i + 1];  // y_i = z_i - l_{i+1} y_{i+1}
+}
+
 }  // namespace
+
+cudaError_t launch_tm_inv(const LanczosBufs& b, double* dwork, double* y, cudaStream_t s) {
+  k_tm_inv<<<(b.nvec + 31) / 32, 32, 0, s>>>(b.st, b.alpha, b.beta, b.m_max, b.nvec, dwork, y);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tm_inv_sqrt(const LanczosBufs& b, bool fp64, TmNodes* nodes, double* scratch, double* y,
                                cudaStream_t s) {

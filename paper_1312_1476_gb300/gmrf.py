@@ -61,6 +61,11 @@ class GmrfLogdetOpts(ctypes.Structure):
                 ("colour_dist", ctypes.c_int32)]
 
 
+class GmrfSolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("m_max", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class GmrfTuning(ctypes.Structure):
     _fields_ = [("block_width", ctypes.c_int32), ("zchunk", ctypes.c_int32), ("vec_steps_per_s", ctypes.c_double),
                 ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -78,6 +83,7 @@ def _load():
         "gmrf_sample": (ctypes.c_int, [P, ctypes.POINTER(GmrfSampleOpts), P, ctypes.POINTER(GmrfResultInfo)]),
         "gmrf_logdet": (ctypes.c_int, [P, ctypes.POINTER(GmrfLogdetOpts), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(GmrfResultInfo)]),
+        "gmrf_solve": (ctypes.c_int, [P, ctypes.POINTER(GmrfSolveOpts), P, P, ctypes.POINTER(GmrfResultInfo)]),
         "gmrf_apply": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int64, P, P]),
         "gmrf_rng": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                     ctypes.c_uint64, P, P]),
@@ -239,6 +245,18 @@ class Problem:
         if raise_on_error and rc not in (OK, ERR_NOT_CONVERGED):
             raise GmrfError(rc, "gmrf_logdet")
         return ld.value, se.value, q, infos, rc
+
+    def solve(self, b, out, nrhs=1, tol=1e-6, m_max=300, check_every=16, raise_on_error=True):
+        """x = Q^{-1} b into ``out`` ([nrhs][n], host or device) by the Lanczos
+        form of (preconditioned) conjugate gradients; returns (return code,
+        list of SampleInfo with err_est = the relative residual)."""
+        o = GmrfSolveOpts(float(tol), int(m_max), int(nrhs), int(check_every), 0)
+        info = (GmrfResultInfo * int(nrhs))()
+        rc = _lib.gmrf_solve(self._h, ctypes.byref(o), _ptr(b), _ptr(out), info)
+        infos = [SampleInfo(i.m_used, i.status, i.err_est) for i in info]
+        if raise_on_error and rc not in (OK, ERR_NOT_CONVERGED):
+            raise GmrfError(rc, "gmrf_solve")
+        return rc, infos
 
     def apply_inv_sqrt_noalloc(self, v, y, nvec=1):
         """y = M^{-1/2} v without any device allocation (device pointers only;

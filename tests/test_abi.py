@@ -50,6 +50,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(gmrf_desc, kappa2), offsetof(gmrf_desc, tau),
          offsetof(gmrf_desc, precision), offsetof(gmrf_sample_opts, z_in));
   printf("%zu %zu\n", offsetof(gmrf_result_info, err_est), offsetof(gmrf_logdet_opts, probes_in));
+  printf("%zu %zu %zu\n", sizeof(gmrf_solve_opts), offsetof(gmrf_solve_opts, nrhs),
+         offsetof(gmrf_solve_opts, reserved));
   return 0;
 }
 """
@@ -63,7 +65,8 @@ int main(void) {
     assert vals[:4] == [cs(g.GmrfDesc), cs(g.GmrfSampleOpts), cs(g.GmrfResultInfo), cs(g.GmrfLogdetOpts)]
     assert vals[4:] == [g.GmrfDesc.kappa2.offset, g.GmrfDesc.tau.offset, g.GmrfDesc.precision.offset,
                         g.GmrfSampleOpts.z_in.offset, g.GmrfResultInfo.err_est.offset,
-                        g.GmrfLogdetOpts.probes_in.offset]
+                        g.GmrfLogdetOpts.probes_in.offset, cs(g.GmrfSolveOpts), g.GmrfSolveOpts.nrhs.offset,
+                        g.GmrfSolveOpts.reserved.offset]
 
 
 def test_invalid_descriptors_rejected_on_host(g):
@@ -82,4 +85,5 @@ def test_invalid_descriptors_rejected_on_host(g):
         d = g.GmrfDesc(**{**base, **b})
         assert lib.gmrf_create(ctypes.byref(d), None, ctypes.byref(h)) == g.ERR_UNSUPPORTED, b
     assert lib.gmrf_sample(None, None, None, None) == g.ERR_INVALID
+    assert lib.gmrf_solve(None, None, None, None, None) == g.ERR_INVALID
     assert g.strerror(g.ERR_NOT_SPD).startswith("operator")

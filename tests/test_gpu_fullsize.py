@@ -4,7 +4,8 @@ Proposition 1 for the preconditioned case), plus the sample covariance
 against Q^{-1}.
 
 * 1024 x 1024 SPDE, mirror-preconditioned, one FP32 sample at tol 1e-6:
-  whole vector against the oracle's FP64 Lanczos run to 1e-9.
+  whole vector against the oracle's FP64 Lanczos run to 1e-9; the linear
+  solve x = Q^{-1} b of the same problem against the oracle's FP64 CG.
 * 512 x 512 SPDE, 256 samples in one batch: two of the vectors against the
   oracle; 64 fixed Rademacher probes: two per-probe quadratures.
 * 3-D 7-point at 128^3 (the 256^3 recipe one size down): two of 16 vectors
@@ -58,6 +59,34 @@ def test_headline_1024_mirror_fp32(g):
     assert rc == g.OK and info[0].err_est <= 1e-6
     xe = _spde_oracle_sample(shape, k2, kb, z[0])
     assert _rel(x.cpu().numpy(), xe) <= 1e-6
+
+
+def test_headline_1024_solve_fp32(g):
+    # The Section 5.1 linear solve on the headline problem: x = Q^{-1} b from
+    # the mirror-preconditioned Lanczos/CG iteration at tol 1e-6 (relative
+    # residual of A u = M^{-1/2} b), against the oracle's preconditioned CG in
+    # FP64 run to 1e-12.  Error bound kappa(A) tol plus the FP32 floor
+    # 64 u kappa(A); kappa(A) >= theta_max / theta_min of the oracle's own
+    # Lanczos run (extreme Ritz values converge first), used with a margin of 2.
+    shape = (1024, 1024)
+    n = 1024 * 1024
+    k2 = inputs.kappa2_gp_field(shape, seed=1)
+    kb = precond.kappa2_bar(k2)
+    b = inputs.gaussian_vectors(1, n, seed=7, dtype=np.float32)
+    with g.Problem(shape, "neumann", "spde_squared", kappa2=_dev(k2), precond="mirror", kappa2_precond=kb) as p:
+        x = torch.empty(n, dtype=torch.float32, device="cuda")
+        rc, info = p.solve(_dev(b), x, nrhs=1, tol=1e-6, m_max=2000)
+    assert rc == g.OK and info[0].err_est <= 1e-6
+    Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2.astype(np.float64), 1.0)
+    A = olz.preconditioned_operator(Q, shape, "neumann", "spde_squared", kb, 1.0)
+    P = lambda v: precond.apply_power(shape, "neumann", "spde_squared", kb, 1.0, v, -0.5)
+    u, k, st = olz.cg_solve(A, P(b[0].astype(np.float64)), 1e-12, 2000)
+    assert st == "ok"
+    xe = P(u)
+    run = olz.lanczos(A, inputs.gaussian_vectors(1, n, seed=8, dtype=np.float64)[0], m=60)
+    th = olz.tm_eigh(run["alpha"], run["beta"])[0]
+    kap = 2.0 * th[-1] / th[0]
+    assert _rel(x.cpu().numpy(), xe) <= kap * 1e-6 + 64 * 2.0 ** -24 * kap
 
 
 def test_batched_512_samples_and_logdet_probes(g):

@@ -75,3 +75,27 @@ def test_quadform_log_routes_and_trace(bc):
     # unit-vector probes give the trace exactly: sum_i e_i^T log(Q) e_i = log det Q
     tr = exact.quadform_log_dense(Q, np.eye(n)).sum()
     assert abs(tr - exact.logdet_cholesky(Q)) <= 1e-9 * abs(tr)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("bc", stencil.BCS)
+@pytest.mark.parametrize("op", stencil.OPS)
+def test_solve_routes(shape, bc, op):
+    # x = Q^{-1} b (Section 5.1's mean solve): the sparse LU solution has a
+    # vanishing residual under the sparse matvec, and for constant kappa^2 it
+    # equals the closed-form spectral solve; a variable kappa^2 field is
+    # checked through the residual and x^T Q x = x^T b.
+    rng = np.random.default_rng(7)
+    n = int(np.prod(shape))
+    B = inputs.gaussian_vectors(2, n, seed=13, dtype=np.float64)
+    Qc = stencil.precision_matrix(shape, bc, op, 0.3, tau=1.7, kappa2_prior=KP)
+    xs = exact.solve_sparse(Qc, B)
+    for x, b in zip(xs, B):
+        assert np.linalg.norm(Qc @ x - b) <= 1e-11 * np.linalg.norm(b)
+        xf = exact.solve_spectral(shape, bc, op, 0.3, 1.7, b, kappa2_prior=KP)
+        np.testing.assert_allclose(xf, x, rtol=0, atol=1e-10 * np.linalg.norm(x))
+    k2 = rng.uniform(0.05, 1.0, size=shape)
+    Qv = stencil.precision_matrix(shape, bc, op, k2, tau=0.6, kappa2_prior=KP)
+    xv = exact.solve_sparse(Qv, B[:1])[0]
+    assert np.linalg.norm(Qv @ xv - B[0]) <= 1e-11 * np.linalg.norm(B[0])
+    assert abs(xv @ (Qv @ xv) - xv @ B[0]) <= 1e-10 * abs(xv @ B[0])

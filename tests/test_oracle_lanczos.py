@@ -207,3 +207,38 @@ def test_coloured_lanczos_quadrature_matches_dense():
             ref = exact.quadform_log_dense(Q.toarray(), np.where(mk, draws[d], 0.0)[None, :])[0]
             assert abs(q[d, c] - ref) <= 1e-9 * abs(ref) + 1e-9
     assert abs(est - q.sum(axis=1).mean()) <= 1e-12 * abs(est)
+
+
+def test_cg_exact_termination_and_lanczos_iterates():
+    # CG on an operator with k distinct eigenvalues ends in k steps with the
+    # exact solution; every CG iterate equals the Lanczos one
+    # ||b|| V_k T_k^{-1} e_1 built by the independent Lanczos code.
+    rng = np.random.default_rng(2)
+    d = np.repeat([0.5, 1.5, 4.0, 9.0], 10)
+    rng.shuffle(d)
+    b = rng.standard_normal(d.size)
+    x, k, st = lanczos.cg_solve(lambda v: d * v, b, tol=1e-13, m_max=40)
+    assert st == "ok" and k == 4
+    np.testing.assert_allclose(x, b / d, rtol=1e-11)
+    k2, Q = _problem((6, 7), "dirichlet", "spde_squared")
+    b = inputs.gaussian_vectors(1, 42, seed=3, dtype=np.float64)[0]
+    run = lanczos.lanczos(lambda v: Q @ v, b, m=12, reorth=True)
+    for m in (3, 7, 12):
+        T = lanczos.tridiagonal(run["alpha"][:m], run["beta"][:m])
+        y = run["znorm"] * (run["V"][:m].T @ np.linalg.solve(T, np.eye(m)[0]))
+        xc, kc, _ = lanczos.cg_solve(lambda v: Q @ v, b, tol=0.0, m_max=m)
+        assert kc == m
+        np.testing.assert_allclose(xc, y, rtol=0, atol=1e-9 * np.linalg.norm(y))
+
+
+def test_cg_reaches_the_sparse_solve_with_the_stopping_rule():
+    # the relative-residual rule is met, and the error obeys ||e|| / ||x|| <= kappa(Q) tol
+    k2, Q = _problem((8, 9), "neumann", "shifted_laplacian")
+    b = inputs.gaussian_vectors(1, 72, seed=6, dtype=np.float64)[0]
+    xe = exact.solve_sparse(Q, b)[0]
+    lam = np.linalg.eigvalsh(Q.toarray())
+    for tol in (1e-4, 1e-8, 1e-12):
+        x, k, st = lanczos.cg_solve(lambda v: Q @ v, b, tol=tol, m_max=400)
+        assert st == "ok"
+        assert np.linalg.norm(b - Q @ x) <= tol * np.linalg.norm(b) * (1 + 1e-6)
+        assert np.linalg.norm(x - xe) <= (lam[-1] / lam[0]) * tol * np.linalg.norm(xe) * 1.01
