@@ -579,7 +579,7 @@ __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[vpl<LOGL
 }
 
 template <int KIND, int LOGL, int MODE>
-__global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>()), LOGL == 9 ? 1 : 0)
+__global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>()), LOGL == 9 ? 1 : (LOGL == 8 ? 4 : 0))
     k_row(Args a) {
   constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), NX = 2 * L;
   constexpr int RB = rows_per_block<KIND, LOGL>(), TP = tile_pitch<KIND, LOGL>();
