@@ -406,6 +406,11 @@ def measure_variants(args, gmrf, torch, flush, peak):
             mc, lc = timed(lambda i: p.logdet(nprobes=nd, tol=TOL, m_max=M_MAX_512, seed=30 + i, colour_dist=pd), 2)
             coloured["p%d" % pd] = {"draws": nd, "quadratures": nd * (pd + 1) ** 2, "logdet": lc[0],
                                     "std_err": lc[1], "logdets_per_s": 1e3 / mc}
+        # the same 256 samples and 64 probes as one block of 320 vectors (one call)
+        msc, rsl = timed(lambda i: p.sample_logdet(x, nsamples=ns, nprobes=64, tol=TOL, m_max=M_MAX_512,
+                                                   seed=20 + i, probe_seed=30 + i), 3)
+        one_block = {"vectors": ns + 64, "ms_per_call": msc, "samples_per_s": ns * 1e3 / msc,
+                     "logdets_per_s": 1e3 / msc, "logdet": rsl[2], "logdet_std_err": rsl[3], "status": rsl[0]}
         out["batched_512"] = {
             "workload": "512x512 SPDE (same recipe, ell 64), mirror M, 256 samples per call (m_max %d, one "
                         "batch); log det with 64 Rademacher probes per call" % M_MAX_512,
@@ -413,7 +418,7 @@ def measure_variants(args, gmrf, torch, flush, peak):
             "m_mean": float(np.mean([i.m_used for i in info])), "status": rc,
             "logdets_per_s": 1e3 / mld, "logdet": ld[0], "logdet_std_err": ld[1],
             "logdet_m_mean": float(np.mean([i.m_used for i in ld[3]])), "autotune": tune512,
-            "logdet_coloured": coloured}
+            "logdet_coloured": coloured, "samples_and_probes_one_block": one_block}
 
     # 3-D 256^3 Dirichlet 7-point, kappa^2 ~ U[0.01, 1], 16 samples; m_max capped
     # so that all 16 Lanczos bases (m_max + 3 vectors each) stay resident in HBM

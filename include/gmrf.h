@@ -188,6 +188,22 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* opts, void* x_out, gmrf
 int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* opts, double* logdet, double* std_err,
                 double* q_out, gmrf_result_info* info);
 
+/* Sections 4 and 6 in one Lanczos batch: the nsamples samples of sample_opts
+ * (Algorithm 1) and the nprobes * ncolours log-det probes of logdet_opts run
+ * as one block of vectors through the same step kernels (many z vectors and
+ * Hutchinson probes per launch), samples first.  Every output is bitwise the
+ * one of the separate calls gmrf_sample(sample_opts) and
+ * gmrf_logdet(logdet_opts) with the same seeds or inputs: the arithmetic of a
+ * vector does not depend on the rest of its batch.  Both option sets must
+ * have the same tol and m_max, and sample_opts.v_storage must be NATIVE
+ * (otherwise GMRF_ERR_INVALID); sample_opts.check_every is used.  Outputs as
+ * for the two calls (x_out, sample_info [nsamples]; logdet, std_err host
+ * pointers; q_out, probe_info [nprobes * ncolours], may be NULL).  Returns the
+ * worst status over all vectors; GMRF_ERR_OOM when one vector does not fit. */
+int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* sample_opts, const gmrf_logdet_opts* logdet_opts,
+                       void* x_out, gmrf_result_info* sample_info, double* logdet, double* std_err, double* q_out,
+                       gmrf_result_info* probe_info);
+
 typedef struct {
   double tol;          /* relative residual at which an iteration stops, > 0 (see gmrf_solve) */
   int32_t m_max;       /* largest subspace size (CG steps), 1 .. 8192 */

@@ -332,6 +332,24 @@ int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, in
   return GMRF_OK;
 }
 
+// The vectors [off, off + cnt) of a Lanczos batch as a batch of their own
+// (the T_m functions and the assembly of a mixed batch of samples and probes).
+LanczosBufs sub_batch(const LanczosBufs& b, int off, int cnt, size_t n, size_t es) {
+  LanczosBufs r = b;
+  const size_t vo = (size_t)off * n * es;
+  r.W[0] = (char*)b.W[0] + vo;
+  r.W[1] = (char*)b.W[1] + vo;
+  r.V = (char*)b.V + vo * b.nslots;
+  r.Vb = nullptr;
+  r.st = b.st + off;
+  r.alpha = b.alpha + (size_t)off * b.m_max;
+  r.beta = b.beta + (size_t)off * b.m_max;
+  r.alpha_f = b.alpha_f + (size_t)off * b.m_max;
+  r.beta2_f = b.beta2_f + (size_t)off * b.m_max;
+  r.nvec = cnt;
+  return r;
+}
+
 void fill_info(const VecState* st, int nvec, gmrf_result_info* info) {
   if (!info) return;
   for (int s = 0; s < nvec; ++s) {
@@ -723,6 +741,113 @@ int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, doub
   *std_err = res[1];
   fill_info(all.data(), nq, info);
   return worst_status(all.data(), nq);
+}
+
+int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_logdet_opts* lo, void* x_out,
+                       gmrf_result_info* sinfo, double* logdet, double* std_err, double* q_out,
+                       gmrf_result_info* linfo) {
+  if (!p || !so || !lo || !x_out || !logdet || !std_err) return GMRF_ERR_INVALID;
+  if (!(so->tol > 0.0) || !std::isfinite(so->tol) || so->m_max < 1 || so->m_max > 8192 || so->nsamples < 1 ||
+      so->v_storage != GMRF_VSTORE_NATIVE || lo->tol != so->tol || lo->m_max != so->m_max || lo->nprobes < 1 ||
+      lo->colour_dist < 0 || lo->colour_dist > 15)
+    return GMRF_ERR_INVALID;
+  const size_t n = p->g.n, es = esize(p);
+  const int m_max = so->m_max, nslots = m_max + 1;
+  const int P = lo->colour_dist + 1;
+  int ncol = 1;
+  for (int d = 0; d < p->g.dim; ++d) ncol *= P;
+  const int64_t total64 = (int64_t)so->nsamples + (int64_t)lo->nprobes * ncol;
+  if (total64 > (1 << 24)) return GMRF_ERR_INVALID;
+  const int ns = so->nsamples, nq = (int)(total64 - ns), total = (int)total64;
+  const bool x_dev = is_device_ptr(x_out);
+  const bool z_dev = so->z_in && is_device_ptr(so->z_in);
+  const bool r_dev = lo->probes_in && is_device_ptr(lo->probes_in);
+  const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) + n * es : 0);
+  int chunk = batch_size(p, total, nslots, m_max, true, extra);
+  if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
+  if (chunk < 1) return GMRF_ERR_OOM;
+  cudaStream_t s = p->ws;
+  CKR(enter(p));
+  CKR(ensure(p->stage2, sizeof(double) * (nq + 2), p->ws));
+  double* qall = (double*)p->stage2.p;
+  std::vector<VecState> all((size_t)total);
+  for (int t0 = 0; t0 < total; t0 += chunk) {
+    const int c = std::min(chunk, total - t0);
+    const int nsc = std::max(0, std::min(ns, t0 + c) - t0);  // samples of this chunk come first
+    const int nqc = c - nsc, q0 = std::max(0, t0 - ns);     // then probes q0 .. q0 + nqc - 1
+    LanczosBufs b;
+    CKR(ensure_lanczos(p, c, nslots, m_max, true, b));
+    // the same z and probes as gmrf_sample and gmrf_logdet (per-vector streams)
+    if (nsc > 0) {
+      if (so->z_in)
+        CK(cudaMemcpyAsync(b.W[0], (const char*)so->z_in + (size_t)t0 * n * es, (size_t)nsc * n * es,
+                           z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      else
+        CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, nsc, (int64_t)n, so->seed, t0, b.W[0], s); }));
+    }
+    if (nqc > 0) {
+      void* dst = (char*)b.W[0] + (size_t)nsc * n * es;
+      if (lo->probes_in)
+        CK(cudaMemcpyAsync(dst, (const char*)lo->probes_in + (size_t)q0 * n * es, (size_t)nqc * n * es,
+                           r_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      else if (ncol > 1)
+        CK(traced(KC_RNG, s, 1, [&] {
+          return launch_rng_coloured(p->fp64, nqc, (int64_t)n, lo->seed, q0, p->g.nx, p->g.ny, P, ncol, dst, s);
+        }));
+      else
+        CK(traced(KC_RNG, s, 1, [&] { return launch_rng(1, p->fp64, nqc, (int64_t)n, lo->seed, q0, dst, s); }));
+    }
+    CKR(run_lanczos(p, b, so->tol, m_max, so->check_every));
+    if (nsc > 0) {
+      const LanczosBufs bs = sub_batch(b, 0, nsc, n, es);
+      CK(traced(KC_TM, s, 3, [&] {
+        return launch_tm_inv_sqrt(bs, p->fp64, (TmNodes*)p->nodes.p, (double*)p->scratch.p, (double*)p->y.p, s);
+      }));
+      void* xdst = (char*)x_out + (size_t)t0 * n * es;
+      if (!x_dev) {
+        CKR(ensure(p->stage, (size_t)nsc * n * es, p->ws));
+        xdst = p->stage.p;
+      }
+      if (p->precond == GMRF_PREC_NONE) {
+        CK(traced(KC_ASSEMBLE, s, 1, [&] {
+          return launch_assemble(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0 / std::sqrt(p->tau), xdst, s);
+        }));
+      } else {
+        CKR(ensure(p->work, (size_t)nsc * n * es, p->ws));
+        CK(traced(KC_ASSEMBLE, s, 1,
+                  [&] { return launch_assemble(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
+        CK(traced(KC_PRE_APPLY, s, 3, [&] {
+          return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, p->work.p, xdst, nsc, s);
+        }));
+        CK(traced(KC_OTHER, s, 1,
+                  [&] { return launch_scale(p->fp64, xdst, (size_t)nsc * n, 1.0 / std::sqrt(p->tau), s); }));
+      }
+      if (!x_dev)
+        CK(cudaMemcpyAsync((char*)x_out + (size_t)t0 * n * es, xdst, (size_t)nsc * n * es, cudaMemcpyDeviceToHost,
+                           s));
+    }
+    if (nqc > 0) {
+      const LanczosBufs bq = sub_batch(b, nsc, nqc, n, es);
+      CK(traced(KC_TM, s, 2, [&] { return launch_tm_log(bq, p->fp64, (TmNodes*)p->nodes.p, qall + q0, s); }));
+    }
+    CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * c, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    trace_collect();
+    std::memcpy(all.data() + t0, p->st_host, sizeof(VecState) * c);
+  }
+  const double shift = p->logdet_M + (double)n * std::log(p->tau);
+  CK(traced(KC_TM, s, 1, [&] { return launch_logdet_reduce(qall, nq, ncol, shift, qall + nq, s); }));
+  double res[2];
+  CK(cudaMemcpyAsync(res, qall + nq, sizeof(res), cudaMemcpyDeviceToHost, s));
+  if (q_out) CK(cudaMemcpyAsync(q_out, qall, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  trace_collect();
+  CKR(leave(p));
+  *logdet = res[0];
+  *std_err = res[1];
+  fill_info(all.data(), ns, sinfo);
+  fill_info(all.data() + ns, nq, linfo);
+  return worst_status(all.data(), total);
 }
 
 int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void* y) {

@@ -84,6 +84,9 @@ def _load():
         "gmrf_logdet": (ctypes.c_int, [P, ctypes.POINTER(GmrfLogdetOpts), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(GmrfResultInfo)]),
         "gmrf_solve": (ctypes.c_int, [P, ctypes.POINTER(GmrfSolveOpts), P, P, ctypes.POINTER(GmrfResultInfo)]),
+        "gmrf_sample_logdet": (ctypes.c_int, [P, ctypes.POINTER(GmrfSampleOpts), ctypes.POINTER(GmrfLogdetOpts), P,
+                                              ctypes.POINTER(GmrfResultInfo), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(GmrfResultInfo)]),
         "gmrf_apply": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int64, P, P]),
         "gmrf_rng": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                     ctypes.c_uint64, P, P]),
@@ -245,6 +248,29 @@ class Problem:
         if raise_on_error and rc not in (OK, ERR_NOT_CONVERGED):
             raise GmrfError(rc, "gmrf_logdet")
         return ld.value, se.value, q, infos, rc
+
+    def sample_logdet(self, out, nsamples=1, nprobes=16, tol=1e-6, m_max=300, seed=2, probe_seed=3, z=None,
+                      probes=None, check_every=16, colour_dist=0, raise_on_error=True):
+        """Samples and log-det probes in one Lanczos batch (bitwise the results
+        of ``sample`` and ``logdet`` with the same arguments); returns
+        (return code, sample infos, logdet, std_err, q array, probe infos)."""
+        so = GmrfSampleOpts(float(tol), int(m_max), int(nsamples), int(seed) & (2 ** 64 - 1),
+                            _ptr(z) if z is not None else None, int(check_every), VSTORE["native"])
+        lo = GmrfLogdetOpts(float(tol), int(m_max), int(nprobes), int(probe_seed) & (2 ** 64 - 1),
+                            _ptr(probes) if probes is not None else None, int(check_every), int(colour_dist))
+        nq = int(nprobes) * (int(colour_dist) + 1) ** len(self.shape)
+        sinfo = (GmrfResultInfo * int(nsamples))()
+        linfo = (GmrfResultInfo * nq)()
+        ld = ctypes.c_double()
+        se = ctypes.c_double()
+        q = np.zeros(nq, dtype=np.float64)
+        rc = _lib.gmrf_sample_logdet(self._h, ctypes.byref(so), ctypes.byref(lo), _ptr(out), sinfo,
+                                     ctypes.byref(ld), ctypes.byref(se), ctypes.c_void_p(q.ctypes.data), linfo)
+        sinfos = [SampleInfo(i.m_used, i.status, i.err_est) for i in sinfo]
+        linfos = [SampleInfo(i.m_used, i.status, i.err_est) for i in linfo]
+        if raise_on_error and rc not in (OK, ERR_NOT_CONVERGED):
+            raise GmrfError(rc, "gmrf_sample_logdet")
+        return rc, sinfos, ld.value, se.value, q, linfos
 
     def solve(self, b, out, nrhs=1, tol=1e-6, m_max=300, check_every=16, raise_on_error=True):
         """x = Q^{-1} b into ``out`` ([nrhs][n], host or device) by the Lanczos

@@ -86,4 +86,5 @@ def test_invalid_descriptors_rejected_on_host(g):
         assert lib.gmrf_create(ctypes.byref(d), None, ctypes.byref(h)) == g.ERR_UNSUPPORTED, b
     assert lib.gmrf_sample(None, None, None, None) == g.ERR_INVALID
     assert lib.gmrf_solve(None, None, None, None, None) == g.ERR_INVALID
+    assert lib.gmrf_sample_logdet(None, None, None, None, None, None, None, None, None) == g.ERR_INVALID
     assert g.strerror(g.ERR_NOT_SPD).startswith("operator")

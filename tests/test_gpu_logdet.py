@@ -117,3 +117,39 @@ def test_coloured_estimator_unbiased_and_lower_variance(g):
             assert abs(ld - ld_exact) <= 4 * se
             ses.append(se)
     assert ses[1] < 0.7 * ses[0] and ses[2] < ses[1]
+
+
+@pytest.mark.parametrize("colour_dist", [0, 1])
+@pytest.mark.parametrize("block_width", [0, 3])
+@pytest.mark.parametrize("pre", ["mirror", "none"])
+def test_samples_and_probes_in_one_batch(g, colour_dist, block_width, pre):
+    # gmrf_sample_logdet runs the samples and the probes as one block of
+    # vectors; every output equals the separate calls bitwise (per-vector
+    # arithmetic does not depend on the batch).  Block width 3 makes chunks
+    # that straddle the samples / probes boundary.
+    shape = (64, 64)
+    n = 4096
+    k2 = inputs.kappa2_gp_field(shape, seed=1, ell=8.0)
+    op = "spde_squared" if pre == "mirror" else "shifted_laplacian"
+    with g.Problem(shape, "neumann", op, kappa2=_dev(k2), precond=pre) as p:
+        if block_width:
+            p.set_tuning(block_width=block_width)
+        m_max = 300
+        x1 = torch.empty(5 * n, device="cuda")
+        rc1, si1 = p.sample(x1, nsamples=5, tol=1e-6, m_max=m_max, seed=11)
+        ld1, se1, q1, li1, rc2 = p.logdet(nprobes=4, tol=1e-6, m_max=m_max, seed=12, colour_dist=colour_dist)
+        x2 = torch.empty(5 * n, device="cuda")
+        rc, si2, ld2, se2, q2, li2 = p.sample_logdet(x2, nsamples=5, nprobes=4, tol=1e-6, m_max=m_max, seed=11,
+                                                     probe_seed=12, colour_dist=colour_dist)
+        xh = np.zeros((5, n), dtype=np.float32)
+        rch, _, ldh, _, _, _ = p.sample_logdet(xh, nsamples=5, nprobes=4, tol=1e-6, m_max=m_max, seed=11,
+                                               probe_seed=12, colour_dist=colour_dist)
+        with pytest.raises(g.GmrfError):
+            p.sample_logdet(x2, nsamples=5, nprobes=4, tol=1e-6, m_max=m_max, seed=11, probe_seed=12,
+                            colour_dist=-1)
+    assert rc == rc1 == rc2 == rch == g.OK
+    assert torch.equal(x1, x2) and np.array_equal(xh, x1.cpu().numpy().reshape(5, n))
+    assert np.array_equal(q1, q2) and ld1 == ld2 == ldh and se1 == se2
+    assert [i.m_used for i in si1] == [i.m_used for i in si2]
+    assert [i.m_used for i in li1] == [i.m_used for i in li2]
+    assert len(q2) == 4 * (colour_dist + 1) ** 2
