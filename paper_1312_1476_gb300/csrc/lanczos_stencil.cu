@@ -466,6 +466,9 @@ cudaError_t dispatch(const Grid& g, StencilArgs<T> a, int nvec, cudaStream_t s) 
     return cudaGetLastError();
   }
   a.nzc = 1;
+  if (stencil2d_strip_eligible(g, sizeof(T) == 8) &&
+      (STEP || stencil2d_strip_pointers_ok(a.Win, a.Wout, a.kappa2)))
+    return launch_stencil2d_strip<T>(g, a, nvec, STEP, s);
 #define GMRF_L2(OPV, BCV) k_stencil2d<T, OPV, BCV, STEP><<<grd, blk, 0, s>>>(a)
   if (g.op == GMRF_OP_SPDE_SQUARED) {
     switch (g.bc) {
@@ -511,7 +514,10 @@ int stencil_blocks_per_vector(const Grid& g) {
     const int t = stencil3d_tma_eligible(g, false) ? stencil3d_tma_items_per_vector(g) : 0;
     return r > t ? r : t;
   }
-  return ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+  int r = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+  for (int fp64 = 0; fp64 < 2; ++fp64)
+    if (stencil2d_strip_eligible(g, fp64 != 0)) r = std::max(r, stencil2d_strip_blocks_per_vector(g, fp64 != 0));
+  return r;
 }
 
 cudaError_t launch_stencil_step(const Grid& g, bool fp64, const void* kappa2, double kappa2_const,

@@ -39,4 +39,12 @@ bool stencil3d_tma_pointers_ok(const void* win, const void* wout, const float* k
 // step = true: fused Lanczos step on a.W0/W1/V; false: a.Wout = Q a.Win.
 cudaError_t launch_stencil3d_tma(const Grid& g, const StencilArgs<float>& a, int nvec, bool step, cudaStream_t s);
 
+// stencil2d_strip.cu: the 2-D step streamed down strips of rows, for grids
+// with nx a multiple of 128 (FP32) / 64 (FP64) and at least 65536 cells.
+bool stencil2d_strip_eligible(const Grid& g, bool fp64);
+int stencil2d_strip_blocks_per_vector(const Grid& g, bool fp64);
+bool stencil2d_strip_pointers_ok(const void* win, const void* wout, const float* kappa2);
+template <typename T>
+cudaError_t launch_stencil2d_strip(const Grid& g, const StencilArgs<T>& a, int nvec, bool step, cudaStream_t s);
+
 }  // namespace gmrf

@@ -60,7 +60,12 @@ STENCIL_CASES = [((17, 23), "periodic", "shifted_laplacian"), ((17, 23), "neuman
                  ((9, 40, 35), "dirichlet", "shifted_laplacian"), ((3, 2, 70), "periodic", "shifted_laplacian"),
                  ((4, 9, 128), "dirichlet", "shifted_laplacian"), ((5, 6, 256), "periodic", "shifted_laplacian"),
                  ((3, 17, 132), "neumann", "shifted_laplacian"), ((19, 3, 64), "periodic", "shifted_laplacian"),
-                 ((70, 12, 384), "neumann", "shifted_laplacian"), ((37, 29, 256), "dirichlet", "shifted_laplacian")]
+                 ((70, 12, 384), "neumann", "shifted_laplacian"), ((37, 29, 256), "dirichlet", "shifted_laplacian"),
+                 # 2-D grids streamed in strips of 128 (FP32) / 64 (FP64) columns: one or several strips,
+                 # row counts that leave partial slabs and partial row chunks
+                 ((513, 128), "periodic", "shifted_laplacian"), ((256, 512), "neumann", "shifted_laplacian"),
+                 ((1030, 128), "dirichlet", "shifted_laplacian"), ((256, 256), "periodic", "spde_squared"),
+                 ((300, 256), "neumann", "spde_squared"), ((260, 384), "dirichlet", "spde_squared")]
 
 
 @pytest.mark.parametrize("shape,bc,op", STENCIL_CASES)
@@ -151,3 +156,33 @@ def test_preconditioned_operator(g, shape, bc, kind, op, precision):
     for s in range(2):
         ref = A(V[s].astype(np.float64))
         assert _rel(Y[s], ref) <= (1e-12 if precision == "fp64" else 3e-6)
+
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_stencil_strip_plus_diag_and_constant_kappa(g, bc, precision):
+    # the streamed 2-D kernel on Q = tau((kc + L)^2 + D) and on a constant-kappa^2
+    # squared operator (the coefficient taken in the problem's precision)
+    shape = (264, 256)
+    n = 264 * 256
+    d = inputs.kappa2_uniform_field(shape, seed=6, lo=0.2, hi=2.0)
+    dt = np.float64 if precision == "fp64" else np.float32
+    V = inputs.gaussian_vectors(2, n, seed=7, dtype=dt)
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    Q = stencil.precision_matrix(shape, bc, "spde_plus_diag", d.astype(np.float64), 1.3, kappa2_prior=0.37)
+    with g.Problem(shape, bc, "spde_plus_diag", kappa2=_dev(d), kappa2_const=0.37, tau=1.3,
+                   precision=precision) as p:
+        y = torch.empty(2 * n, dtype=torch.from_numpy(V).dtype, device="cuda")
+        p.apply(0, _dev(V), y, nvec=2)
+        Y = y.cpu().numpy().reshape(2, n)
+    for s_ in range(2):
+        assert _rel(Y[s_], Q @ V[s_].astype(np.float64)) <= tol
+    kc = 0.1234567890123
+    Q2 = stencil.precision_matrix(shape, bc, "spde_squared", kc, 0.9)
+    with g.Problem(shape, bc, "spde_squared", kappa2_const=kc, tau=0.9, precision=precision) as p:
+        y = torch.empty(2 * n, dtype=torch.from_numpy(V).dtype, device="cuda")
+        p.apply(0, _dev(V), y, nvec=2)
+        Y = y.cpu().numpy().reshape(2, n)
+    for s_ in range(2):
+        assert _rel(Y[s_], Q2 @ V[s_].astype(np.float64)) <= tol

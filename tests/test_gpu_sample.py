@@ -320,3 +320,33 @@ def test_edge_cases(g):
     k2[3, 4] = -1.0
     with pytest.raises(g.GmrfError):
         g.Problem(shape, "neumann", "shifted_laplacian", kappa2=k2)
+
+
+
+@pytest.mark.parametrize("shape,bc,op", [((256, 256), "periodic", "shifted_laplacian"),
+                                         ((300, 256), "dirichlet", "shifted_laplacian"),
+                                         ((256, 384), "neumann", "spde_squared")])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_strip_kernel_samples_vs_oracle(g, shape, bc, op, precision):
+    # the streamed 2-D step (grids of whole 128 / 64-column strips): samples
+    # against the oracle's Algorithm 1 with full reorthogonalisation run to
+    # 1e-12, and three vectors in one batch equal to each alone (bitwise)
+    n = int(np.prod(shape))
+    k2 = inputs.kappa2_uniform_field(shape, seed=3, lo=0.5 if op == "spde_squared" else 0.05, hi=1.0)
+    Q = stencil.precision_matrix(shape, bc, op, k2.astype(np.float64), 1.0)
+    dt = np.float64 if precision == "fp64" else np.float32
+    Z = inputs.gaussian_vectors(3, n, seed=4, dtype=dt)
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    with g.Problem(shape, bc, op, kappa2=_dev(k2), precision=precision) as p:
+        x = torch.empty(3 * n, dtype=torch.from_numpy(Z).dtype, device="cuda")
+        rc, info = p.sample(x, nsamples=3, tol=tol, m_max=3000, z=_dev(Z))
+        assert rc == g.OK
+        X = x.cpu().numpy().reshape(3, n)
+        for s in (0, 2):
+            x1 = torch.empty(n, dtype=torch.from_numpy(Z).dtype, device="cuda")
+            rc1, i1 = p.sample(x1, nsamples=1, tol=tol, m_max=3000, z=_dev(Z[s]))
+            assert rc1 == g.OK and i1[0].m_used == info[s].m_used
+            assert np.array_equal(x1.cpu().numpy(), X[s])
+    xe, m, est, st = olz.adaptive_sample(lambda v: Q @ v, Z[0].astype(np.float64), 1e-12, 3000, reorth=True)
+    assert st == "ok"
+    assert _rel(X[0], xe) <= (1e-9 if precision == "fp64" else 2e-6)
