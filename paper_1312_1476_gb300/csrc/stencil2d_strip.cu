@@ -4,9 +4,10 @@
 // A block owns one strip of BX = 32 VX columns (VX = 16 bytes / element: 4
 // floats or 2 doubles per lane) and a chunk of rows of one vector, and marches
 // down the rows in slabs of 8 (one row per warp).  Every input row of the
-// strip (q_{j-1}, v_{j-1}, kappa^2) is read once with 16-byte loads into
-// rolling shared-memory rings of 32 rows; v_j is formed as the row is stored,
-// with a 16-byte x halo on either side.  The squared operators keep a ring of
+// strip (q_{j-1}, v_{j-1}, kappa^2) is read once, by 16-byte asynchronous
+// copies (cp.async) issued two slabs ahead into rolling shared-memory rings
+// of 32 rows with a 16-byte x halo on either side; v_j is formed in place of
+// q_{j-1} once a slab's copies have landed.  The squared operators keep a ring of
 // g = B v as well:
 //   shifted   q = B v                  (5-point, needs v rows y-1 .. y+1)
 //   squared   q = B g,  g = B v        (13-point, v rows y-2 .. y+2)
@@ -29,12 +30,11 @@
 namespace gmrf {
 namespace {
 
-// ring rows: a slab reads v rows y0 - 2 .. y0 + 9 and g rows y0 - 1 .. y0 + 8;
-// the next one writes v rows y0 + 10 .. y0 + 17 and g rows y0 + 9 .. y0 + 16:
-// spans of 20 and 18 rows, so 20 slots would keep them apart without a
-// barrier; 32 make the slot a mask (the block's shared memory stays below
-// what its registers allow per SM)
+// ring rows: a slab reads rows y0 - 2 .. y0 + 9 while the copies of the next
+// two slabs (rows up to y0 + 25) are in flight: a span of 28 rows, so copies
+// issued during a slab never land in a slot that is read
 constexpr int SR = 32;
+constexpr int DEPTH = 2;     // slabs copied ahead
 constexpr int SNT = 256;     // threads: 8 warps, one row each per slab
 
 template <typename T>
@@ -60,16 +60,19 @@ __device__ __forceinline__ void st16(T* p, const T (&o)[VX]) {
   else *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
 }
 // VX floats of kappa^2 (16 bytes for FP32, 8 for FP64)
-template <int VX>
-__device__ __forceinline__ void ldk(const float* p, float (&o)[VX]) {
-  if constexpr (VX == 4) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  } else {
-    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-    o[0] = v.x; o[1] = v.y;
-  }
+// asynchronous global -> shared copies; valid = false fills zeros and reads nothing
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? BYTES : 0;
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // VX floats of a shared-memory ring row (16-byte aligned for FP32, 8 for FP64)
 template <int VX>
@@ -88,12 +91,13 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
   constexpr int VX = strip_vx<T>(), BX = strip_bx<T>(), PW = BX + 2 * VX;
   constexpr bool SQ = OP != GMRF_OP_SHIFTED_LAPLACIAN;
   constexpr int H = SQ ? 2 : 1;
-  // dynamic shared memory (strip_smem_bytes): vr | gr (squared) | vpr (step) | kr
+  // dynamic shared memory (strip_smem_bytes): vr | gr (squared) | vpr (step) | kr;
+  // vr holds q_{j-1} as copied, then v_j; vpr v_{j-1} with the halo columns
   extern __shared__ __align__(16) unsigned char smraw[];
   T* vr = reinterpret_cast<T*>(smraw);
   T* gr = vr + SR * PW;
   T* vpr = gr + (SQ ? SR * PW : 0);
-  float* kr = reinterpret_cast<float*>(vpr + (STEP ? SR * BX : 0));
+  float* kr = reinterpret_cast<float*>(vpr + (STEP ? SR * PW : 0));
   __shared__ Dots<T> red[SNT / 32];
   __shared__ int s_int[4];
   __shared__ float s_flt[4];
@@ -130,46 +134,36 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
   const T kc = a.kappa2_const;
 
   // Row y of the strip (any y >= -2; outside the grid: wrapped or zero):
-  // fetch() issues the lane's loads into registers (part 0: its interior
-  // vector; lanes 0 / 1 also part 1: the left / right halo vector), put()
-  // forms v_j and writes the rings.  A slab's rows are fetched before the
-  // previous slab is computed, so their loads are in flight meanwhile.
-  struct Raw {
-    T v[2][VX], vp[2][VX];
-    float k[2][VX];
-  };
-  auto fetch = [&](int y, Raw& r) {
+  // copy_row() issues the lane's asynchronous copies (its interior vector;
+  // lanes 0 / 1 also the left / right halo vector), form_row() turns the
+  // landed q_{j-1} into v_j in place.
+  auto copy_row = [&](int y) {
     int gy = y;
     bool rin = gy >= 0 && gy < ny;
     if (!rin && BC == GMRF_BC_PERIODIC) {
       gy = gy < 0 ? gy + ny : gy - ny;
       rin = true;
     }
-    const size_t row0 = (size_t)gy * nx;
+    const size_t row0 = (size_t)(rin ? gy : 0) * nx;
+    const int sl = ring(y);
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
-#pragma unroll
-      for (int e = 0; e < VX; ++e) {
-        r.v[part][e] = 0;
-        r.vp[part][e] = 0;
-        r.k[part][e] = (float)kc;
-      }
       if (part == 1 && lane >= 2) continue;
       int xx = part == 0 ? x0 + VX * lane : (lane == 0 ? x0 - VX : x0 + BX);
+      const int col = part == 0 ? VX + VX * lane : (lane == 0 ? 0 : VX + BX);
       bool in = rin && xx >= 0 && xx < nx;
       if (rin && !in && BC == GMRF_BC_PERIODIC) {
         xx = xx < 0 ? xx + nx : xx - nx;
         in = true;
       }
-      if (in) {
-        const size_t i = row0 + xx;
-        ld16<T, VX>(Win + i, r.v[part]);
-        if (STEP && j > 0) ld16<T, VX>(Vp + i, r.vp[part]);
-        if (kfield) ldk<VX>(a.kappa2 + i, r.k[part]);
-      }
+      const size_t i = row0 + (in ? xx : 0);
+      cp_async<16>(vr + sl * PW + col, Win + i, in);
+      if (STEP && j > 0) cp_async<16>(vpr + sl * PW + col, Vp + i, in);
+      if (kfield) cp_async<4 * VX>(kr + sl * PW + col, a.kappa2 + i, in);
     }
   };
-  auto put = [&](int y, const Raw& r) {
+  auto form_row = [&](int y) {
+    if (!STEP) return;
     const int sl = ring(y);
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
@@ -178,16 +172,17 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
       // the same expression for interior and halo cells: a halo cell is another
       // strip's interior cell and must get the same v_j bitwise
       T v[VX];
+      ld16<T, VX>(vr + sl * PW + col, v);
+      if (j > 0) {
+        T vp[VX];
+        ld16<T, VX>(vpr + sl * PW + col, vp);
 #pragma unroll
-      for (int e = 0; e < VX; ++e) {
-        T t = r.v[part][e];
-        if (STEP) t = j > 0 ? (t - coef * r.vp[part][e]) * inv_b : t * inv_b;
-        v[e] = t;
+        for (int e = 0; e < VX; ++e) v[e] = (v[e] - coef * vp[e]) * inv_b;
+      } else {
+#pragma unroll
+        for (int e = 0; e < VX; ++e) v[e] = v[e] * inv_b;
       }
       st16<T, VX>(vr + sl * PW + col, v);
-#pragma unroll
-      for (int e = 0; e < VX; ++e) kr[sl * PW + col + e] = r.k[part][e];
-      if (STEP && part == 0) st16<T, VX>(vpr + sl * BX + VX * lane, r.vp[0]);
     }
   };
   // B applied at ring column c of row y (global column xg), reading array src
@@ -294,7 +289,7 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
     }
     if (STEP && j > 0) {
       T vp[VX];
-      ld16<T, VX>(vpr + sl * BX + VX * lane, vp);
+      ld16<T, VX>(vpr + sl * PW + c0, vp);
 #pragma unroll
       for (int e = 0; e < VX; ++e) q[e] -= bprev * vp[e];
     }
@@ -315,16 +310,25 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
     }
   };
 
-  Raw raw;
-  if (w < 2 * H) {  // the rows above the chunk's first slab
-    fetch(ya - H + w, raw);
-    put(ya - H + w, raw);
+  // prologue: the rows above the chunk's first slab, then DEPTH slabs of copies
+  if (w < 2 * H) copy_row(ya - H + w);
+#pragma unroll
+  for (int k = 0; k < DEPTH; ++k) {
+    const int y = ya + 8 * k + H + w;
+    if (y < yb + H) copy_row(y);
+    cp_async_commit();
   }
-  if (ya + H + w < yb + H) fetch(ya + H + w, raw);
   for (int y0 = ya; y0 < yb; y0 += 8) {
-    if (y0 + H + w < yb + H) put(y0 + H + w, raw);
+    cp_async_wait<DEPTH - 1>();  // this thread's copies of slab y0 have landed
     __syncthreads();
-    if (y0 + 8 + H + w < yb + H) fetch(y0 + 8 + H + w, raw);  // the next slab's rows, in flight meanwhile
+    if (y0 == ya && w < 2 * H) form_row(ya - H + w);
+    if (y0 + H + w < yb + H) form_row(y0 + H + w);
+    __syncthreads();
+    {
+      const int y = y0 + 8 * DEPTH + H + w;  // the slab DEPTH ahead, into slots no slab in flight reads
+      if (y < yb + H) copy_row(y);
+      cp_async_commit();
+    }
     if (SQ) {
       const int g0 = y0 == ya ? ya - 1 : y0 + 1;
       const int g1 = min(y0 + 8, yb);
@@ -335,10 +339,8 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
       const int y = y0 + w;
       if (y < yb) q_row(y);
     }
-    // no barrier here: with 32 ring rows the next slab's rows (y0 + 8 + H ..)
-    // and g rows (y0 + 9 ..) land in slots of rows this slab no longer reads;
-    // the next slab's first barrier orders the rest
   }
+  cp_async_wait<0>();
   if (!STEP) return;
   d = block_reduce(d, red);
   const int nblk = gridDim.x * gridDim.y;
@@ -351,7 +353,7 @@ template <typename T, int OP, bool STEP>
 constexpr size_t strip_smem_bytes() {
   constexpr int VX = strip_vx<T>(), BX = strip_bx<T>(), PW = BX + 2 * VX;
   return (size_t)SR * PW * sizeof(T) * (OP != GMRF_OP_SHIFTED_LAPLACIAN ? 2 : 1) +
-         (STEP ? (size_t)SR * BX * sizeof(T) : 0) + (size_t)SR * PW * sizeof(float);
+         (STEP ? (size_t)SR * PW * sizeof(T) : 0) + (size_t)SR * PW * sizeof(float);
 }
 
 template <typename T>
