@@ -474,6 +474,31 @@ def measure_variants(args, gmrf, torch, flush, peak):
             "samples_per_s": ns * 1e3 / mst, "ms_per_call": mst, "status": rct,
             "basis_bytes_per_vector": {"stored_fp32": 4 * n * (m3 + 1), "two_pass": 4 * n * 2 + 8 * n},
             "bitwise_equal_to_stored_basis": bool(torch.equal(xb, x))}
+    # 2-D fused stencil step without a preconditioner (the streamed strip kernel), on
+    # HBM-bound batches: 40 steps per vector (tol below reach), kernel time traced
+    st2d = {}
+    for shp, op, bc, nv in (((1024, 1024), "spde_squared", "neumann", 16),
+                            ((2048, 2048), "shifted_laplacian", "dirichlet", 8)):
+        n2 = shp[0] * shp[1]
+        kk = torch.from_numpy(inputs.kappa2_gp_field(shp, seed=KAPPA_SEED, ell=64.0)).cuda()
+        with gmrf.Problem(shp, bc, op, kappa2=kk, stream=stream.cuda_stream) as p:
+            x2 = torch.empty(nv * n2, dtype=torch.float32, device="cuda")
+            p.sample(x2, nsamples=nv, tol=1e-12, m_max=40, seed=1, raise_on_error=False)
+            gmrf.trace_reset()
+            gmrf.trace_timing(True)
+            _, (rc2, inf2) = timed(lambda i: p.sample(x2, nsamples=nv, tol=1e-12, m_max=40, seed=60 + i,
+                                                      raise_on_error=False), 1)
+            gmrf.trace_timing(False)
+            sm2, sl2, stt2 = gmrf.trace_query("stencil_step")
+            vs2 = int(sum(i.m_used for i in inf2))
+            by2 = 20.0 * n2 * vs2
+            ach2 = by2 / (sm2 / 1e3) / 1e9
+            st2d["%dx%d_%s_x%d" % (shp[0], shp[1], op, nv)] = {
+                "kernel": "k_stencil2d_strip", "avg_launch_us": sm2 * 1e3 / max(stt2, 1), "launches": stt2,
+                "achieved_GBps": ach2, "peak_GBps": peak, "frac": ach2 / peak,
+                "algorithmic_bytes_per_launch": by2 / max(stt2, 1),
+                "bytes_rule": "20 n per vector-step (read q_{j-1}, v_{j-1}, kappa^2; write q_j, v_j)"}
+    out["2d_stencil_step"] = {"workload": "unpreconditioned 2-D fused step, 40 steps per vector, FP32", **st2d}
     out["cfg1_64x64_periodic_fp64"] = measure_cfg1(gmrf, torch, timed)
     if not getattr(args, "no_cpu_baseline", False):
         # the oracle beside the batched and 3-D workloads (bounded samples on the host cores)
@@ -618,8 +643,14 @@ def measure_serving(nreq=32):
     base.serve(reqs[:2], realtime=False)
     _, met = base.serve(reqs, realtime=True)
     res["fp64_one_at_a_time_rate_0.5x"] = dict(met, rate_req_per_s=0.5 * sat_rate)
+    # the same stream with a fifth of the requests turned into linear solves
+    # (Section 5.1's mean solve, 1-8 seeded right-hand sides), at 0.5x
+    reqs = serve.make_mix(nreq, rate=0.5 * sat_rate, seed=4, max_samples=8, p_logdet=0.25, p_solve=0.2)
+    srv.prepare(reqs)
+    _, met = srv.serve(reqs, realtime=True)
+    res["with_solves_rate_0.5x"] = dict(met, rate_req_per_s=0.5 * sat_rate)
     res["workload"] = ("%d requests per run; samples and log dets of 2-D SPDE (mirror M) and 3-D 7-point GMRFs of "
-                       "mixed sizes; latency = completion - arrival" % nreq)
+                       "mixed sizes (with_solves: 20%% of them linear solves); latency = completion - arrival" % nreq)
     return res
 
 

@@ -35,10 +35,10 @@ from . import inputs
 class Request:
     arrival: float
     rid: int = field(compare=False)
-    kind: str = field(compare=False)          # "sample" or "logdet"
+    kind: str = field(compare=False)          # "sample", "logdet" or "solve" (x = Q^{-1} b, Section 5.1)
     shape: tuple = field(compare=False)       # (N, N) 2-D SPDE or (N, N, N) 3-D
     tau: float = field(compare=False, default=1.0)
-    count: int = field(compare=False, default=1)   # samples or probes
+    count: int = field(compare=False, default=1)   # samples, probes or right-hand sides
     seed: int = field(compare=False, default=0)
     field_id: int = field(compare=False, default=0)
     tol: float = field(compare=False, default=1e-6)
@@ -55,14 +55,16 @@ class Result:
     end_ms: float
     m_used: list
     status: int
-    x: object = None          # device tensor [count][n] for samples
+    x: object = None          # device tensor [count][n] for samples and solves
     logdet: float = None
     std_err: float = None
 
 
 def make_mix(nreq, rate, seed=4, sizes2d=(128, 256, 512, 1024), sizes3d=(64, 96, 128), nfields=4,
-             max_samples=64, probes=(16, 64), p_logdet=0.25):
-    """A Poisson request stream (rate requests/s) of the serving mix."""
+             max_samples=64, probes=(16, 64), p_logdet=0.25, p_solve=0.0):
+    """A Poisson request stream (rate requests/s) of the serving mix; a
+    fraction p_solve are linear solves with 1 .. max_samples seeded
+    right-hand sides (the stream is the same as without solves for p_solve = 0)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
@@ -72,7 +74,8 @@ def make_mix(nreq, rate, seed=4, sizes2d=(128, 256, 512, 1024), sizes3d=(64, 96,
             shape = (int(rng.choice(sizes2d)),) * 2
         else:
             shape = (int(rng.choice(sizes3d)),) * 3
-        kind = "logdet" if rng.random() < p_logdet else "sample"
+        u = rng.random()
+        kind = "logdet" if u < p_logdet else ("solve" if u < p_logdet + p_solve else "sample")
         count = int(rng.integers(probes[0], probes[1] + 1)) if kind == "logdet" else int(rng.integers(1, max_samples + 1))
         reqs.append(Request(arrival=t, rid=i, kind=kind, shape=shape, tau=float(rng.uniform(0.5, 5.0)),
                             count=count, seed=int(rng.integers(1, 2 ** 31)), field_id=int(rng.integers(0, nfields))))
@@ -129,7 +132,7 @@ class Server:
         n = int(np.prod(req.shape))
         es = 8 if self.precision == "fp64" else 4
         m = self._m_max(req)
-        slots = m + 1 if req.kind == "sample" else 2
+        slots = 2 if req.kind == "logdet" else m + 1
         b = (slots + 4) * n * es + 2 * m * 384 * 8 + 64 * m
         if len(req.shape) == 2:
             b += 3 * n * es + 2 * req.shape[0] * es   # spectrum, g, w workspaces
@@ -166,6 +169,18 @@ class Server:
                     cc = min(c, req.count - s0)
                     rc, info = prob.sample(x[s0 * n:(s0 + cc) * n], nsamples=cc, tol=req.tol, m_max=self._m_max(req),
                                            seed=(req.seed + s0) & 0x7FFFFFFF, raise_on_error=False)
+                    res.m_used += [i.m_used for i in info]
+                    res.status = min(res.status, rc)
+                res.x = x
+            elif req.kind == "solve":
+                # seeded right-hand sides from the library's Philox stream, on the problem's stream
+                b = torch.empty(req.count * n, dtype=dt, device="cuda")
+                g.rng(0, req.count, n, req.seed, b, precision=self.precision, stream=stream.cuda_stream)
+                x = torch.empty_like(b)
+                for s0 in range(0, req.count, c):
+                    cc = min(c, req.count - s0)
+                    rc, info = prob.solve(b[s0 * n:(s0 + cc) * n], x[s0 * n:(s0 + cc) * n], nrhs=cc, tol=req.tol,
+                                          m_max=self._m_max(req), raise_on_error=False)
                     res.m_used += [i.m_used for i in info]
                     res.status = min(res.status, rc)
                 res.x = x
@@ -257,8 +272,9 @@ class Server:
         lat = np.array([r.latency_ms for r in out])
         nsamp = sum(r.count for r in out if r.kind == "sample")
         nld = sum(1 for r in out if r.kind == "logdet")
+        nsol = sum(r.count for r in out if r.kind == "solve")
         metrics = {"requests": len(out), "wall_s": wall, "samples": nsamp, "samples_per_s": nsamp / wall,
-                   "logdets": nld, "logdets_per_s": nld / wall,
+                   "logdets": nld, "logdets_per_s": nld / wall, "solves": nsol, "solves_per_s": nsol / wall,
                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                    "statuses": sorted(set(r.status for r in out))}
         return out, metrics

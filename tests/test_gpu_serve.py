@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 
 def _mix():
     reqs = serve.make_mix(12, rate=1e6, seed=9, sizes2d=(128, 256), sizes3d=(32, 48), nfields=2,
-                          max_samples=6, probes=(4, 8), p_logdet=0.3)
+                          max_samples=6, probes=(4, 8), p_logdet=0.3, p_solve=0.3)
     for r in reqs:
         r.arrival = 0.0
     return reqs
@@ -30,12 +30,15 @@ def test_alone_equals_mix(tune):
     mixed, metrics = srv.serve(reqs, realtime=False)
     assert metrics["requests"] == len(reqs)
     assert all(r.status in (0, -3) for r in mixed)
-    for target in (0, 5, 11):
+    kinds = {r.kind for r in reqs}
+    assert kinds == {"sample", "logdet", "solve"}
+    targets = sorted({0, 5, 11} | {min(i for i, r in enumerate(reqs) if r.kind == k) for k in kinds})
+    for target in targets:
         one = serve.Server(max_inflight=1)
         one.tuning = dict(srv.tuning)
         alone, _ = one.serve([reqs[target]], realtime=False)
         a, b = alone[0], mixed[target]
-        if a.kind == "sample":
+        if a.kind in ("sample", "solve"):
             assert torch.equal(a.x, b.x)
         else:
             assert a.logdet == b.logdet and a.std_err == b.std_err
