@@ -238,6 +238,35 @@ typedef struct {
  * A zero right-hand side gives x = 0 with status GMRF_OK and m_used = 0. */
 int gmrf_solve(gmrf_problem* p, const gmrf_solve_opts* opts, const void* b, void* x, gmrf_result_info* info);
 
+/* Asynchronous calls.  gmrf_submit_sample / _logdet / _solve queue the call
+ * with the same arguments as the synchronous function and return at once with
+ * a ticket (> 0); a host worker thread owned by the library (one per problem,
+ * started at its first submit, on the device current at that submit) runs the
+ * problem's submitted calls in submission order, each exactly as the
+ * synchronous call, on the problem's stream.  The option struct is copied at
+ * submit; every buffer it or the call names (x_out, info, z_in, probes_in, b,
+ * logdet, std_err, q_out) belongs to the caller and must stay valid and
+ * untouched until the ticket has completed.  While calls are outstanding the
+ * problem must not be used by synchronous calls.  Calls on different problems
+ * run concurrently.  gmrf_destroy runs what was submitted, then frees.
+ * Submit returns GMRF_ERR_INVALID for NULL p, opts or ticket (other argument
+ * errors are the completed call's result).
+ *   gmrf_poll: *done = 1 once the call has completed, and then *result (may be
+ *   NULL) = its return code; non-blocking.
+ *   gmrf_wait: blocks until the call has completed; *result (may be NULL) =
+ *   its return code.
+ * Both return GMRF_ERR_INVALID for a ticket this problem did not issue.
+ * The paper's method has no counterpart: this is the call form a serving layer
+ * needs to keep several problems' iterations in flight from one host thread. */
+int gmrf_submit_sample(gmrf_problem* p, const gmrf_sample_opts* opts, void* x_out, gmrf_result_info* info,
+                       int64_t* ticket);
+int gmrf_submit_logdet(gmrf_problem* p, const gmrf_logdet_opts* opts, double* logdet, double* std_err,
+                       double* q_out, gmrf_result_info* info, int64_t* ticket);
+int gmrf_submit_solve(gmrf_problem* p, const gmrf_solve_opts* opts, const void* b, void* x, gmrf_result_info* info,
+                      int64_t* ticket);
+int gmrf_poll(gmrf_problem* p, int64_t ticket, int32_t* done, int32_t* result);
+int gmrf_wait(gmrf_problem* p, int64_t ticket, int32_t* result);
+
 /* Matrix-free operator applies on nvec vectors of the problem's precision
  * (Section 2's "routine that computes the matrix-vector product"), for
  * testing and for callers composing their own solvers:

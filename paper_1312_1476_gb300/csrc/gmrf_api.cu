@@ -507,6 +507,7 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
 
 void gmrf_destroy(gmrf_problem* p) {
   if (!p) return;
+  async_shutdown(p);  // submitted calls finish first
   if (p->ws) cudaStreamSynchronize(p->ws);
   p->graph.reset();
   DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,

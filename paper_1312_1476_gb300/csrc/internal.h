@@ -102,6 +102,8 @@ constexpr int kMaxNodes = 384;
 // y stride = m_max.  scratch: >= nvec * kMaxNodes * m_max * 2 doubles.
 cudaError_t launch_tm_inv_sqrt(const LanczosBufs& b, bool fp64, TmNodes* nodes, double* scratch, double* y,
                                cudaStream_t s);
+// async.cu: runs what was submitted for p, then joins its worker (gmrf_destroy).
+void async_shutdown(const gmrf_problem* p);
 // y[s] = T_m^{-1} e_1 (linear solve), y and dwork stride = m_max (dwork: nvec * m_max doubles).
 cudaError_t launch_tm_inv(const LanczosBufs& b, double* dwork, double* y, cudaStream_t s);
 // q[s] = ||v_s||^2 e_1^T log(T_m) e_1 (Gauss quadrature, rational form).

@@ -87,6 +87,15 @@ def _load():
         "gmrf_sample_logdet": (ctypes.c_int, [P, ctypes.POINTER(GmrfSampleOpts), ctypes.POINTER(GmrfLogdetOpts), P,
                                               ctypes.POINTER(GmrfResultInfo), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(GmrfResultInfo)]),
+        "gmrf_submit_sample": (ctypes.c_int, [P, ctypes.POINTER(GmrfSampleOpts), P, ctypes.POINTER(GmrfResultInfo),
+                                              ctypes.POINTER(ctypes.c_int64)]),
+        "gmrf_submit_logdet": (ctypes.c_int, [P, ctypes.POINTER(GmrfLogdetOpts), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(GmrfResultInfo),
+                                              ctypes.POINTER(ctypes.c_int64)]),
+        "gmrf_submit_solve": (ctypes.c_int, [P, ctypes.POINTER(GmrfSolveOpts), P, P, ctypes.POINTER(GmrfResultInfo),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+        "gmrf_poll": (ctypes.c_int, [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "gmrf_wait": (ctypes.c_int, [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
         "gmrf_apply": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int64, P, P]),
         "gmrf_rng": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                     ctypes.c_uint64, P, P]),
@@ -193,6 +202,7 @@ class Problem:
         if rc != OK:
             raise GmrfError(rc, "gmrf_create")
         self._stream = stream
+        self._tickets = []  # submitted calls: their buffers live until close()
 
     @property
     def dtype(self):
@@ -200,8 +210,9 @@ class Problem:
 
     def close(self):
         if self._h:
-            _lib.gmrf_destroy(self._h)
+            _lib.gmrf_destroy(self._h)  # runs what was submitted first
             self._h = ctypes.c_void_p()
+        self._tickets = []              # their buffers may go now
 
     def __del__(self):
         try:
@@ -272,6 +283,45 @@ class Problem:
             raise GmrfError(rc, "gmrf_sample_logdet")
         return rc, sinfos, ld.value, se.value, q, linfos
 
+    # ---- asynchronous calls: return a Ticket at once (see include/gmrf.h)
+    def _track(self, t):
+        self._tickets = [x for x in self._tickets if x.rc is None] + [t]
+        return t
+
+    def submit_sample(self, out, nsamples=1, tol=1e-6, m_max=300, seed=2, z=None, check_every=16,
+                      v_storage="native"):
+        o = GmrfSampleOpts(float(tol), int(m_max), int(nsamples), int(seed) & (2 ** 64 - 1),
+                           _ptr(z) if z is not None else None, int(check_every), VSTORE[v_storage])
+        info = (GmrfResultInfo * int(nsamples))()
+        t = ctypes.c_int64()
+        rc = _lib.gmrf_submit_sample(self._h, ctypes.byref(o), _ptr(out), info, ctypes.byref(t))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_submit_sample")
+        return self._track(Ticket(self, t.value, "sample", info, keep=(out, z)))
+
+    def submit_logdet(self, nprobes=16, tol=1e-6, m_max=300, seed=3, probes=None, check_every=16, colour_dist=0):
+        o = GmrfLogdetOpts(float(tol), int(m_max), int(nprobes), int(seed) & (2 ** 64 - 1),
+                           _ptr(probes) if probes is not None else None, int(check_every), int(colour_dist))
+        nq = int(nprobes) * (int(colour_dist) + 1) ** len(self.shape)
+        info = (GmrfResultInfo * nq)()
+        q = np.zeros(nq, dtype=np.float64)
+        ld, se = ctypes.c_double(), ctypes.c_double()
+        t = ctypes.c_int64()
+        rc = _lib.gmrf_submit_logdet(self._h, ctypes.byref(o), ctypes.byref(ld), ctypes.byref(se),
+                                     ctypes.c_void_p(q.ctypes.data), info, ctypes.byref(t))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_submit_logdet")
+        return self._track(Ticket(self, t.value, "logdet", info, keep=(probes, q, ld, se), logdet=(ld, se, q)))
+
+    def submit_solve(self, b, out, nrhs=1, tol=1e-6, m_max=300, check_every=16):
+        o = GmrfSolveOpts(float(tol), int(m_max), int(nrhs), int(check_every), 0)
+        info = (GmrfResultInfo * int(nrhs))()
+        t = ctypes.c_int64()
+        rc = _lib.gmrf_submit_solve(self._h, ctypes.byref(o), _ptr(b), _ptr(out), info, ctypes.byref(t))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_submit_solve")
+        return self._track(Ticket(self, t.value, "solve", info, keep=(b, out)))
+
     def solve(self, b, out, nrhs=1, tol=1e-6, m_max=300, check_every=16, raise_on_error=True):
         """x = Q^{-1} b into ``out`` ([nrhs][n], host or device) by the Lanczos
         form of (preconditioned) conjugate gradients; returns (return code,
@@ -313,6 +363,41 @@ class Problem:
         rc = _lib.gmrf_apply(self._h, int(which), int(nvec), _ptr(v), _ptr(y))
         if rc != OK:
             raise GmrfError(rc, "gmrf_apply")
+
+
+class Ticket:
+    """An asynchronous call in flight: holds its buffers until it completes."""
+
+    def __init__(self, prob, ticket, kind, info, keep=(), logdet=None):
+        self.prob, self.ticket, self.kind, self._info, self._keep, self._ld = prob, ticket, kind, info, keep, logdet
+        self.rc = None
+
+    def poll(self):
+        """True once the call has completed (its return code is then in .rc)."""
+        if self.rc is not None:
+            return True
+        d, r = ctypes.c_int32(), ctypes.c_int32()
+        rc = _lib.gmrf_poll(self.prob._h, self.ticket, ctypes.byref(d), ctypes.byref(r))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_poll")
+        if d.value:
+            self.rc = r.value
+        return bool(d.value)
+
+    def wait(self):
+        """Blocks until completion; returns (return code, infos) or, for a log
+        det, (logdet, std_err, q, infos, return code) as the synchronous calls."""
+        if self.rc is None:
+            r = ctypes.c_int32()
+            rc = _lib.gmrf_wait(self.prob._h, self.ticket, ctypes.byref(r))
+            if rc != OK:
+                raise GmrfError(rc, "gmrf_wait")
+            self.rc = r.value
+        infos = [SampleInfo(i.m_used, i.status, i.err_est) for i in self._info]
+        if self.kind == "logdet":
+            ld, se, q = self._ld
+            return ld.value, se.value, q, infos, self.rc
+        return self.rc, infos
 
 
 def rng(kind, nvec, n, seed, out, precision="fp32", stream=None):

@@ -11,6 +11,8 @@ Cases:
   headline_1024  1024 x 1024 SPDE, zero-Neumann, mirror preconditioner, FP32
   batched_512    512 x 512 SPDE, mirror preconditioner, FP32, N vectors per launch
   3d_256         256^3 Dirichlet 7-point, kappa^2 i.i.d. U[0.01, 1], FP32
+  stencil2d_1024 1024 x 1024 SPDE, zero-Neumann, no preconditioner, FP32 (the
+                 streamed 2-D step), N vectors per launch
 """
 from __future__ import annotations
 
@@ -30,6 +32,10 @@ def run(case: str, nsamples: int, steps: int) -> dict:
         shape = (512, 512)
         k2 = torch.from_numpy(inputs.kappa2_gp_field(shape, seed=1, ell=64.0)).cuda()
         prob = gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond="mirror")
+    elif case == "stencil2d_1024":
+        shape = (1024, 1024)
+        k2 = torch.from_numpy(inputs.kappa2_gp_field(shape, seed=1, ell=64.0)).cuda()
+        prob = gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2)
     elif case == "3d_256":
         shape = (256, 256, 256)
         k2 = torch.from_numpy(inputs.kappa2_uniform_field(shape, seed=1)).cuda()
@@ -49,7 +55,7 @@ def run(case: str, nsamples: int, steps: int) -> dict:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("case", choices=["headline_1024", "batched_512", "3d_256"])
+    ap.add_argument("case", choices=["headline_1024", "batched_512", "3d_256", "stencil2d_1024"])
     ap.add_argument("--nsamples", type=int, default=1)
     ap.add_argument("--steps", type=int, default=24)
     a = ap.parse_args(argv)

@@ -350,3 +350,53 @@ def test_strip_kernel_samples_vs_oracle(g, shape, bc, op, precision):
     xe, m, est, st = olz.adaptive_sample(lambda v: Q @ v, Z[0].astype(np.float64), 1e-12, 3000, reorth=True)
     assert st == "ok"
     assert _rel(X[0], xe) <= (1e-9 if precision == "fp64" else 2e-6)
+
+
+def test_async_submit_poll_wait_equal_synchronous(g):
+    # gmrf_submit_* run on a library worker per problem; two problems in flight
+    # from one host thread give bitwise the synchronous results
+    shape = (128, 128)
+    n = 128 * 128
+    k2 = inputs.kappa2_gp_field(shape, seed=1, ell=16.0)
+    b = inputs.gaussian_vectors(2, n, seed=5, dtype=np.float32)
+    p1 = g.Problem(shape, "neumann", "spde_squared", kappa2=_dev(k2), precond="mirror")
+    p2 = g.Problem((32, 32, 32), "dirichlet", "shifted_laplacian", kappa2_const=0.3)
+    try:
+        xa = torch.empty(3 * n, device="cuda")
+        sa = torch.empty(2 * n, device="cuda")
+        x3 = torch.empty(2 * 32768, device="cuda")
+        ta = p1.submit_sample(xa, nsamples=3, tol=1e-6, m_max=300, seed=7)
+        tb = p1.submit_solve(_dev(b), sa, nrhs=2, tol=1e-6, m_max=300)
+        tc = p1.submit_logdet(nprobes=4, tol=1e-6, m_max=300, seed=8)
+        td = p2.submit_sample(x3, nsamples=2, tol=1e-6, m_max=300, seed=9)
+        pending = [ta, tb, tc, td]
+        while not all(t.poll() for t in pending):
+            pass
+        rca, ia = ta.wait()
+        rcb, ib = tb.wait()
+        lda, sea, qa, ic, rcc = tc.wait()
+        rcd, idd = td.wait()
+        assert rca == rcb == rcc == rcd == g.OK
+        xs = torch.empty(3 * n, device="cuda")
+        rc, i2 = p1.sample(xs, nsamples=3, tol=1e-6, m_max=300, seed=7)
+        assert torch.equal(xs, xa) and [i.m_used for i in i2] == [i.m_used for i in ia]
+        ss = torch.empty(2 * n, device="cuda")
+        p1.solve(_dev(b), ss, nrhs=2, tol=1e-6, m_max=300)
+        assert torch.equal(ss, sa)
+        ld, se, q, _, _ = p1.logdet(nprobes=4, tol=1e-6, m_max=300, seed=8)
+        assert ld == lda and np.array_equal(q, qa)
+        x3s = torch.empty(2 * 32768, device="cuda")
+        p2.sample(x3s, nsamples=2, tol=1e-6, m_max=300, seed=9)
+        assert torch.equal(x3s, x3)
+        # an invalid option is the completed call's result; unknown tickets are rejected
+        tbad = p1.submit_sample(xa, nsamples=0)
+        assert tbad.wait()[0] == g.ERR_INVALID
+        with pytest.raises(g.GmrfError):
+            g.Ticket(p1, 10 ** 6, "sample", []).wait()
+        # destroy runs what was submitted
+        xl = torch.empty(n, device="cuda")
+        p1.submit_sample(xl, nsamples=1, tol=1e-6, m_max=300, seed=7)
+    finally:
+        p1.close()
+        p2.close()
+    assert torch.equal(xl, xa[:n])
