@@ -188,3 +188,21 @@ def test_sample_covariance(g, case):
     d = np.diag(S)
     se = np.sqrt((np.outer(d, d) + S ** 2) / N)
     assert np.max(np.abs(C - S) / se) <= 6.0
+
+
+@pytest.mark.parametrize("shape,bc,op,nv", [((1024, 1024), "neumann", "spde_squared", 16),
+                                            ((2048, 2048), "dirichlet", "shifted_laplacian", 8)])
+def test_2d_strip_apply_at_bench_size(g, shape, bc, op, nv):
+    # the streamed 2-D kernel in the bench's launch configurations (16 / 8
+    # vectors): Q v of two of the vectors against the oracle's sparse Q, whole
+    # vectors; FP32 rounding of the 5/13-point differences ~ a few u relative
+    n = shape[0] * shape[1]
+    k2 = inputs.kappa2_gp_field(shape, seed=1, ell=64.0)
+    Q = stencil.precision_matrix(shape, bc, op, k2.astype(np.float64), 1.0)
+    V = inputs.gaussian_vectors(nv, n, seed=12, dtype=np.float32)
+    with g.Problem(shape, bc, op, kappa2=_dev(k2)) as p:
+        y = torch.empty(nv * n, dtype=torch.float32, device="cuda")
+        p.apply(0, _dev(V), y, nvec=nv)
+        Y = y.view(nv, n)
+        for s in (0, nv - 1):
+            assert _rel(Y[s].cpu().numpy(), Q @ V[s].astype(np.float64)) <= 2e-6
