@@ -579,7 +579,7 @@ def measure_table1(gmrf, torch):
     prior (circulant, applied by FFT) and without preconditioning."""
     from paper_1312_1476_gb300 import inputs
     pre, un, ms_sample, pre_solve = {}, {}, {}, {}
-    for N in (16, 32, 64, 128, 256, 512, 1024, 2048):
+    for N in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096):
         mdl = inputs.lgcp_smmala_model(N)
         kw = dict(kappa2=torch.from_numpy(mdl["d"]).cuda(), kappa2_const=mdl["kappa2_prior"], tau=mdl["tau"],
                   precision="fp64")

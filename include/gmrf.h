@@ -89,7 +89,11 @@ typedef enum {
  *                mirror-extended torus, i.e. the cell-centred Neumann
  *                operator, applied by 2-D DCT-II (an FFT of the reflected
  *                grid).
- * Preconditioning needs dim == 2 and power-of-two nx, ny in [8, 4096]. */
+ * Preconditioning needs dim == 2 and power-of-two nx, ny in [8, 4096].  FP64
+ * problems with 4096-point lines are supported only where the preconditioner
+ * matches the boundary (CIRCULANT with periodic, MIRROR with Neumann: no
+ * boundary correction terms); otherwise gmrf_create returns
+ * GMRF_ERR_UNSUPPORTED. */
 typedef enum { GMRF_PREC_NONE = 0, GMRF_PREC_CIRCULANT = 1, GMRF_PREC_MIRROR = 2 } gmrf_precond;
 
 /* Vector arithmetic of the Krylov iteration.  FP32: vectors, stencil and

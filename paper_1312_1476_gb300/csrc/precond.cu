@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(256) k_prow(PArgs<R> a) {
   }
   __syncthreads();
   nl = rows[19];
-  const int LMAX = rb + 2;
+  // staged lines: the block's rows, plus the two y-partner rows when R has edge terms
+  const int LMAX = rb + (has_edge_terms<KIND>(a.bc) ? 2 : 0);
   R* B0 = (R*)smraw;
   R* B1 = B0 + (size_t)LMAX * PL;
   R* B2 = B1 + (size_t)LMAX * PL;
@@ -585,9 +586,13 @@ int col_width(const PrecondTables& t) {
   return cw;
 }
 
+bool host_has_edge_terms(const PrecondTables& t) {
+  return t.kind == GMRF_PREC_CIRCULANT ? t.bc != GMRF_BC_PERIODIC : t.bc != GMRF_BC_NEUMANN;
+}
+// must match the line count LMAX of k_prow
 template <typename R>
 size_t row_smem(const PrecondTables& t) {
-  return (size_t)4 * (t.rb + 2) * (t.nx + 2) * sizeof(R);
+  return (size_t)4 * (t.rb + (host_has_edge_terms(t) ? 2 : 0)) * (t.nx + 2) * sizeof(R);
 }
 template <typename R>
 size_t col_smem(const PrecondTables& t, int cw) {
@@ -905,12 +910,20 @@ int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar
   t.kbar2 = kbar2;
   t.bc = g.bc;
   t.fast = fast_eligible(kind, fp64, g.nx, g.ny);
-  if (fp64 && (g.nx > 2048 || g.ny > 2048)) return GMRF_ERR_UNSUPPORTED;
   int rb = (fp64 ? 2048 : 4096) / g.nx;
   if (rb < 1) rb = 1;
   if (rb > 16) rb = 16;
   if (rb > g.ny) rb = g.ny;
   t.rb = rb;
+  // the generic row and column kernels stage whole lines in shared memory
+  // (FP64 4096-point lines fit only without the y-partner rows of edge terms)
+  {
+    const size_t lim = (size_t)smem_optin() - 2048;
+    const size_t rs = fp64 ? row_smem<double>(t) : row_smem<float>(t);
+    const int cw = col_width(t);
+    const size_t cs = fp64 ? col_smem<double>(t, cw) : col_smem<float>(t, cw);
+    if (rs > lim || cs > lim) return GMRF_ERR_UNSUPPORTED;
+  }
   std::vector<double> lx64, ly64;
   const int r = fp64 ? upload_tables<double>(t, s, lx64, ly64) : upload_tables<float>(t, s, lx64, ly64);
   if (r) return GMRF_ERR_CUDA;

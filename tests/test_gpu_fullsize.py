@@ -206,3 +206,39 @@ def test_2d_strip_apply_at_bench_size(g, shape, bc, op, nv):
         Y = y.view(nv, n)
         for s in (0, nv - 1):
             assert _rel(Y[s].cpu().numpy(), Q @ V[s].astype(np.float64)) <= 2e-6
+
+
+def test_table1_4096_fp64_preconditioned(g):
+    # Table 1's largest grid: the LGCP sMMALA proposal on a 4096^2 torus in FP64
+    # at tol 1e-8, preconditioned by the prior.  The step count stays at the
+    # small-grid value, and the sample satisfies x^T Q x = z^T z, which holds
+    # for the Proposition 1 map as for Q^{-1/2} z (x = M^{-1/2} A^{-1/2} z gives
+    # x^T Q x = z^T A^{-1/2} A A^{-1/2} z); the mean solve meets its stopping rule.
+    N = 4096
+    n = N * N
+    mdl = inputs.lgcp_smmala_model(N)
+    kw = dict(kappa2=_dev(mdl["d"]), kappa2_const=mdl["kappa2_prior"], tau=mdl["tau"], precision="fp64")
+    z = inputs.gaussian_vectors(1, n, seed=2, dtype=np.float64)
+    b = inputs.lgcp_gradient(N)
+    with g.Problem((N, N), "periodic", "spde_plus_diag", precond="circulant", **kw) as p:
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        rc, info = p.sample(x, nsamples=1, tol=1e-8, m_max=200, z=_dev(z), check_every=1)
+        assert rc == g.OK and info[0].m_used <= 8
+        xs = torch.empty(n, dtype=torch.float64, device="cuda")
+        rcs, infs = p.solve(_dev(b), xs, nrhs=1, tol=1e-8, m_max=200, check_every=1)
+        assert rcs == g.OK and infs[0].m_used <= 9
+    Q = stencil.precision_matrix((N, N), "periodic", "spde_plus_diag", mdl["d"].astype(np.float64), mdl["tau"],
+                                 kappa2_prior=mdl["kappa2_prior"])
+    X = x.cpu().numpy()
+    e = float(X @ (Q @ X))
+    assert abs(e - float(z[0] @ z[0])) <= 1e-7 * float(z[0] @ z[0])
+    # the solve's stopping quantity, recomputed by the oracle: the relative residual
+    # of A u = M^{-1/2} b with u = M^{1/2} x.  Q = M + tau D exactly (M the prior),
+    # so A u = u + M^{-1/2} (tau D x) and the residual is
+    # M^{-1/2}(b - tau D x) - M^{1/2} x: spectral applies and a diagonal, without
+    # the cancellation of the 13-point stencil in Q x (its terms are ~1e12 |b| here)
+    pw = lambda v, e: precond.apply_power((N, N), "periodic", "spde_squared", mdl["kappa2_prior"], mdl["tau"], v, e)
+    XS = xs.cpu().numpy()
+    rt = pw(b - mdl["tau"] * mdl["d"].astype(np.float64).reshape(-1) * XS, -0.5) - pw(XS, 0.5)
+    r = np.linalg.norm(rt) / np.linalg.norm(pw(b, -0.5))
+    assert r <= 1.05e-8 and abs(r - infs[0].err_est) <= 1e-3 * infs[0].err_est + 1e-12
