@@ -2,6 +2,8 @@
 // Lanczos start-up (v_1 = z / ||z||), sample assembly x_m = ||z|| V_m y
 // (Algorithm 1, last step) and small elementwise helpers.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 #include <math.h>
 
 #include "internal.h"
@@ -176,16 +178,28 @@ __global__ void k_assemble(const S* __restrict__ V, int nslots, size_t n, const 
       yl[j] = (float)(yy - (double)h);
     }
     __syncthreads();
+    // x_i += vv * y_j in a compensated (sum, error) pair; the order of the terms is j = 0 .. m-1
+    auto acc = [&](float vv, int j, float& sum, float& comp) {
+      const float t = __fmaf_rn(vv, yh[j], __fmul_rn(vv, yl[j]));
+      const float s2 = __fadd_rn(sum, t);
+      comp = __fadd_rn(comp, fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t)
+                                                     : __fadd_rn(__fsub_rn(t, s2), sum));
+      sum = s2;
+    };
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+      // bfloat16 basis: half the bytes per load, so more loads in flight per
+      // thread (the same arithmetic and order per element as below)
+      for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float sum = 0.f, comp = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < m; ++j) acc(__bfloat162float(Vs[(size_t)j * n + i]), j, sum, comp);
+        xo[i] = (T)__fadd_rn(sum, comp);
+      }
+      return;
+    }
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
       float sum = 0.f, comp = 0.f;
-      for (int j = 0; j < m; ++j) {
-        const float vv = (float)to_f(Vs[(size_t)j * n + i]);
-        const float t = __fmaf_rn(vv, yh[j], __fmul_rn(vv, yl[j]));
-        const float s2 = __fadd_rn(sum, t);
-        comp = __fadd_rn(comp, fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t)
-                                                       : __fadd_rn(__fsub_rn(t, s2), sum));
-        sum = s2;
-      }
+      for (int j = 0; j < m; ++j) acc((float)to_f(Vs[(size_t)j * n + i]), j, sum, comp);
       xo[i] = (T)__fadd_rn(sum, comp);
     }
   } else {
