@@ -131,3 +131,30 @@ def solve_spectral(shape, bc, op, kappa2_const, tau, b, kappa2_prior=None):
     """x = Q^{-1} b for constant kappa^2 through the closed-form eigenvalues."""
     mu = stencil.operator_eigenvalues(shape, bc, op, kappa2_const, tau, kappa2_prior=kappa2_prior)
     return spectral_apply(shape, bc, 1.0 / mu, b)
+
+
+# ----------------------------------------------------- a second route to Q^{-1/2} z
+def sample_stieltjes(Q, z, lam_lo, lam_hi, h=0.35, pad=30.0):
+    """x = Q^{-1/2} z from the Stieltjes integral of the inverse square root,
+    Q^{-1/2} = (2/pi) int_0^inf (Q + s^2 I)^{-1} ds = (2/pi) int_R e^u (Q + e^{2u} I)^{-1} du,
+    by the trapezoid rule in u with step h on [log(lam_lo)/2 - pad, log(lam_hi)/2 + pad],
+    one sparse LU solve per node.  [lam_lo, lam_hi] must contain the spectrum
+    of Q (bounds suffice).  For an eigenvalue lam the integrand is
+    sech(u - log(lam)/2) / (2 sqrt(lam)): the discretisation error is about
+    4 exp(-pi^2 / h) relative and the truncation error about (2/pi) exp(-pad).
+    A route independent of Algorithm 1, for variable-kappa^2 grids where no
+    closed form exists."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    Qc = sp.csc_matrix(Q)
+    n = Qc.shape[0]
+    I = sp.identity(n, format="csc")
+    z = np.asarray(z, dtype=np.float64).reshape(-1)
+    lo = 0.5 * np.log(lam_lo) - pad
+    hi = 0.5 * np.log(lam_hi) + pad
+    nodes = int(np.ceil((hi - lo) / h))
+    x = np.zeros(n)
+    for k in range(nodes + 1):
+        u = lo + k * h
+        x += np.exp(u) * spla.splu(Qc + np.exp(2.0 * u) * I).solve(z)
+    return (2.0 / np.pi) * h * x

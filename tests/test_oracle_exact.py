@@ -99,3 +99,18 @@ def test_solve_routes(shape, bc, op):
     xv = exact.solve_sparse(Qv, B[:1])[0]
     assert np.linalg.norm(Qv @ xv - B[0]) <= 1e-11 * np.linalg.norm(B[0])
     assert abs(xv @ (Qv @ xv) - xv @ B[0]) <= 1e-10 * abs(xv @ B[0])
+
+
+def test_stieltjes_route_matches_dense():
+    # the quadrature route against dense eigh on a small variable-kappa^2 grid,
+    # with loose spectral bounds (Gershgorin above, min kappa^2 below)
+    rng = np.random.default_rng(8)
+    shape = (9, 11)
+    k2 = rng.uniform(0.05, 1.0, size=shape)
+    Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2, tau=1.3)
+    z = inputs.gaussian_vectors(1, 99, seed=3, dtype=np.float64)[0]
+    lo = 1.3 * k2.min() ** 2
+    hi = 1.3 * (k2.max() + 8.0) ** 2
+    x = exact.sample_stieltjes(Q, z, lo, hi)
+    xe = exact.sample_dense(Q, z)[0]
+    assert np.linalg.norm(x - xe) <= 1e-10 * np.linalg.norm(xe)

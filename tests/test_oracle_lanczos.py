@@ -242,3 +242,19 @@ def test_cg_reaches_the_sparse_solve_with_the_stopping_rule():
         assert st == "ok"
         assert np.linalg.norm(b - Q @ x) <= tol * np.linalg.norm(b) * (1 + 1e-6)
         assert np.linalg.norm(x - xe) <= (lam[-1] / lam[0]) * tol * np.linalg.norm(xe) * 1.01
+
+
+def test_lanczos_reference_against_the_stieltjes_route_at_mid_size():
+    # The large-grid reference of the GPU parity tests (Algorithm 1 in FP64 with
+    # full reorthogonalisation, run to 1e-12) against an independent route, the
+    # Stieltjes-integral quadrature with sparse LU solves, on a 64 x 96
+    # variable-kappa^2 grid (no closed form, too large for a dense check)
+    shape = (64, 96)
+    n = 64 * 96
+    k2 = inputs.kappa2_uniform_field(shape, seed=1, lo=0.3, hi=1.0)  # kappa(Q) ~ 770: a few hundred steps
+    Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2.astype(np.float64), 1.0)
+    z = inputs.gaussian_vectors(1, n, seed=2, dtype=np.float64)[0]
+    x_l, m, est, st = lanczos.adaptive_sample(lambda v: Q @ v, z, 1e-12, 3000, reorth=True)
+    assert st == "ok"
+    x_q = exact.sample_stieltjes(Q, z, float(k2.min()) ** 2, (float(k2.max()) + 8.0) ** 2)
+    assert np.linalg.norm(x_l - x_q) <= 1e-9 * np.linalg.norm(x_q)
