@@ -119,8 +119,11 @@ __global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>*
   const T* z = W + (size_t)s * n;
   Dots<T> d;
   d.zero();
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    d.add(z[i], (T)0);
+  // only ||z||^2 (the s3 slot) is used: one compensated sum per element
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 4) Dots<float>::dot2(d.s3, z[i], z[i]);
+    else d.s3 = fma(z[i], z[i], d.s3);
+  }
   d = block_reduce(d, red);
   const int nblk = gridDim.x;
   if (threadIdx.x == 0) partials[(size_t)s * nblk + blockIdx.x] = d;
