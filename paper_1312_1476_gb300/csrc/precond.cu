@@ -652,6 +652,8 @@ fast::Args fast_args(const PrecondTables& t, const Grid& g, const void* kappa2, 
   a.twy = (const float2*)t.twy;
   a.dctx = (const float2*)t.dctx;
   a.dcty = (const float2*)t.dcty;
+  a.pairx = (const float4*)t.pairx;
+  a.pairy = (const float4*)t.pairy;
   a.T = (float*)t.S;
   a.tstride = (size_t)t.ny * (t.nx + 2);
   a.G = (float*)t.G;
@@ -886,6 +888,40 @@ int upload_tables(PrecondTables& t, cudaStream_t s, std::vector<double>& lx64, s
       up(&t.twx, twx.data(), twx.size() * sizeof(C)) || up(&t.twy, twy.data(), twy.size() * sizeof(C)) ||
       up(&t.dctx, dx.data(), dx.size() * sizeof(C)) || up(&t.dcty, dy.data(), dy.size() * sizeof(C)))
     return -1;
+  // pair planes of the FP32 mirror passes (the same float values, regrouped)
+  auto planes = [&](int N, const std::vector<C>& tw_, const std::vector<C>& d_, const std::vector<R>* lam_,
+                    std::vector<R>& pr) {
+    const int L = N / 2, HP = L / 2, np = lam_ ? 4 : 3;
+    pr.assign((size_t)np * (HP + 1) * 4, (R)0);
+    for (int k = 0; k <= HP; ++k) {
+      const int kp = L - k;
+      // entry q of pair k at float (q / 4) * 4 (HP + 1) + 4 k + q % 4
+      auto at = [&](int q) -> R& { return pr[(size_t)(q / 4) * 4 * (HP + 1) + (size_t)4 * k + q % 4]; };
+      const C v[6] = {tw_[k], tw_[kp], d_[k], d_[N - k], d_[kp], d_[N - kp]};
+      for (int q = 0; q < 6; ++q) {
+        at(2 * q) = v[q].x;
+        at(2 * q + 1) = v[q].y;
+      }
+      if (!lam_) continue;
+      const std::vector<R>& lm = *lam_;
+      if (k == 0) {
+        at(12) = lm[0];
+        at(13) = lm[L];
+      } else {
+        at(12) = lm[k];
+        at(13) = lm[N - k];
+        at(14) = lm[kp];
+        at(15) = lm[N - kp];
+      }
+    }
+  };
+  std::vector<R> prx, pry;
+  if (sizeof(R) == 4 && t.kind == GMRF_PREC_MIRROR && t.nx >= 4 && t.ny >= 4) {
+    planes(t.nx, twx, dx, nullptr, prx);
+    planes(t.ny, twy, dy, &lyr, pry);
+    if (up(&t.pairx, prx.data(), prx.size() * sizeof(R)) || up(&t.pairy, pry.data(), pry.size() * sizeof(R)))
+      return -1;
+  }
   // host vectors must outlive the async copies
   return cudaStreamSynchronize(s) == cudaSuccess ? 0 : -1;
 }
@@ -955,7 +991,7 @@ int precond_build(PrecondTables& t, const Grid& g, int kind, int op, double kbar
 }
 
 void precond_free(PrecondTables& t, cudaStream_t s) {
-  void* ps[] = {t.lamx, t.lamy, t.twx, t.twy, t.dctx, t.dcty, t.S, t.G, t.Wg};
+  void* ps[] = {t.lamx, t.lamy, t.twx, t.twy, t.dctx, t.dcty, t.pairx, t.pairy, t.S, t.G, t.Wg};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, s);
   t = PrecondTables();

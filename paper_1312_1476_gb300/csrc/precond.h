@@ -36,6 +36,13 @@ struct PrecondTables {
   void* twy = nullptr;   // C[ny]
   void* dctx = nullptr;  // C[nx+1]: exp(-i pi t / (2 nx))
   void* dcty = nullptr;  // C[ny+1]
+  // FP32 mirror passes: for each pair k = 0 .. N/4 of a line of N points (L =
+  // N/2), the 16 floats {tw[k], tw[L-k], dct[k], dct[N-k], dct[L-k],
+  // dct[N-L+k], lam of the pair's four coefficients} (k = 0: lam[0], lam[L]),
+  // stored as planes of N/4 + 1 float4 so that consecutive pairs are
+  // contiguous: rows (N = nx) the first three planes, columns (N = ny) all four
+  void* pairx = nullptr;
+  void* pairy = nullptr;
   void* S = nullptr;     // spectral workspace, per vector spec_elems() complex/real pairs
   size_t S_bytes = 0;
   void* G = nullptr;     // g = C v workspace (SPDE squared), per vector n reals

@@ -261,27 +261,33 @@ __device__ __forceinline__ void stage_table(float2* dst, const float2* __restric
 __device__ __forceinline__ void stage_table(float* dst, const float* __restrict__ src, int count) {
   for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
 }
+__device__ __forceinline__ void stage_table(float4* dst, const float4* __restrict__ src, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
+}
 
 // warps per column block: with one line per warp, 8 lines share the staged tables
 template <int LOGL>
 __host__ __device__ constexpr int col_warps() { return one_line<LOGL, true>() ? 8 : 4; }
 
 // Dynamic shared memory of the row kernel:
-//   tile[RB][TP] floats | per-warp scratch [WPC][scratch_f2] float2 | twx[NX] | dctx[NX + 1] (MIRROR only)
+//   tile[RB][TP] floats | per-warp scratch [WPC][scratch_f2] float2 | twx[NX] |
+//   MIRROR: pair planes [3][L/2 + 1] float4 (see pair_tab)
 template <int KIND, int LOGL>
 __host__ __device__ constexpr size_t row_smem_bytes() {
   return (size_t)rows_per_block<KIND, LOGL>() * tile_pitch<KIND, LOGL>() * sizeof(float) +
          (size_t)(rows_per_block<KIND, LOGL>() / lpw<LOGL>()) * scratch_f2<LOGL>() * sizeof(float2) +
-         (size_t)(2 * (1 << LOGL) + (KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 1 : 0)) * sizeof(float2);
+         (size_t)2 * (1 << LOGL) * sizeof(float2) +
+         (KIND == GMRF_PREC_MIRROR ? (size_t)3 * ((1 << LOGL) / 2 + 1) * sizeof(float4) : 0);
 }
 // Dynamic shared memory of the column kernel:
-//   per-warp scratch [col_warps][scratch_f2] float2 | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny] floats
+//   per-warp scratch [col_warps][scratch_f2] float2 | twy[ny] |
+//   CIRCULANT: lamy[ny] floats;  MIRROR: pair records [(L/2 + 1) * 4] float4
 template <int KIND, int LOGL>
 __host__ __device__ constexpr size_t col_smem_bytes() {
   return (size_t)col_warps<LOGL>() * scratch_f2<LOGL, true>() * sizeof(float2) +
-         (size_t)((KIND == GMRF_PREC_CIRCULANT ? (1 << LOGL) : 2 * (1 << LOGL)) +
-                  (KIND == GMRF_PREC_MIRROR ? 2 * (1 << LOGL) + 1 : 0)) * sizeof(float2) +
-         (size_t)(KIND == GMRF_PREC_CIRCULANT ? (1 << LOGL) : 2 * (1 << LOGL)) * sizeof(float);
+         (KIND == GMRF_PREC_CIRCULANT
+              ? (size_t)(1 << LOGL) * (sizeof(float2) + sizeof(float))
+              : (size_t)2 * (1 << LOGL) * sizeof(float2) + (size_t)((1 << LOGL) / 2 + 1) * 4 * sizeof(float4));
 }
 
 template <int KIND>
@@ -378,12 +384,38 @@ __device__ __forceinline__ void unpack_row(const float2* v, float2* p) {
   }
 }
 
+// Twiddles and DCT factors of the pair (k, L-k) of a real line of N = 2L
+// points.  MIRROR reads them from three planes of L/2 + 1 float4 (consecutive
+// pairs contiguous, so a warp's load is conflict-free):
+//   plane 0 {tw_k, tw_{L-k}}, plane 1 {d_k, d_{N-k}}, plane 2 {d_{L-k}, d_{N-L+k}}
+// with tw_t = exp(-2 pi i t / N) and d_t = exp(-i pi t / (2N)).  CIRCULANT has
+// only the twiddles, read from tw[].
+struct PairTab {
+  float2 twk, twkp, dk, dnk, dkp, dnkp;
+};
+template <int KIND, int L>
+__device__ __forceinline__ PairTab pair_tab(int k, const float2* __restrict__ tw, const float4* __restrict__ pt) {
+  PairTab t;
+  if (KIND == GMRF_PREC_MIRROR) {
+    constexpr int HP1 = L / 2 + 1;
+    const float4 P0 = pt[k], P1 = pt[HP1 + k], P2 = pt[2 * HP1 + k];
+    t.twk = f2(P0.x, P0.y); t.twkp = f2(P0.z, P0.w);
+    t.dk = f2(P1.x, P1.y); t.dnk = f2(P1.z, P1.w);
+    t.dkp = f2(P2.x, P2.y); t.dnkp = f2(P2.z, P2.w);
+  } else {
+    t.twk = tw[k];
+    t.twkp = tw[(L - k) & (2 * L - 1)];
+    t.dk = t.dnk = t.dkp = t.dnkp = f2(0.f, 0.f);
+  }
+  return t;
+}
+
 // Post-processing of one pair (k, L-k) of the half-length FFT output Z (natural
 // order in sm line zl) into the spectrum of the real line: CIRCULANT writes
 // X_k (complex) at out[k]; MIRROR writes the DCT-II coefficients C at outr[].
 template <int KIND, int L>
 __device__ __forceinline__ void post_pair(const float2* zl, int k, const float2* __restrict__ tw,
-                                          const float2* __restrict__ dct, float2* outc, float* outr) {
+                                          const float4* __restrict__ pt, float2* outc, float* outr) {
   constexpr int N = 2 * L;
   const float2 zk = zl[k & (L - 1)];
   const float2 zr = zl[(L - k) & (L - 1)];
@@ -394,27 +426,28 @@ __device__ __forceinline__ void post_pair(const float2* zl, int k, const float2*
       outc[L] = f2(xl, 0.f);
     } else {
       outr[0] = x0;
-      outr[L] = dct[L].x * xl;
+      outr[L] = pt[2 * (L / 2 + 1)].x * xl;  // d_L
     }
     return;
   }
+  const PairTab t = pair_tab<KIND, L>(k, tw, pt);
   const float2 zc = conj2(zr);
-  const float2 d = mul2(tw[k], sub2(zk, zc));
+  const float2 d = mul2(t.twk, sub2(zk, zc));
   const float2 Xk = f2(0.5f * (zk.x + zc.x + d.y), 0.5f * (zk.y + zc.y - d.x));
   if (KIND == GMRF_PREC_CIRCULANT) outc[k] = Xk;
   else {
-    outr[k] = mul2(dct[k], Xk).x;
-    outr[N - k] = mulc2(dct[N - k], Xk).x;
+    outr[k] = mul2(t.dk, Xk).x;
+    outr[N - k] = mulc2(t.dnk, Xk).x;
   }
   if (2 * k == L) return;
   const int kp = L - k;
   const float2 zkc = conj2(zk);
-  const float2 d2 = mul2(tw[kp], sub2(zr, zkc));
+  const float2 d2 = mul2(t.twkp, sub2(zr, zkc));
   const float2 Xp = f2(0.5f * (zr.x + zkc.x + d2.y), 0.5f * (zr.y + zkc.y - d2.x));
   if (KIND == GMRF_PREC_CIRCULANT) outc[kp] = Xp;
   else {
-    outr[kp] = mul2(dct[kp], Xp).x;
-    outr[N - kp] = mulc2(dct[N - kp], Xp).x;
+    outr[kp] = mul2(t.dkp, Xp).x;
+    outr[N - kp] = mulc2(t.dnkp, Xp).x;
   }
 }
 
@@ -423,30 +456,31 @@ __device__ __forceinline__ void post_pair(const float2* zl, int k, const float2*
 // half-length FFT is the packed real line (times L).
 template <int KIND, int L>
 __device__ __forceinline__ void pre_pair(const float2* inc, const float* inr, int k, const float2* __restrict__ tw,
-                                         const float2* __restrict__ dct, float2* zl) {
+                                         const float4* __restrict__ pt, float2* zl) {
   constexpr int N = 2 * L;
   float2 Vk, Vp;
   const int kp = L - k;
+  const PairTab t = pair_tab<KIND, L>(k, tw, pt);
   if (KIND == GMRF_PREC_CIRCULANT) {
     Vk = inc[k];
     Vp = inc[kp];
   } else {
     const float ck = inr[k], cnk = k == 0 ? 0.f : inr[N - k];
     const float cp = inr[kp], cnp = inr[N - kp];
-    Vk = mulc2(f2(ck, -cnk), dct[k]);
-    Vp = mulc2(f2(cp, -cnp), dct[kp]);
+    Vk = mulc2(f2(ck, -cnk), t.dk);
+    Vp = mulc2(f2(cp, -cnp), t.dkp);
   }
   {
     const float2 c = conj2(Vp);
     const float2 E = scl2(add2(Vk, c), 0.5f);
-    const float2 O = mulc2(scl2(sub2(Vk, c), 0.5f), tw[k]);
+    const float2 O = mulc2(scl2(sub2(Vk, c), 0.5f), t.twk);
     zl[k] = f2(E.x - O.y, E.y + O.x);
   }
   if (k == 0 || 2 * k == L) return;
   {
     const float2 c = conj2(Vk);
     const float2 E = scl2(add2(Vp, c), 0.5f);
-    const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), tw[kp]);
+    const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), t.twkp);
     zl[kp] = f2(E.x - O.y, E.y + O.x);
   }
 }
@@ -517,7 +551,7 @@ __device__ __forceinline__ void tile_load_T(const Args& a, float* tile, const fl
 // rows written to the tile rows tr0 + g.
 template <int KIND, int LOGL>
 __device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[vpl<LOGL>()], float2* sm, float* tile,
-                                             int tr0, const float2* twx, const float2* dctx) {
+                                             int tr0, const float2* twx, const float4* ptx) {
   constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), TP = tile_pitch<KIND, LOGL>();
   const int lane = threadIdx.x & 31;
   float2 v[vpl<LOGL>()];
@@ -542,15 +576,15 @@ __device__ __forceinline__ void rows_forward(const Args& a, float2 (&p)[vpl<LOGL
   for (int idx = lane; idx < G * HP; idx += 32) {
     const int g = idx / HP, k = idx - g * HP;
     float* trow = tile + (tr0 + g) * TP;
-    post_pair<KIND, L>(sm + g * L, k, twx, dctx, reinterpret_cast<float2*>(trow), trow);
-    if (k == 0) post_pair<KIND, L>(sm + g * L, HP, twx, dctx, reinterpret_cast<float2*>(trow), trow);
+    post_pair<KIND, L>(sm + g * L, k, twx, ptx, reinterpret_cast<float2*>(trow), trow);
+    if (k == 0) post_pair<KIND, L>(sm + g * L, HP, twx, ptx, reinterpret_cast<float2*>(trow), trow);
   }
 }
 
 // inverse real transform: tile rows tr0 + g -> pairs p[g][E] (times L).
 template <int KIND, int LOGL>
 __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[vpl<LOGL>()], float2* sm, const float* tile,
-                                             int tr0, const float2* twx, const float2* dctx) {
+                                             int tr0, const float2* twx, const float4* ptx) {
   constexpr int L = 1 << LOGL, E = L / 32, G = lpw<LOGL>(), TP = tile_pitch<KIND, LOGL>();
   const int lane = threadIdx.x & 31;
   constexpr int HP = L / 2;  // k = 0 and k = L/2 go to one lane (see rows_forward)
@@ -558,8 +592,8 @@ __device__ __forceinline__ void rows_inverse(const Args& a, float2 (&p)[vpl<LOGL
   for (int idx = lane; idx < G * HP; idx += 32) {
     const int g = idx / HP, k = idx - g * HP;
     const float* trow = tile + (tr0 + g) * TP;
-    pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, k, twx, dctx, sm + g * L);
-    if (k == 0) pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, HP, twx, dctx, sm + g * L);
+    pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, k, twx, ptx, sm + g * L);
+    if (k == 0) pre_pair<KIND, L>(reinterpret_cast<const float2*>(trow), trow, HP, twx, ptx, sm + g * L);
   }
   __syncwarp();
   float2 v[vpl<LOGL>()];
@@ -592,7 +626,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* sm = reinterpret_cast<float2*>(smf + RB * TP) + warp * scratch_f2<LOGL>();
   float2* twx = reinterpret_cast<float2*>(smf + RB * TP) + WPC * scratch_f2<LOGL>();  // [NX] exp(-2 pi i t / NX)
-  float2* dctx = twx + NX;                                                    // [NX + 1] (MIRROR)
+  float4* ptx = reinterpret_cast<float4*>(twx + NX);  // MIRROR: 3 planes of NX/4 + 1 (see pair_tab)
   const int s = blockIdx.y;
   const bool step = (MODE == R_FWD || MODE == R_LAST || MODE == R_MID || MODE == R_MIDW || MODE == R_MIDG) &&
                     a.in == nullptr;
@@ -611,7 +645,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
   // so that both latencies overlap (one barrier)
   auto stage_tables = [&]() {
     stage_table(twx, a.twx, NX);
-    if (KIND == GMRF_PREC_MIRROR) stage_table(dctx, a.dctx, NX + 1);
+    if (KIND == GMRF_PREC_MIRROR) stage_table(ptx, a.pairx, 3 * (NX / 4 + 1));
   };
 
   if (MODE == R_FWD) {
@@ -653,7 +687,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
         if (a.P.vb) store_row_bf16<KIND, E>(p + g * E, vb_at(a.P, s, j, n, ro));
       }
     }
-    rows_forward<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);
+    rows_forward<KIND, LOGL>(a, p, sm, tile, tr0, twx, ptx);
     __syncthreads();
     tile_store_T<KIND, LOGL>(a, tile, Tv, y0);
     return;
@@ -684,7 +718,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
   stage_tables();
   if (MODE != R_MIDG) tile_load_T<KIND, LOGL>(a, tile, Tv, y0);
   __syncthreads();
-  if (MODE != R_MIDG) rows_inverse<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);
+  if (MODE != R_MIDG) rows_inverse<KIND, LOGL>(a, p, sm, tile, tr0, twx, ptx);
   if (MODE == R_INV) {
 #pragma unroll
     for (int g = 0; g < G; ++g) store_row<KIND, E>(p + g * E, a.out + (size_t)s * n + (size_t)(y0 + tr0 + g) * NX);
@@ -786,7 +820,7 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
       }
     }
     __syncthreads();  // tile rows consumed by every warp before they are rewritten
-    rows_forward<KIND, LOGL>(a, p, sm, tile, tr0, twx, dctx);
+    rows_forward<KIND, LOGL>(a, p, sm, tile, tr0, twx, ptx);
     __syncthreads();
     tile_store_T<KIND, LOGL>(a, tile, Tv, y0);
     return;
@@ -849,9 +883,12 @@ __global__ void __launch_bounds__(32 * (rows_per_block<KIND, LOGL>() / lpw<LOGL>
 
 // ----------------------------------------------------------------- columns
 // symbol of B_bar^{-p/2} (times the transform normalisation); cx = kappa_bar^2 + lambda_x
-__device__ __forceinline__ float sym(const Args& a, float cx, const float* lamy, int ky) {
-  const float r = rsqrtf(cx + lamy[ky]);  // lam^{-1/2}; lam^{-1} = r^2 (a few ulp, no division)
+__device__ __forceinline__ float sym_l(const Args& a, float cx, float lam_y) {
+  const float r = rsqrtf(cx + lam_y);  // lam^{-1/2}; lam^{-1} = r^2 (a few ulp, no division)
   return (a.power == 2 ? r * r : r) * a.dscale;
+}
+__device__ __forceinline__ float sym(const Args& a, float cx, const float* lamy, int ky) {
+  return sym_l(a, cx, lamy[ky]);
 }
 
 template <int KIND, int LOGL>
@@ -863,15 +900,15 @@ __global__ void __launch_bounds__(32 * col_warps<LOGL>()) k_col(Args a, int step
   if (step_mode && a.st[s].status != VS_RUNNING) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* sm = reinterpret_cast<float2*>(smf) + warp * scratch_f2<LOGL, true>();
-  // layout (must match col_smem_bytes): warp scratch | twy[ny] | dcty[ny + 1] (MIRROR only) | lamy[ny]
+  // layout (must match col_smem_bytes): warp scratch | twy[ny] | CIRCULANT: lamy[ny]; MIRROR: pair records
   float2* twy = reinterpret_cast<float2*>(smf) + col_warps<LOGL>() * scratch_f2<LOGL, true>();
-  float2* dcty = twy + NYc;
-  float* lamy = reinterpret_cast<float*>(dcty + (KIND == GMRF_PREC_MIRROR ? NYc + 1 : 0));
+  float* lamy = reinterpret_cast<float*>(twy + NYc);
+  float4* ptab = reinterpret_cast<float4*>(twy + NYc);  // NYc float2 keep it 16-byte aligned
   // the tables are staged after the warp's line loads are issued (one barrier)
   auto stage_tables = [&]() {
     stage_table(twy, a.twy, NYc);
-    if (KIND == GMRF_PREC_MIRROR) stage_table(dcty, a.dcty, NYc + 1);
-    stage_table(lamy, a.lamy, NYc);
+    if (KIND == GMRF_PREC_MIRROR) stage_table(ptab, a.pairy, 4 * (L / 2 + 1));
+    else stage_table(lamy, a.lamy, NYc);
     __syncthreads();
   };
   float* Tv = a.T + (size_t)s * a.tstride;
@@ -958,57 +995,61 @@ __global__ void __launch_bounds__(32 * col_warps<LOGL>()) k_col(Args a, int step
     for (int q = 1; q < G; ++q)
       if (g == q) cx = cxl[q];
     float C[4] = {0.f, 0.f, 0.f, 0.f};
-    int ci[4] = {0, 0, 0, 0};
     int nc = 0;
     float2* zl = sm + g * L;
     const bool live = kx < a.nx;
+    // the pair's entries, one float4 from each of four planes (consecutive k are contiguous):
+    // twiddles tw_k, tw_kp | DCT factors d_k, d_{NY-k} | d_kp, d_{NY-kp} | 4 lambda_y
+    const float4 P0 = ptab[k], P1 = ptab[(HP + 1) + k], P2 = ptab[2 * (HP + 1) + k], P3 = ptab[3 * (HP + 1) + k];
+    const float2 twk = f2(P0.x, P0.y), twkp = f2(P0.z, P0.w);
+    const float2 dk = f2(P1.x, P1.y), dnk = f2(P1.z, P1.w), dkp = f2(P2.x, P2.y), dnkp = f2(P2.z, P2.w);
+    const float lam[4] = {P3.x, P3.y, P3.z, P3.w};
     // DCT coefficients of this pair, scaled by the symbol
     {
       const float2 zk = zl[k & (L - 1)];
       const float2 zr = zl[(L - k) & (L - 1)];
       if (k == 0) {
-        ci[0] = 0; C[0] = zk.x + zk.y;
-        ci[1] = L; C[1] = dcty[L].x * (zk.x - zk.y);
+        C[0] = zk.x + zk.y;
+        C[1] = dkp.x * (zk.x - zk.y);  // d_L
         nc = 2;
       } else {
         const float2 zc = conj2(zr);
-        const float2 d = mul2(twy[k], sub2(zk, zc));
+        const float2 d = mul2(twk, sub2(zk, zc));
         const float2 Xk = f2(0.5f * (zk.x + zc.x + d.y), 0.5f * (zk.y + zc.y - d.x));
-        ci[0] = k; C[0] = mul2(dcty[k], Xk).x;
-        ci[1] = NY - k; C[1] = mulc2(dcty[NY - k], Xk).x;
+        C[0] = mul2(dk, Xk).x;
+        C[1] = mulc2(dnk, Xk).x;
         nc = 2;
         if (2 * k != L) {
-          const int kp = L - k;
           const float2 zkc = conj2(zk);
-          const float2 d2 = mul2(twy[kp], sub2(zr, zkc));
+          const float2 d2 = mul2(twkp, sub2(zr, zkc));
           const float2 Xp = f2(0.5f * (zr.x + zkc.x + d2.y), 0.5f * (zr.y + zkc.y - d2.x));
-          ci[2] = kp; C[2] = mul2(dcty[kp], Xp).x;
-          ci[3] = NY - kp; C[3] = mulc2(dcty[NY - kp], Xp).x;
+          C[2] = mul2(dkp, Xp).x;
+          C[3] = mulc2(dnkp, Xp).x;
           nc = 4;
         }
       }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      if (i < nc) C[i] = live ? C[i] * sym(a, cx, lamy, ci[i]) : 0.f;
+      if (i < nc) C[i] = live ? C[i] * sym_l(a, cx, lam[i]) : 0.f;
     // inverse pre-processing of the same pair
     const int kp = L - k;
     float ck, cnk, cp, cnp;
     if (k == 0) { ck = C[0]; cnk = 0.f; cp = C[1]; cnp = C[1]; }
     else if (2 * k == L) { ck = C[0]; cnk = C[1]; cp = C[0]; cnp = C[1]; }
     else { ck = C[0]; cnk = C[1]; cp = C[2]; cnp = C[3]; }
-    const float2 Vk = mulc2(f2(ck, -cnk), dcty[k]);
-    const float2 Vp = mulc2(f2(cp, -cnp), dcty[kp]);
+    const float2 Vk = mulc2(f2(ck, -cnk), dk);
+    const float2 Vp = mulc2(f2(cp, -cnp), dkp);
     {
       const float2 c = conj2(Vp);
       const float2 Ev = scl2(add2(Vk, c), 0.5f);
-      const float2 O = mulc2(scl2(sub2(Vk, c), 0.5f), twy[k]);
+      const float2 O = mulc2(scl2(sub2(Vk, c), 0.5f), twk);
       zl[k] = f2(Ev.x - O.y, Ev.y + O.x);
     }
     if (k != 0 && 2 * k != L) {
       const float2 c = conj2(Vk);
       const float2 Ev = scl2(add2(Vp, c), 0.5f);
-      const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), twy[kp]);
+      const float2 O = mulc2(scl2(sub2(Vp, c), 0.5f), twkp);
       zl[kp] = f2(Ev.x - O.y, Ev.y + O.x);
     }
   };

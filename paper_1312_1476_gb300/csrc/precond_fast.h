@@ -21,6 +21,8 @@ struct Args {
   const float2* twy;   // exp(-2 pi i t / ny)
   const float2* dctx;  // exp(-i pi t / (2 nx)), t <= nx
   const float2* dcty;
+  const float4* pairx; // mirror rows: 3 planes of nx/4 + 1 float4 (see PrecondTables::pairx)
+  const float4* pairy; // mirror columns: 4 planes of ny/4 + 1 float4 (see PrecondTables::pairy)
   float* T;            // transposed spectrum
   size_t tstride;      // floats per vector
   float* G;            // g = C v (squared operator)

@@ -1,11 +1,14 @@
 """Bounded runs of the library's hot path for profiler captures.
 
-    python -m paper_1312_1476_gb300.profile_case <case> [--nsamples N] [--steps M]
+    python -m paper_1312_1476_gb300.profile_case <case> [--nsamples N] [--steps M] [--trace]
 
 Each case builds one benchmark configuration on its synthetic inputs, runs
 one sample call capped at M Lanczos steps (so it ends after M steps whatever
 the tolerance) and exits.  The sizes keep a capture small: one or a few
-vectors, a few GB of device memory at most.
+vectors, a few GB of device memory at most.  With --trace it then repeats the
+call twice more, timed as a whole and then with CUDA events around every
+launch, and reports each kernel class's time per vector-step (the sum of the
+Lanczos steps of all vectors).
 
 Cases:
   headline_1024  1024 x 1024 SPDE, zero-Neumann, mirror preconditioner, FP32
@@ -21,7 +24,7 @@ import argparse
 import numpy as np
 
 
-def run(case: str, nsamples: int, steps: int) -> dict:
+def run(case: str, nsamples: int, steps: int, trace: bool = False) -> dict:
     import torch
     from . import gmrf, inputs
     if case == "headline_1024":
@@ -43,14 +46,43 @@ def run(case: str, nsamples: int, steps: int) -> dict:
     else:
         raise ValueError("unknown case %r" % case)
     n = int(np.prod(shape))
-    with prob:
-        x = torch.empty(nsamples * n, dtype=torch.float32, device="cuda")
+    out = {"case": case, "nsamples": nsamples}
+
+    def call():
         rc, info = prob.sample(x, nsamples=nsamples, tol=1e-6, m_max=steps, seed=2, check_every=8,
                                raise_on_error=False)
         torch.cuda.synchronize()
-    if rc not in (gmrf.OK, gmrf.ERR_NOT_CONVERGED):
-        raise gmrf.GmrfError(rc, "profile case " + case)
-    return {"case": case, "nsamples": nsamples, "m_used": [i.m_used for i in info], "rc": rc}
+        if rc not in (gmrf.OK, gmrf.ERR_NOT_CONVERGED):
+            raise gmrf.GmrfError(rc, "profile case " + case)
+        return rc, info
+
+    with prob:
+        x = torch.empty(nsamples * n, dtype=torch.float32, device="cuda")
+        rc, info = call()
+        out.update(m_used=[i.m_used for i in info], rc=rc)
+        if trace:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rc, info = call()
+            e1.record()
+            torch.cuda.synchronize()
+            vs = sum(i.m_used for i in info)
+            out["ms_call"] = round(e0.elapsed_time(e1), 3)
+            out["us_per_vec_step"] = round(e0.elapsed_time(e1) * 1e3 / vs, 3)
+            gmrf.trace_reset()
+            gmrf.trace_timing(True)
+            try:
+                call()
+            finally:
+                gmrf.trace_timing(False)
+            per = {}
+            for c in gmrf.KERNEL_CLASSES:
+                ms, _, launches = gmrf.trace_query(c)
+                if launches:
+                    per[c] = {"launches": launches, "us_per_launch": round(ms * 1e3 / launches, 2),
+                              "us_per_vec_step": round(ms * 1e3 / vs, 3)}
+            out["traced"] = per
+    return out
 
 
 def main(argv=None):
@@ -58,8 +90,9 @@ def main(argv=None):
     ap.add_argument("case", choices=["headline_1024", "batched_512", "3d_256", "stencil2d_1024"])
     ap.add_argument("--nsamples", type=int, default=1)
     ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--trace", action="store_true", help="also report per-kernel-class times")
     a = ap.parse_args(argv)
-    print(run(a.case, a.nsamples, a.steps))
+    print(run(a.case, a.nsamples, a.steps, a.trace))
 
 
 if __name__ == "__main__":
