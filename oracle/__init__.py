@@ -26,6 +26,10 @@ from massive Gaussian random vectors"):
   reorthogonalisation), the Theorem 1 bounds, the preconditioned sampler of
   Proposition 1, and the Hutchinson / Gauss-quadrature log-determinant of
   Section 6.
+* ``sparse``   -- general sparse Q with an incomplete-Cholesky factor F as the
+  preconditioner (Section 5.2, Figure 3): the threshold factorisation, and the
+  Proposition 1 map x = F^{-T} (F^{-1} Q F^{-T})^{-1/2} z and log-determinant,
+  by dense linear algebra.
 * ``philox``   -- the Philox-4x32-10 counter-based generator (Salmon et al.,
   SC'11) that the device path uses for z and Rademacher probes, restated from
   its published definition, with the Box-Muller transform.
