@@ -505,8 +505,53 @@ def measure_variants(args, gmrf, torch, flush, peak):
         out["batched_512"]["cpu_oracle"] = cpu_oracle_rate("batched_512", out["batched_512"]["m_mean"])
         out["3d_256"]["cpu_oracle"] = cpu_oracle_rate("3d_128", out["3d_256"]["m_mean"])
     out["table1"] = measure_table1(gmrf, torch)
+    out["figure3_ichol"] = measure_figure3(gmrf, torch, timed, cpu=not getattr(args, "no_cpu_baseline", False))
     out["serving"] = measure_serving()
     return out
+
+
+def measure_figure3(gmrf, torch, timed, cpu=True):
+    """Section 5.2 (Figure 3): the sparse sampler on Q = (31^2 G)^2, G the
+    5-point Dirichlet Laplacian of a 30 x 30 lattice (n = 900), without a
+    preconditioner and with incomplete-Cholesky factors F of several drop
+    thresholds (M = F F^T, Proposition 1): factor size, subspace size to the
+    Theorem 1 estimate 1e-8 (FP64) and samples/s at 256 samples per call."""
+    from paper_1312_1476_gb300 import inputs
+    Q = inputs.figure3_matrix()
+    n = 900
+    m_max = 3000
+    cfgs = [("none", None, None), ("jacobi (droptol inf)", float("inf"), 0.0),
+            ("IC(0), shift 1e-2", -1.0, 1e-2), ("ICT droptol 1e-3, shift 1e-3", 1e-3, 1e-3),
+            ("ICT droptol 1e-5, shift 1e-4", 1e-5, 1e-4), ("exact Cholesky (droptol 0)", 0.0, 0.0)]
+    res = {"workload": "Figure 3 matrix (31^2 G)^2, n = 900, FP64, tol 1e-8, 256 samples per call; "
+                       "IC drop rule: |update| < droptol * ||column of Q + shift diag(Q)||_1",
+           "factors": {}}
+    x = torch.empty(256 * n, dtype=torch.float64, device="cuda")
+    for name, dt, sh in cfgs:
+        F = None if dt is None else gmrf.ichol(Q, droptol=dt, shift=sh)
+        with gmrf.SparseProblem(Q, F, precision="fp64") as p:
+            p.sample(x, nsamples=256, tol=1e-8, m_max=m_max, seed=1)
+            ms, (rc, info) = timed(lambda i: p.sample(x, nsamples=256, tol=1e-8, m_max=m_max, seed=3 + i), 2)
+        ms_used = [i.m_used for i in info]
+        res["factors"][name] = {"nnz_F": int(len(F[1])) if F is not None else 0,
+                                "m_mean": float(np.mean(ms_used)), "m_max": int(max(ms_used)),
+                                "samples_per_s": 256e3 / ms, "ms_per_call": ms, "status": rc}
+    if cpu:
+        # the oracle's map (dense eigendecomposition of A, FP64) for the ICT 1e-3 factor
+        from oracle import sparse as osp
+        Qs = osp.csr(*Q)
+        F = osp.ichol(Qs, droptol=1e-3, shift=1e-3)
+        z = inputs.gaussian_vectors(1, n, seed=2, dtype=np.float64)
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 2.0:
+            osp.sample_precond_dense(Qs, F, z)
+            reps += 1
+        dtm = (time.perf_counter() - t0) / reps
+        res["cpu_oracle"] = {"value": 1.0 / dtm, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                             "sample": "%d samples of the oracle's dense Proposition 1 map (eigendecomposition of "
+                                       "A = F^{-1} Q F^{-T}, ICT 1e-3 factor, FP64)" % reps}
+    return res
 
 
 def measure_cfg1(gmrf, torch, timed):

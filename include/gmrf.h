@@ -12,6 +12,9 @@
  *   gmrf_sample  -- x_m ~= Q^{-1/2} z by the Lanczos sampler (Section 4,
  *                   Algorithm 1), m chosen adaptively from the a-posteriori
  *                   bound of Theorem 1 (eq. krylov_bound).
+ *   gmrf_create_sparse -- a general sparse Q in CSR, optionally with an
+ *                   incomplete-Cholesky factor as the preconditioner
+ *                   (Section 5.2); gmrf_ichol computes that factor.
  *   gmrf_logdet  -- log det Q by the Hutchinson estimator with Rademacher
  *                   probes and Lanczos (Gauss) quadrature (Section 6), with
  *                   the preconditioned split of Section 6.2
@@ -293,7 +296,8 @@ int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t 
  * and CUDA-event timing of the library's kernels by class, for profiling and
  * the roofline report.  Classes: 0 fused stencil step, 1 preconditioned
  * row-forward, 2 column transform, 3 row-mid, 4 row-last, 5 ||z||, 6 Philox,
- * 7 T_m functions, 8 assembly, 9 plain preconditioner applies, 10 other.
+ * 7 T_m functions, 8 assembly, 9 plain preconditioner applies, 10 other,
+ * 11 sparse (CSR) Lanczos step.
  *   op 0: reset counters and times;  op 1: enable event timing (events are
  *   recorded around every launch on its stream);  op 2: disable timing;
  *   op 3: query class kclass (-1 = all): *total_ms = summed kernel time,
@@ -364,6 +368,94 @@ int gmrf_autotune(gmrf_problem* p, int32_t nvec_max, gmrf_tuning* out);
  * problem with the same grid).  GMRF_ERR_INVALID for negative fields or a
  * non-zero reserved. */
 int gmrf_set_tuning(gmrf_problem* p, const gmrf_tuning* t);
+
+/* ---- General sparse Q with an incomplete-Cholesky preconditioner ----------
+ * Section 5.2 proposes the incomplete Cholesky factor F of a general sparse Q
+ * (F lower triangular and sparse, F F^T close to Q) as the preconditioner
+ * M = F F^T of Proposition 1, so that
+ *     x = tau^{-1/2} F^{-T} A^{-1/2} z,     A = F^{-1} Q F^{-T},
+ *     log det(tau Q) = log det A + 2 sum_i log F_ii + n log tau   (Section 6.2),
+ * with A^{-1/2} z and the quadrature of log A from Algorithm 1 on A.  Figure 3
+ * runs it on (31^2 G)^2, G the 5-point Dirichlet Laplacian of a 30 x 30
+ * lattice, for factors with several drop thresholds.
+ *
+ * gmrf_sparse_desc (all arrays are host memory, copied by gmrf_create_sparse):
+ *   n                     dimension, >= 1
+ *   rowptr[n+1], colind[nnz], val[nnz]
+ *                         Q in CSR with both triangles; rowptr[0] = 0 and
+ *                         non-decreasing; columns in [0, n), no duplicates
+ *                         within a row, any order; Q must be symmetric
+ *                         (value Q_ij == Q_ji exactly) with a positive diagonal
+ *   f_rowptr, f_colind, f_val
+ *                         F in CSR, or f_rowptr == NULL for no preconditioner
+ *                         (Algorithm 1 on Q itself); every entry has column
+ *                         <= row, every row has a positive diagonal entry
+ *   tau                   precision scale (> 0): the problem is tau Q
+ *   precision             gmrf_precision of the vectors and of the copies of
+ *                         Q and F the kernels use (FP32 rounds them to float)
+ *   reserved              must be 0
+ *
+ * A sparse problem supports gmrf_sample (v_storage GMRF_VSTORE_NATIVE only,
+ * otherwise GMRF_ERR_UNSUPPORTED), gmrf_logdet and gmrf_sample_logdet
+ * (colour_dist 0 only: the coloured probes of Section 6.1 need the lattice),
+ * gmrf_solve (x = tau^{-1} F^{-T} A^{-1} F^{-1} b), the asynchronous forms,
+ * gmrf_size, gmrf_autotune and gmrf_set_tuning, and gmrf_apply with
+ *   which = 0: y = tau Q v
+ *   which = 1: y = A v = F^{-1} Q F^{-T} v      (needs F)
+ *   which = 2: y = tau^{-1/2} F^{-T} v          (needs F; the map from
+ *              A^{-1/2} z to the sample, the role M^{-1/2} has on lattices).
+ * gmrf_apply_inv_sqrt_noalloc returns GMRF_ERR_UNSUPPORTED.
+ *
+ * Device design: one thread block per vector keeps that vector's working
+ * vectors in shared memory for a whole Lanczos step; the products with Q
+ * read Q's CSR arrays from L2, and the triangular solves with F and F^T run
+ * level by level (the rows of one level depend only on earlier levels and
+ * are solved in parallel).  Hence n is limited by the shared memory of one
+ * block: 3 n elements of the precision must fit in the device's opt-in
+ * limit less 2 KiB (about n <= 18,000 in FP32, 9,000 in FP64 on a GPU with
+ * 227 KiB); larger n returns GMRF_ERR_UNSUPPORTED.
+ *
+ * Errors: GMRF_ERR_INVALID for NULL desc/out/rowptr/colind/val, n < 1, a
+ * malformed or asymmetric Q, a non-positive diagonal, an F entry above the
+ * diagonal or a missing / non-positive F diagonal, non-finite values,
+ * tau <= 0, reserved != 0; GMRF_ERR_UNSUPPORTED for n above the limit;
+ * GMRF_ERR_OOM, GMRF_ERR_CUDA. */
+typedef struct {
+  int64_t n;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* val;
+  const int64_t* f_rowptr;
+  const int32_t* f_colind;
+  const double* f_val;
+  double tau;
+  int32_t precision;
+  int32_t reserved;
+} gmrf_sparse_desc;
+int gmrf_create_sparse(const gmrf_sparse_desc* desc, void* stream, gmrf_problem** out);
+
+/* Threshold incomplete Cholesky factor F of A' = Q + shift diag(Q) (Section
+ * 5.2), host code only (no device work, callable without a GPU).  Column j =
+ * 0 .. n-1, left-looking:
+ *     w = A'[j:, j] - F[j:, :j] F[j, :j]^T,   F_jj = sqrt(w_0),
+ *     F_ij = w_i / F_jj (i > j), kept unless
+ *       droptol <  0 (IC(0)):  A'_ij == 0      (no fill outside Q's pattern)
+ *       droptol >= 0 (ICT):    |w_i| < droptol * sum_{i >= j} |A'_ij|
+ * (the paper gives no dropping rule; this one does not depend on the scale
+ * of Q).  droptol = 0 gives the exact Cholesky factor, a very large droptol
+ * the diagonal sqrt(diag A').  Q: CSR as in gmrf_sparse_desc.
+ * Output F in CSR: f_rowptr[n+1], and per row its columns ascending with the
+ * diagonal last, in f_colind / f_val.
+ *   Size query: with f_colind == NULL or f_val == NULL only *f_nnz (and
+ *   f_rowptr, if not NULL) are written.  Otherwise cap is the capacity of
+ *   f_colind and f_val; a factor with more entries returns GMRF_ERR_INVALID
+ *   with *f_nnz set and nothing else written.
+ * Errors: GMRF_ERR_INVALID (NULL rowptr/colind/val/f_nnz, malformed or
+ * asymmetric Q, non-finite values, shift < 0 or not finite, droptol NaN);
+ * GMRF_ERR_NOT_SPD for a pivot w_0 <= 0, with *f_nnz = the column where it
+ * occurred (a larger shift usually cures it); GMRF_ERR_OOM for host memory. */
+int gmrf_ichol(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double droptol,
+               double shift, int64_t cap, int64_t* f_rowptr, int32_t* f_colind, double* f_val, int64_t* f_nnz);
 
 void gmrf_destroy(gmrf_problem* p);
 const char* gmrf_strerror(int code);

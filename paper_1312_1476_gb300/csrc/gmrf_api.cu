@@ -117,6 +117,7 @@ struct gmrf_problem {
   StepGraph graph;
   DevBuf kappa2;  // float [n] or empty (constant)
   PrecondTables pre;
+  SparseOp* sp = nullptr;  // general sparse Q (gmrf_create_sparse), else null
   // Lanczos workspace (grow-only)
   DevBuf W0, W1, V, st, alpha, beta, alpha_f, beta2_f, partials, counters, y, scratch, nodes, q, out2, stage,
       stage2, work, Vb, xacc, accn, solvew;
@@ -128,6 +129,11 @@ struct gmrf_problem {
 namespace {
 
 size_t esize(const gmrf_problem* p) { return p->fp64 ? 8 : 4; }
+
+// A sparse problem with an incomplete-Cholesky factor: the sample and solve
+// map their Lanczos result through F^{-T} (and the solve its start vector
+// through F^{-1}).
+bool sparse_f(const gmrf_problem* p) { return p->sp && sparse_has_factor(p->sp); }
 
 // Order the work stream after the caller's stream (entry) and the caller's
 // stream after the work stream (exit).
@@ -236,7 +242,9 @@ int worst_status(const VecState* st, int nvec) {
 // gmrf code for launch failures only; per-vector outcomes are in st_host.
 int launch_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, int c, cudaStream_t s) {
   for (int k = 0; k < c; ++k) {
-    if (p->precond == GMRF_PREC_NONE)
+    if (p->sp)
+      CK(traced(KC_SPARSE_STEP, s, 1, [&] { return launch_sparse_step(*p->sp, b, P, s); }));
+    else if (p->precond == GMRF_PREC_NONE)
       CK(traced(KC_STENCIL_STEP, s, 1,
                 [&] { return launch_stencil_step(p->g, p->fp64, p->kappa2.p, p->kappa2_const, b, P, s); }));
     else
@@ -293,7 +301,7 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   G.S = S;
   G.partials = b.partials;
   G.timed = timed;
-  G.kernels_per_step = (p->precond ? 5 : 1) + (b.Xacc ? 1 : 0);
+  G.kernels_per_step = (p->precond && !p->sp ? 5 : 1) + (b.Xacc ? 1 : 0);
   return GMRF_OK;
 }
 
@@ -505,6 +513,47 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
   return GMRF_OK;
 }
 
+int gmrf_create_sparse(const gmrf_sparse_desc* d, void* stream, gmrf_problem** out) {
+  if (!d || !out) return GMRF_ERR_INVALID;
+  *out = nullptr;
+  if (d->precision != GMRF_FP32 && d->precision != GMRF_FP64) return GMRF_ERR_INVALID;
+  if (d->reserved != 0 || !(d->tau > 0.0) || !std::isfinite(d->tau)) return GMRF_ERR_INVALID;
+  if (!d->rowptr || !d->colind || !d->val || d->n < 1) return GMRF_ERR_INVALID;
+  if (d->f_rowptr && (!d->f_colind || !d->f_val)) return GMRF_ERR_INVALID;
+  gmrf_problem* p = new (std::nothrow) gmrf_problem();
+  if (!p) return GMRF_ERR_OOM;
+  // the lattice fields describe a 1-D index space of n cells (no stencil is used)
+  p->g.dim = 1;
+  p->g.nx = (int)std::min<int64_t>(d->n, 1 << 30);
+  p->g.ny = 1;
+  p->g.nz = 1;
+  p->g.n = (size_t)d->n;
+  p->g.bc = GMRF_BC_DIRICHLET;
+  p->g.op = GMRF_OP_SHIFTED_LAPLACIAN;
+  p->precond = GMRF_PREC_NONE;
+  p->fp64 = d->precision == GMRF_FP64;
+  p->tau = d->tau;
+  p->stream = (cudaStream_t)stream;
+  auto fail = [&](int code) {
+    gmrf_destroy(p);
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&p->ws, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GMRF_ERR_CUDA);
+  }
+  if (enter(p) != GMRF_OK) return fail(GMRF_ERR_CUDA);
+  double ldf = 0.0;
+  const int r = sparse_create(&p->sp, d, p->fp64, p->ws, &ldf);
+  if (r != GMRF_OK) return fail(r);
+  p->logdet_M = ldf;  // log det(F F^T); 0 without F
+  if (leave(p) != GMRF_OK || cudaStreamSynchronize(p->ws) != cudaSuccess) return fail(GMRF_ERR_CUDA);
+  *out = p;
+  return GMRF_OK;
+}
+
 void gmrf_destroy(gmrf_problem* p) {
   if (!p) return;
   async_shutdown(p);  // submitted calls finish first
@@ -515,6 +564,8 @@ void gmrf_destroy(gmrf_problem* p) {
                     &p->stage2, &p->work, &p->Vb, &p->xacc, &p->accn, &p->solvew};
   for (DevBuf* b : bufs) release(*b, p->ws);
   precond_free(p->pre, p->ws);
+  sparse_free(p->sp, p->ws);
+  p->sp = nullptr;
   if (p->ws) cudaStreamSynchronize(p->ws);
   delete[] p->st_host;
   if (p->ev_in) cudaEventDestroy(p->ev_in);
@@ -532,13 +583,14 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
   const bool bf16 = o->v_storage == GMRF_VSTORE_BF16;
   const bool two_pass = o->v_storage == GMRF_VSTORE_NONE;
   if (bf16 && p->fp64) return GMRF_ERR_UNSUPPORTED;
+  if (p->sp && o->v_storage != GMRF_VSTORE_NATIVE) return GMRF_ERR_UNSUPPORTED;
   const size_t n = p->g.n, es = esize(p);
   const int m_max = o->m_max;
   const int nslots = (bf16 || two_pass) ? 2 : m_max + 1;
   const bool x_dev = is_device_ptr(x_out);
   const bool z_dev = o->z_in && is_device_ptr(o->z_in);
   const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) : 0) +
-                       (bf16 ? (size_t)(m_max + 1) * n * sizeof(__nv_bfloat16) : 0) +
+                       (sparse_f(p) ? n * es : 0) + (bf16 ? (size_t)(m_max + 1) * n * sizeof(__nv_bfloat16) : 0) +
                        (two_pass ? 2 * n * sizeof(float) + (p->precond ? n * es : 0) : 0);
   int chunk = batch_size(p, o->nsamples, nslots, m_max, true, extra);
   if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
@@ -590,7 +642,14 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
       return two_pass ? launch_accumulate_finish(p->fp64, n, b, dst, s)
                       : launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, extra, dst, s);
     };
-    if (p->precond == GMRF_PREC_NONE) {
+    if (sparse_f(p)) {
+      // u = ||z|| V_m y, then x = tau^{-1/2} F^{-T} u (Proposition 1 with M = F F^T)
+      CKR(ensure(p->work, (size_t)c * n * es, p->ws));
+      CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0, p->work.p); }));
+      CK(traced(KC_PRE_APPLY, s, 1, [&] { return launch_sparse_ops(*p->sp, 2, p->work.p, xdst, c, s); }));
+      CK(traced(KC_OTHER, s, 1,
+                [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / std::sqrt(p->tau), s); }));
+    } else if (p->precond == GMRF_PREC_NONE) {
       CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0 / std::sqrt(p->tau), xdst); }));
     } else {
       // u = ||z|| V_m y, then x = M^{-1/2} u = tau^{-1/2} B_bar^{-p/2} u (Proposition 1)
@@ -624,7 +683,8 @@ int gmrf_solve(gmrf_problem* p, const gmrf_solve_opts* o, const void* b_in, void
   const bool x_dev = is_device_ptr(x_out);
   const bool b_dev = is_device_ptr(b_in);
   const size_t extra = (x_dev ? 0 : n * es) + (b_dev ? 0 : n * es) +
-                       (p->precond ? precond_extra_bytes(p->pre, es) + n * es : 0) + sizeof(double) * m_max;
+                       (p->precond ? precond_extra_bytes(p->pre, es) + n * es : 0) + (sparse_f(p) ? n * es : 0) +
+                       sizeof(double) * m_max;
   int chunk = batch_size(p, o->nrhs, nslots, m_max, false, extra);
   if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
   if (chunk < 1) return GMRF_ERR_OOM;
@@ -637,8 +697,17 @@ int gmrf_solve(gmrf_problem* p, const gmrf_solve_opts* o, const void* b_in, void
     CKR(ensure_lanczos(p, c, nslots, m_max, false, b));
     CKR(ensure(p->solvew, sizeof(double) * (size_t)c * m_max, p->ws));
     const char* bsrc = (const char*)b_in + (size_t)s0 * n * es;
-    // start vector: b (no preconditioner) or B_bar^{-p/2} b, normalised by the first step
-    if (p->precond == GMRF_PREC_NONE) {
+    // start vector: b (no preconditioner), F^{-1} b (sparse with F) or
+    // B_bar^{-p/2} b, normalised by the first step
+    if (sparse_f(p)) {
+      const void* dsrc = bsrc;
+      if (!b_dev) {
+        CKR(ensure(p->stage2, (size_t)c * n * es, p->ws));
+        CK(cudaMemcpyAsync(p->stage2.p, bsrc, (size_t)c * n * es, cudaMemcpyHostToDevice, s));
+        dsrc = p->stage2.p;
+      }
+      CK(traced(KC_PRE_APPLY, s, 1, [&] { return launch_sparse_ops(*p->sp, 3, dsrc, b.W[0], c, s); }));
+    } else if (p->precond == GMRF_PREC_NONE) {
       CK(cudaMemcpyAsync(b.W[0], bsrc, (size_t)c * n * es, b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          s));
     } else {
@@ -659,7 +728,14 @@ int gmrf_solve(gmrf_problem* p, const gmrf_solve_opts* o, const void* b_in, void
       xdst = p->stage.p;
     }
     // x_m = ||b~|| V_m T_m^{-1} e_1; Q = tau Q~ (the steps run on Q~ or A, both tau-free)
-    if (p->precond == GMRF_PREC_NONE) {
+    if (sparse_f(p)) {
+      // u = A^{-1} F^{-1} b, then x = tau^{-1} F^{-T} u
+      CKR(ensure(p->work, (size_t)c * n * es, p->ws));
+      CK(traced(KC_ASSEMBLE, s, 1,
+                [&] { return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
+      CK(traced(KC_PRE_APPLY, s, 1, [&] { return launch_sparse_ops(*p->sp, 2, p->work.p, xdst, c, s); }));
+      CK(traced(KC_OTHER, s, 1, [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / p->tau, s); }));
+    } else if (p->precond == GMRF_PREC_NONE) {
       CK(traced(KC_ASSEMBLE, s, 1, [&] {
         return launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, 1.0 / p->tau, xdst, s);
       }));
@@ -690,6 +766,7 @@ int gmrf_logdet(gmrf_problem* p, const gmrf_logdet_opts* o, double* logdet, doub
   if (!(o->tol > 0.0) || !std::isfinite(o->tol) || o->m_max < 1 || o->m_max > 8192 || o->nprobes < 1 ||
       o->colour_dist < 0 || o->colour_dist > 15)
     return GMRF_ERR_INVALID;
+  if (p->sp && o->colour_dist != 0) return GMRF_ERR_UNSUPPORTED;  // colouring needs the lattice
   const size_t n = p->g.n, es = esize(p);
   const int m_max = o->m_max;
   const bool z_dev = o->probes_in && is_device_ptr(o->probes_in);
@@ -752,6 +829,7 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
       so->v_storage != GMRF_VSTORE_NATIVE || lo->tol != so->tol || lo->m_max != so->m_max || lo->nprobes < 1 ||
       lo->colour_dist < 0 || lo->colour_dist > 15)
     return GMRF_ERR_INVALID;
+  if (p->sp && lo->colour_dist != 0) return GMRF_ERR_UNSUPPORTED;
   const size_t n = p->g.n, es = esize(p);
   const int m_max = so->m_max, nslots = m_max + 1;
   const int P = lo->colour_dist + 1;
@@ -763,7 +841,8 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
   const bool x_dev = is_device_ptr(x_out);
   const bool z_dev = so->z_in && is_device_ptr(so->z_in);
   const bool r_dev = lo->probes_in && is_device_ptr(lo->probes_in);
-  const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) + n * es : 0);
+  const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) + n * es : 0) +
+                       (sparse_f(p) ? n * es : 0);
   int chunk = batch_size(p, total, nslots, m_max, true, extra);
   if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
   if (chunk < 1) return GMRF_ERR_OOM;
@@ -809,7 +888,14 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
         CKR(ensure(p->stage, (size_t)nsc * n * es, p->ws));
         xdst = p->stage.p;
       }
-      if (p->precond == GMRF_PREC_NONE) {
+      if (sparse_f(p)) {
+        CKR(ensure(p->work, (size_t)nsc * n * es, p->ws));
+        CK(traced(KC_ASSEMBLE, s, 1,
+                  [&] { return launch_assemble(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
+        CK(traced(KC_PRE_APPLY, s, 1, [&] { return launch_sparse_ops(*p->sp, 2, p->work.p, xdst, nsc, s); }));
+        CK(traced(KC_OTHER, s, 1,
+                  [&] { return launch_scale(p->fp64, xdst, (size_t)nsc * n, 1.0 / std::sqrt(p->tau), s); }));
+      } else if (p->precond == GMRF_PREC_NONE) {
         CK(traced(KC_ASSEMBLE, s, 1, [&] {
           return launch_assemble(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0 / std::sqrt(p->tau), xdst, s);
         }));
@@ -853,7 +939,7 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
 
 int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void* y) {
   if (!p || !v || !y || nvec < 1 || nvec > 65535 || which < 0 || which > 2) return GMRF_ERR_INVALID;
-  if (which > 0 && p->precond == GMRF_PREC_NONE) return GMRF_ERR_INVALID;
+  if (which > 0 && (p->sp ? !sparse_f(p) : p->precond == GMRF_PREC_NONE)) return GMRF_ERR_INVALID;
   const size_t n = p->g.n, es = esize(p), bytes = (size_t)nvec * n * es;
   cudaStream_t s = p->ws;
   CKR(enter(p));
@@ -869,7 +955,15 @@ int gmrf_apply(gmrf_problem* p, int32_t which, int64_t nvec, const void* v, void
     CKR(ensure(p->stage2, bytes, p->ws));
     yout = p->stage2.p;
   }
-  if (which == 0) {
+  if (p->sp) {
+    // 0: tau Q v; 1: A v; 2: tau^{-1/2} F^{-T} v
+    const int mode = which == 0 ? 0 : (which == 1 ? 1 : 2);
+    CK(traced(KC_PRE_APPLY, s, 1, [&] { return launch_sparse_ops(*p->sp, mode, vin, yout, (int)nvec, s); }));
+    if (which != 1) {
+      const double f = which == 0 ? p->tau : 1.0 / std::sqrt(p->tau);
+      CK(traced(KC_OTHER, s, 1, [&] { return launch_scale(p->fp64, yout, (size_t)nvec * n, f, s); }));
+    }
+  } else if (which == 0) {
     CK(traced(KC_STENCIL_STEP, s, 1, [&] {
       return launch_stencil_apply(p->g, p->fp64, p->kappa2.p, p->kappa2_const, vin, yout, (int)nvec, s);
     }));
@@ -1070,6 +1164,7 @@ int noalloc_scratch(void** out) {
 
 extern "C" int gmrf_apply_inv_sqrt_noalloc(gmrf_problem* p, int64_t nvec, const void* v, void* y) {
   if (!p || !v || !y || nvec < 1 || nvec > 65535) return GMRF_ERR_INVALID;
+  if (p->sp) return GMRF_ERR_UNSUPPORTED;
   if (p->precond == GMRF_PREC_NONE) return GMRF_ERR_INVALID;
   if (!is_device_ptr(v) || !is_device_ptr(y)) return GMRF_ERR_INVALID;
   if (precond_apply_scratch_bytes(p->pre, (int)nvec) > (size_t)GMRF_NOALLOC_SCRATCH_BYTES) return GMRF_ERR_INVALID;

@@ -102,6 +102,21 @@ constexpr int kMaxNodes = 384;
 // y stride = m_max.  scratch: >= nvec * kMaxNodes * m_max * 2 doubles.
 cudaError_t launch_tm_inv_sqrt(const LanczosBufs& b, bool fp64, TmNodes* nodes, double* scratch, double* y,
                                cudaStream_t s);
+// sparse.cu -----------------------------------------------------------------
+// A general sparse Q (CSR) with an optional incomplete-Cholesky factor F of
+// the preconditioner M = F F^T (Section 5.2).  Device copies, level schedules.
+struct SparseOp;
+// Validates and copies desc (see gmrf_create_sparse); *logdet_f = 2 sum log F_ii.
+int sparse_create(SparseOp** out, const gmrf_sparse_desc* desc, bool fp64, cudaStream_t s, double* logdet_f);
+void sparse_free(SparseOp* S, cudaStream_t s);
+bool sparse_has_factor(const SparseOp* S);
+int sparse_size(const SparseOp* S);
+// One Lanczos step (Algorithm 1) on A = F^{-1} Q F^{-T} (or on Q without F):
+// one block per vector, the same buffers and state as the lattice steps.
+cudaError_t launch_sparse_step(const SparseOp& S, const LanczosBufs& b, const StepParams& P, cudaStream_t s);
+// nvec vectors [nvec][n]: mode 0 y = Q v, 1 y = A v, 2 y = F^{-T} v, 3 y = F^{-1} v (modes 1-3 need F).
+cudaError_t launch_sparse_ops(const SparseOp& S, int mode, const void* in, void* out, int nvec, cudaStream_t s);
+
 // async.cu: runs what was submitted for p, then joins its worker (gmrf_destroy).
 void async_shutdown(const gmrf_problem* p);
 // y[s] = T_m^{-1} e_1 (linear solve), y and dwork stride = m_max (dwork: nvec * m_max doubles).

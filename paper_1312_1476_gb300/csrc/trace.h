@@ -26,7 +26,8 @@ enum KernelClass {
   KC_ASSEMBLE = 8,      // x = ||z|| V_m y
   KC_PRE_APPLY = 9,     // plain M^{-1/2} / A applies, final M^{-1/2} u
   KC_OTHER = 10,        // scale, convert, field statistics, log det M
-  KC_COUNT = 11
+  KC_SPARSE_STEP = 11,  // Lanczos step with a CSR Q (and incomplete-Cholesky solves)
+  KC_COUNT = 12
 };
 
 void trace_begin(int kc, cudaStream_t s, int nkernels = 1);

@@ -45,6 +45,13 @@ class GmrfDesc(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class GmrfSparseDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("f_rowptr", ctypes.c_void_p), ("f_colind", ctypes.c_void_p),
+                ("f_val", ctypes.c_void_p), ("tau", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class GmrfSampleOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("m_max", ctypes.c_int32), ("nsamples", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("z_in", ctypes.c_void_p), ("check_every", ctypes.c_int32),
@@ -104,6 +111,9 @@ def _load():
         "gmrf_apply_inv_sqrt_noalloc": (ctypes.c_int, [P, ctypes.c_int64, P, P]),
         "gmrf_autotune": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(GmrfTuning)]),
         "gmrf_set_tuning": (ctypes.c_int, [P, ctypes.POINTER(GmrfTuning)]),
+        "gmrf_create_sparse": (ctypes.c_int, [ctypes.POINTER(GmrfSparseDesc), P, ctypes.POINTER(P)]),
+        "gmrf_ichol": (ctypes.c_int, [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                      P, P, P, ctypes.POINTER(ctypes.c_int64)]),
         "gmrf_destroy": (None, [P]),
         "gmrf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -410,7 +420,7 @@ def rng(kind, nvec, n, seed, out, precision="fp32", stream=None):
 
 VSTORE = {"native": 0, "bf16": 1, "none": 2}
 KERNEL_CLASSES = {"stencil_step": 0, "pre_row_fwd": 1, "pre_col": 2, "pre_row_mid": 3, "pre_row_last": 4,
-                  "init": 5, "rng": 6, "tm": 7, "assemble": 8, "pre_apply": 9, "other": 10}
+                  "init": 5, "rng": 6, "tm": 7, "assemble": 8, "pre_apply": 9, "other": 10, "sparse_step": 11}
 
 
 def trace_reset():
@@ -431,3 +441,72 @@ def trace_query(kclass="all"):
     if rc != OK:
         raise GmrfError(rc, "gmrf_trace")
     return ms.value, la.value, ti.value
+
+
+# ---------------------------------------------------------------- sparse Q
+def _csr_parts(Q):
+    """(n, rowptr int64, colind int32, val float64) from a scipy sparse matrix
+    or a (rowptr, colind, val) triple (argument marshalling only)."""
+    if isinstance(Q, tuple):
+        rowptr, colind, val = Q
+    else:
+        Q = Q.tocsr()
+        rowptr, colind, val = Q.indptr, Q.indices, Q.data
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    return len(rowptr) - 1, rowptr, colind, val
+
+
+def ichol(Q, droptol=-1.0, shift=0.0):
+    """Threshold incomplete Cholesky factor F of Q + shift diag(Q) (gmrf_ichol;
+    droptol < 0: IC(0)).  Returns (f_rowptr, f_colind, f_val) CSR arrays."""
+    n, rp, ci, va = _csr_parts(Q)
+    nnz = ctypes.c_int64()
+    f_rowptr = np.zeros(n + 1, dtype=np.int64)
+    rc = _lib.gmrf_ichol(n, _ptr(rp), _ptr(ci), _ptr(va), float(droptol), float(shift), 0, _ptr(f_rowptr), None,
+                         None, ctypes.byref(nnz))
+    if rc != OK:
+        raise GmrfError(rc, "gmrf_ichol (column %d)" % nnz.value if rc == ERR_NOT_SPD else "gmrf_ichol")
+    f_col = np.zeros(nnz.value, dtype=np.int32)
+    f_val = np.zeros(nnz.value, dtype=np.float64)
+    rc = _lib.gmrf_ichol(n, _ptr(rp), _ptr(ci), _ptr(va), float(droptol), float(shift), nnz.value, _ptr(f_rowptr),
+                         _ptr(f_col), _ptr(f_val), ctypes.byref(nnz))
+    if rc != OK:
+        raise GmrfError(rc, "gmrf_ichol")
+    return f_rowptr, f_col, f_val
+
+
+class SparseProblem(Problem):
+    """A general sparse precision tau Q in CSR (gmrf_create_sparse), optionally
+    preconditioned by an incomplete-Cholesky factor F (M = F F^T, Section 5.2).
+    Q and F: scipy sparse matrices or (rowptr, colind, val) triples."""
+
+    def __init__(self, Q, F=None, tau=1.0, precision="fp32", stream=None):
+        n, rp, ci, va = _csr_parts(Q)
+        d = GmrfSparseDesc()
+        d.n = n
+        d.rowptr, d.colind, d.val = _ptr(rp), _ptr(ci), _ptr(va)
+        keep = [rp, ci, va]
+        if F is not None:
+            fn, frp, fci, fva = _csr_parts(F)
+            if fn != n:
+                raise ValueError("F must be n x n")
+            d.f_rowptr, d.f_colind, d.f_val = _ptr(frp), _ptr(fci), _ptr(fva)
+            keep += [frp, fci, fva]
+        else:
+            d.f_rowptr = d.f_colind = d.f_val = None
+        d.tau = float(tau)
+        d.precision = PRECISION[precision]
+        d.reserved = 0
+        self.shape = (n,)
+        self.precision = precision
+        self.n = n
+        self._kappa2 = None
+        self._h = ctypes.c_void_p()
+        rc = _lib.gmrf_create_sparse(ctypes.byref(d), _stream(stream), ctypes.byref(self._h))
+        del keep
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_create_sparse")
+        self._stream = stream
+        self._tickets = []

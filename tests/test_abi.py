@@ -52,6 +52,8 @@ int main(void) {
   printf("%zu %zu\n", offsetof(gmrf_result_info, err_est), offsetof(gmrf_logdet_opts, probes_in));
   printf("%zu %zu %zu\n", sizeof(gmrf_solve_opts), offsetof(gmrf_solve_opts, nrhs),
          offsetof(gmrf_solve_opts, reserved));
+  printf("%zu %zu %zu %zu\n", sizeof(gmrf_sparse_desc), offsetof(gmrf_sparse_desc, f_rowptr),
+         offsetof(gmrf_sparse_desc, tau), offsetof(gmrf_sparse_desc, reserved));
   return 0;
 }
 """
@@ -66,7 +68,8 @@ int main(void) {
     assert vals[4:] == [g.GmrfDesc.kappa2.offset, g.GmrfDesc.tau.offset, g.GmrfDesc.precision.offset,
                         g.GmrfSampleOpts.z_in.offset, g.GmrfResultInfo.err_est.offset,
                         g.GmrfLogdetOpts.probes_in.offset, cs(g.GmrfSolveOpts), g.GmrfSolveOpts.nrhs.offset,
-                        g.GmrfSolveOpts.reserved.offset]
+                        g.GmrfSolveOpts.reserved.offset, cs(g.GmrfSparseDesc), g.GmrfSparseDesc.f_rowptr.offset,
+                        g.GmrfSparseDesc.tau.offset, g.GmrfSparseDesc.reserved.offset]
 
 
 def test_invalid_descriptors_rejected_on_host(g):
