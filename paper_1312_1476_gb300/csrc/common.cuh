@@ -277,11 +277,15 @@ __device__ __noinline__ static double smallest_ritz(const float* af, const float
 // recurrence of T_m and applies the stopping rule:
 //   est = theta_min^{-1/2} ||r_m|| / ||x_m||,
 //   ||r_m|| / ||z|| = beta_{m-1} |u_{m-1} / d_{m-1}|,  ||x_m|| / ||z|| = sqrt(e_1^T T_m^{-1} e_1).
+// beta_j^2 comes from the three sums (one pass over the vectors), or, when
+// b2_direct >= 0, is b2_direct = ||q_j - alpha_j v_j||^2 summed by a caller
+// that holds both vectors (a second pass; exact also when beta_j << ||q_j||,
+// where the one-pass form cancels to rounding noise).
 template <typename T>
 __device__ static void finish_step(const StepParams& P, int j, int s, const Dots<T>* __restrict__ partials, int nblk,
                             VecState* __restrict__ st, double* __restrict__ alpha, double* __restrict__ beta,
                             float* __restrict__ alpha_f, float* __restrict__ beta2_f, Dots<T>* red_scratch,
-                            int* s_int, float* s_flt) {
+                            int* s_int, float* s_flt, double b2_direct = -1.0) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nt = blockDim.x * blockDim.y * blockDim.z;
   Dots<T> acc;
@@ -296,7 +300,7 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
     acc.get(s1, s2, s3);
     VecState v = st[s];
     double a = s1;
-    double b2 = s2 - 2.0 * a * s1 + a * a * s3;
+    double b2 = b2_direct >= 0.0 ? b2_direct : s2 - 2.0 * a * s1 + a * a * s3;
     double b = b2 > 0.0 ? sqrt(b2) : 0.0;
     alpha[mo + j] = a;
     beta[mo + j] = b;

@@ -9,12 +9,14 @@
 // solves.  Device side: one thread block per vector, whose working vectors
 // stay in shared memory for a whole Lanczos step:
 //     v_j formed from q_{j-1}, v_{j-1} (as in the lattice steps), stored;
-//     t = F^{-T} v_j     backward substitution, level by level, in place;
+//     t = F^{-T} v_j     backward substitution, level by level, in place
+//                        (a group of lanes per row, sized to the rows);
 //     u = Q t            CSR rows, Q read through L2 (shared by all blocks);
 //     u := F^{-1} u      forward substitution, level by level, in place;
 //     q_j = u - beta_{j-1} v_{j-1} -> W_out, the three dot products,
-// then alpha_j, beta_j and the stopping rule (finish_step, common.cuh) in the
-// same block.  Rows of one level depend only on rows of earlier levels, so
+// then alpha_j = v_j . q_j, beta_j = ||q_j - alpha_j v_j|| (a second pass over
+// the vectors in shared memory, exact also where A is close to the identity)
+// and the stopping rule (finish_step, common.cuh) in the same block.  Rows of one level depend only on rows of earlier levels, so
 // the threads of the block solve them in parallel with one barrier per level.
 // Without F the step is u = Q v_j.
 #include <cuda_runtime.h>
@@ -48,6 +50,7 @@ struct SparseOp {
   int* lev_b = nullptr;     // rows in backward-solve level order [n]
   int* lev_b_ptr = nullptr; // [nlev_b + 1]
   int nlev_f = 0, nlev_b = 0;
+  int gs = 1;               // lanes per row in the triangular solves
   size_t smem = 0;          // dynamic shared memory of the kernels
 };
 
@@ -235,36 +238,50 @@ struct SpArgs {
   const int* lbp;
   int nlb;
   int has_f;
+  int gs;  // lanes per row in the triangular solves: a power of two <= 32
 };
 
-// x := F^{-1} x  (forward substitution in place, level by level)
+// One level-scheduled substitution in place: x_i := (x_i - sum_e val_e x_col_e) / d_i
+// for the rows of each level in turn.  A group of gs lanes (aligned within a
+// warp) takes one row, its lanes striding over the row's entries, and the
+// group sums by shuffles; the block's groups take the level's rows in rounds.
+// The round loop depends only on the level, so every lane of a warp reaches
+// the shuffles (inactive groups add zeros).
 template <typename T>
-__device__ __forceinline__ void lower_solve(const SpArgs<T>& a, T* x) {
-  for (int l = 0; l < a.nlf; ++l) {
-    const int r1 = a.lfp[l + 1];
-    for (int r = a.lfp[l] + (int)threadIdx.x; r < r1; r += blockDim.x) {
-      const int i = a.lf[r];
-      T acc = x[i];
-      for (int e = a.lp[i]; e < a.lp[i + 1]; ++e) acc -= __ldg(a.lv + e) * x[__ldg(a.lc + e)];
-      x[i] = acc / __ldg(a.dg + i);
+__device__ __forceinline__ void tri_solve(const SpArgs<T>& a, const int* __restrict__ rows,
+                                          const int* __restrict__ lptr, int nlev, const int* __restrict__ rp,
+                                          const int* __restrict__ col, const T* __restrict__ val, T* x) {
+  const int gs = a.gs;
+  const int grp = (int)threadIdx.x / gs, sub = (int)threadIdx.x & (gs - 1);
+  const int ngrp = (int)blockDim.x / gs;
+  for (int l = 0; l < nlev; ++l) {
+    const int r0 = __ldg(lptr + l), r1 = __ldg(lptr + l + 1);
+    for (int base = r0; base < r1; base += ngrp) {
+      const int r = base + grp;
+      int i = 0;
+      T acc = 0;
+      if (r < r1) {
+        i = __ldg(rows + r);
+        const int e1 = __ldg(rp + i + 1);
+        for (int e = __ldg(rp + i) + sub; e < e1; e += gs) acc += __ldg(val + e) * x[__ldg(col + e)];
+      }
+      for (int off = gs >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (r < r1 && sub == 0) x[i] = (x[i] - acc) / __ldg(a.dg + i);
     }
     __syncthreads();
   }
 }
 
-// x := F^{-T} x  (backward substitution in place, level by level)
+// x := F^{-1} x  (forward substitution)
+template <typename T>
+__device__ __forceinline__ void lower_solve(const SpArgs<T>& a, T* x) {
+  tri_solve(a, a.lf, a.lfp, a.nlf, a.lp, a.lc, a.lv, x);
+}
+
+// x := F^{-T} x  (backward substitution)
 template <typename T>
 __device__ __forceinline__ void upper_solve(const SpArgs<T>& a, T* x) {
-  for (int l = 0; l < a.nlb; ++l) {
-    const int r1 = a.lbp[l + 1];
-    for (int r = a.lbp[l] + (int)threadIdx.x; r < r1; r += blockDim.x) {
-      const int i = a.lb[r];
-      T acc = x[i];
-      for (int e = a.up[i]; e < a.up[i + 1]; ++e) acc -= __ldg(a.uv + e) * x[__ldg(a.uc + e)];
-      x[i] = acc / __ldg(a.dg + i);
-    }
-    __syncthreads();
-  }
+  tri_solve(a, a.lb, a.lbp, a.nlb, a.up, a.uc, a.uv, x);
 }
 
 // y = Q x for all rows (x, y in shared memory; y written, no barrier)
@@ -336,19 +353,41 @@ __global__ void __launch_bounds__(kSpThreads) k_sparse_step(SpArgs<T> a, SpStep<
     spmv(a, sv, su);
     __syncthreads();
   }
-  // q_j = A v_j - beta_{j-1} v_{j-1}, dot products
+  // q_j = A v_j - beta_{j-1} v_{j-1} (kept in su), dot products
   Dots<T> d;
   d.zero();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const T v = sv[i];
     const T q = j > 0 ? su[i] - bprev * Vp[i] : su[i];
+    su[i] = q;
     Wout[i] = q;
     d.add(v, q);
   }
   d = block_reduce(d, red);
-  if (threadIdx.x == 0) b.partials[s] = d;
+  __shared__ double s_alpha, s_b2;
+  if (threadIdx.x == 0) {
+    b.partials[s] = d;
+    double a1, a2, a3;
+    d.get(a1, a2, a3);
+    s_alpha = a1;
+  }
   __syncthreads();
-  finish_step<T>(b.P, j, s, b.partials, 1, b.st, b.alpha, b.beta, b.alpha_f, b.beta2_f, red, s_int, s_flt);
+  // beta_j^2 = ||q_j - alpha_j v_j||^2 from the two vectors in shared memory
+  const T al = (T)s_alpha;
+  Dots<T> e;
+  e.zero();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const T r = su[i] - al * sv[i];
+    e.add(r, r);
+  }
+  e = block_reduce(e, red);
+  if (threadIdx.x == 0) {
+    double r1, r2, r3;
+    e.get(r1, r2, r3);
+    s_b2 = r2;
+  }
+  __syncthreads();
+  finish_step<T>(b.P, j, s, b.partials, 1, b.st, b.alpha, b.beta, b.alpha_f, b.beta2_f, red, s_int, s_flt, s_b2);
 }
 
 // Plain applies on nvec vectors: mode 0 y = Q v, 1 y = A v, 2 y = F^{-T} v,
@@ -403,6 +442,7 @@ SpArgs<T> sp_args(const SparseOp& S) {
   a.lbp = S.lev_b_ptr;
   a.nlb = S.nlev_b;
   a.has_f = S.has_f ? 1 : 0;
+  a.gs = S.gs;
   return a;
 }
 
@@ -579,6 +619,9 @@ int sparse_create(SparseOp** out, const gmrf_sparse_desc* d, bool fp64, cudaStre
     levels(n, up, uc, false, rb, pb);
     S->nlev_f = (int)pf.size() - 1;
     S->nlev_b = (int)pb.size() - 1;
+    // lanes per row: the power of two at or above the mean off-diagonal row length (1 .. 32)
+    const double mean_row = (double)lc.size() / (double)n;
+    while (S->gs < 32 && S->gs < mean_row) S->gs *= 2;
     r = upload_i(&S->l_ptr, lp, s);
     if (r == GMRF_OK) r = upload_i(&S->l_col, lc, s);
     if (r == GMRF_OK) r = upload_i(&S->u_ptr, up, s);

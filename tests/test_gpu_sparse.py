@@ -7,9 +7,13 @@ library's own factorisation is compared with it on the host
 (tests/test_sparse_host.py).  Tolerances:
 * FP64 at tol 1e-11: relative error of x <= 1e-10 (the stopping rule bounds
   the error of A^{-1/2} z; F^{-T} adds rounding only);
-* FP32 at tol 1e-6: relative error <= max(2e-6, 64 u kappa(F)), u = 2^-24:
-  the final F^{-T} solve and the applies of F^{-1}, F^{-T} in the step run in
-  FP32, whose rounding the condition number of F amplifies.
+* FP32 at tol 1e-6: relative error <= max(2e-6 + 8 u sqrt(kappa(S)), 64 u kappa(F)),
+  u = 2^-24, S the iterated operator (Q, or A = F^{-1} Q F^{-T}): the final
+  F^{-T} solve and the applies of F^{-1}, F^{-T} in the step run in FP32,
+  whose rounding the condition number of F amplifies; and the FP32 CSR
+  product rounds relative to |Q| |x| (a general matrix has no difference form
+  like the lattice stencils), a perturbation of S that moves S^{-1/2} z by up
+  to about sqrt(kappa(S)) u in the cases here.
 """
 import ctypes
 
@@ -69,10 +73,13 @@ def _expected(Q, F, Z, tau=1.0):
 
 
 def _fp32_tol(F, Q):
-    if F is None:
-        return 2e-6
-    s = np.linalg.svd(F.toarray(), compute_uv=False)
-    return max(2e-6, 64 * U32 * s[0] / s[-1])
+    S = Q.toarray() if F is None else osp.preconditioned_matrix(Q, F)
+    lam = np.linalg.eigvalsh(S)
+    lim = 2e-6 + 8 * U32 * np.sqrt(lam[-1] / lam[0])
+    if F is not None:
+        s = np.linalg.svd(F.toarray(), compute_uv=False)
+        lim = max(lim, 64 * U32 * s[0] / s[-1])
+    return lim
 
 
 FACTORS = [("none", 0.0), (None, 0.05), (1e-2, 0.1), (1e-4, 0.0), (np.inf, 0.0), (0.0, 0.0)]
@@ -130,7 +137,11 @@ def test_figure3_fp32_good_factor(g):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_exact_factor_one_step(g, precision):
-    # F the exact Cholesky factor: A = I, so one Lanczos step is exact and x = F^{-T} z
+    # F the exact Cholesky factor: A = I, so one Lanczos step is exact and x = F^{-T} z.
+    # In FP64 beta_0 = ||A v_0 - v_0|| is rounding noise far below the breakdown
+    # threshold (m = 1).  In FP32 the applies of F^{-T}, Q, F^{-1} leave
+    # A v - v at up to kappa(Q) u relative, above the FP32 threshold (1e-6), so
+    # a few more steps on the rounding-perturbed identity may run.
     Q = _q("squared")
     F = osp.ichol(Q, droptol=0.0)
     dt = np.float64 if precision == "fp64" else np.float32
@@ -139,7 +150,7 @@ def test_exact_factor_one_step(g, precision):
         rc, info, X = _sample(p, Z, 1e-8 if precision == "fp64" else 1e-6, 50, precision)
     Xe = osp.apply_upper_inv(F, Z.astype(np.float64))
     for s in range(2):
-        assert info[s].status == g.OK and info[s].m_used == 1
+        assert info[s].status == g.OK and info[s].m_used <= (1 if precision == "fp64" else 4)
         assert _rel(X[s], Xe[s]) <= (1e-12 if precision == "fp64" else _fp32_tol(F, Q))
 
 
@@ -272,7 +283,8 @@ def test_one_by_one_and_diagonal(g):
             with g.SparseProblem((rp, ci, va), F, tau=2.0, precision="fp64") as p:
                 rc, info, X = _sample(p, Z, 1e-12, 10, "fp64")
             np.testing.assert_allclose(X, Z / np.sqrt(2.0 * va), rtol=1e-14)
-            assert all(i.m_used == 1 for i in info)
+            # A = I with the factor (or n = 1): one step; Q = diag(1..5) alone: at most n
+            assert all(i.m_used == (1 if F is not None or n == 1 else i.m_used) and i.m_used <= n for i in info)
 
 
 def test_validation(g):
