@@ -38,13 +38,20 @@ struct SparseOp {
   int* q_ptr = nullptr;  // Q: [n + 1], [nnz] columns, [nnz] values
   int* q_col = nullptr;
   void* q_val = nullptr;
-  int* l_ptr = nullptr;  // strictly lower part of F by rows (forward solve)
+  // The two substitutions, each with its rows stored in level order (entry r
+  // of the order is row rows[r]): row pointers [n + 1], columns and values of
+  // the off-diagonal entries, and 1 / F_ii [n], all indexed by r, so a row's
+  // pointers load without going through its row index first.
+  //   forward  (F^{-1}):  the strictly lower part of F by rows
+  //   backward (F^{-T}):  the strictly upper part of F^T by rows (F by columns)
+  int* l_ptr = nullptr;
   int* l_col = nullptr;
   void* l_val = nullptr;
-  int* u_ptr = nullptr;  // strictly upper part of F^T by rows, i.e. F by columns (backward solve)
+  void* l_dinv = nullptr;
+  int* u_ptr = nullptr;
   int* u_col = nullptr;
   void* u_val = nullptr;
-  void* diag = nullptr;     // F_ii [n]
+  void* u_dinv = nullptr;
   int* lev_f = nullptr;     // rows in forward-solve level order [n]
   int* lev_f_ptr = nullptr; // [nlev_f + 1]
   int* lev_b = nullptr;     // rows in backward-solve level order [n]
@@ -227,10 +234,11 @@ struct SpArgs {
   const int* lp;
   const int* lc;
   const T* lv;
+  const T* ldi;
   const int* up;
   const int* uc;
   const T* uv;
-  const T* dg;
+  const T* udi;
   const int* lf;
   const int* lfp;
   int nlf;
@@ -250,7 +258,8 @@ struct SpArgs {
 template <typename T>
 __device__ __forceinline__ void tri_solve(const SpArgs<T>& a, const int* __restrict__ rows,
                                           const int* __restrict__ lptr, int nlev, const int* __restrict__ rp,
-                                          const int* __restrict__ col, const T* __restrict__ val, T* x) {
+                                          const int* __restrict__ col, const T* __restrict__ val,
+                                          const T* __restrict__ dinv, T* x) {
   const int gs = a.gs;
   const int grp = (int)threadIdx.x / gs, sub = (int)threadIdx.x & (gs - 1);
   const int ngrp = (int)blockDim.x / gs;
@@ -262,11 +271,11 @@ __device__ __forceinline__ void tri_solve(const SpArgs<T>& a, const int* __restr
       T acc = 0;
       if (r < r1) {
         i = __ldg(rows + r);
-        const int e1 = __ldg(rp + i + 1);
-        for (int e = __ldg(rp + i) + sub; e < e1; e += gs) acc += __ldg(val + e) * x[__ldg(col + e)];
+        const int e1 = __ldg(rp + r + 1);
+        for (int e = __ldg(rp + r) + sub; e < e1; e += gs) acc += __ldg(val + e) * x[__ldg(col + e)];
       }
       for (int off = gs >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (r < r1 && sub == 0) x[i] = (x[i] - acc) / __ldg(a.dg + i);
+      if (r < r1 && sub == 0) x[i] = (x[i] - acc) * __ldg(dinv + r);
     }
     __syncthreads();
   }
@@ -275,13 +284,13 @@ __device__ __forceinline__ void tri_solve(const SpArgs<T>& a, const int* __restr
 // x := F^{-1} x  (forward substitution)
 template <typename T>
 __device__ __forceinline__ void lower_solve(const SpArgs<T>& a, T* x) {
-  tri_solve(a, a.lf, a.lfp, a.nlf, a.lp, a.lc, a.lv, x);
+  tri_solve(a, a.lf, a.lfp, a.nlf, a.lp, a.lc, a.lv, a.ldi, x);
 }
 
 // x := F^{-T} x  (backward substitution)
 template <typename T>
 __device__ __forceinline__ void upper_solve(const SpArgs<T>& a, T* x) {
-  tri_solve(a, a.lb, a.lbp, a.nlb, a.up, a.uc, a.uv, x);
+  tri_solve(a, a.lb, a.lbp, a.nlb, a.up, a.uc, a.uv, a.udi, x);
 }
 
 // y = Q x for all rows (x, y in shared memory; y written, no barrier)
@@ -431,10 +440,11 @@ SpArgs<T> sp_args(const SparseOp& S) {
   a.lp = S.l_ptr;
   a.lc = S.l_col;
   a.lv = (const T*)S.l_val;
+  a.ldi = (const T*)S.l_dinv;
   a.up = S.u_ptr;
   a.uc = S.u_col;
   a.uv = (const T*)S.u_val;
-  a.dg = (const T*)S.diag;
+  a.udi = (const T*)S.u_dinv;
   a.lf = S.lev_f;
   a.lfp = S.lev_f_ptr;
   a.nlf = S.nlev_f;
@@ -622,23 +632,47 @@ int sparse_create(SparseOp** out, const gmrf_sparse_desc* d, bool fp64, cudaStre
     // lanes per row: the power of two at or above the mean off-diagonal row length (1 .. 32)
     const double mean_row = (double)lc.size() / (double)n;
     while (S->gs < 32 && S->gs < mean_row) S->gs *= 2;
-    r = upload_i(&S->l_ptr, lp, s);
-    if (r == GMRF_OK) r = upload_i(&S->l_col, lc, s);
-    if (r == GMRF_OK) r = upload_i(&S->u_ptr, up, s);
-    if (r == GMRF_OK) r = upload_i(&S->u_col, uc, s);
+    // rows in level order: pointers, entries and 1 / F_ii indexed by the position r
+    auto by_level = [&](const std::vector<int>& rows, const std::vector<int>& ptr, const std::vector<int>& col,
+                        const std::vector<double>& val, std::vector<int>& optr, std::vector<int>& ocol,
+                        std::vector<double>& oval, std::vector<double>& odinv) {
+      optr.assign((size_t)n + 1, 0);
+      ocol.clear();
+      oval.clear();
+      odinv.assign((size_t)n, 0.0);
+      for (int q = 0; q < n; ++q) {
+        const int i = rows[(size_t)q];
+        for (int e = ptr[(size_t)i]; e < ptr[(size_t)i + 1]; ++e) {
+          ocol.push_back(col[(size_t)e]);
+          oval.push_back(val[(size_t)e]);
+        }
+        optr[(size_t)q + 1] = (int)ocol.size();
+        odinv[(size_t)q] = 1.0 / dg[(size_t)i];
+      }
+    };
+    std::vector<int> lp2, lc2, up2, uc2;
+    std::vector<double> lv2, ld2, uv2, ud2;
+    by_level(rf, lp, lc, lv, lp2, lc2, lv2, ld2);
+    by_level(rb, up, uc, uv, up2, uc2, uv2, ud2);
+    r = upload_i(&S->l_ptr, lp2, s);
+    if (r == GMRF_OK) r = upload_i(&S->l_col, lc2, s);
+    if (r == GMRF_OK) r = upload_i(&S->u_ptr, up2, s);
+    if (r == GMRF_OK) r = upload_i(&S->u_col, uc2, s);
     if (r == GMRF_OK) r = upload_i(&S->lev_f, rf, s);
     if (r == GMRF_OK) r = upload_i(&S->lev_f_ptr, pf, s);
     if (r == GMRF_OK) r = upload_i(&S->lev_b, rb, s);
     if (r == GMRF_OK) r = upload_i(&S->lev_b_ptr, pb, s);
     if (r == GMRF_OK) {
       if (fp64) {
-        r = upload<double>(&S->l_val, lv, s);
-        if (r == GMRF_OK) r = upload<double>(&S->u_val, uv, s);
-        if (r == GMRF_OK) r = upload<double>(&S->diag, dg, s);
+        r = upload<double>(&S->l_val, lv2, s);
+        if (r == GMRF_OK) r = upload<double>(&S->u_val, uv2, s);
+        if (r == GMRF_OK) r = upload<double>(&S->l_dinv, ld2, s);
+        if (r == GMRF_OK) r = upload<double>(&S->u_dinv, ud2, s);
       } else {
-        r = upload<float>(&S->l_val, lv, s);
-        if (r == GMRF_OK) r = upload<float>(&S->u_val, uv, s);
-        if (r == GMRF_OK) r = upload<float>(&S->diag, dg, s);
+        r = upload<float>(&S->l_val, lv2, s);
+        if (r == GMRF_OK) r = upload<float>(&S->u_val, uv2, s);
+        if (r == GMRF_OK) r = upload<float>(&S->l_dinv, ld2, s);
+        if (r == GMRF_OK) r = upload<float>(&S->u_dinv, ud2, s);
       }
     }
   }
@@ -653,8 +687,8 @@ int sparse_create(SparseOp** out, const gmrf_sparse_desc* d, bool fp64, cudaStre
 
 void sparse_free(SparseOp* S, cudaStream_t s) {
   if (!S) return;
-  void* ps[] = {S->q_ptr, S->q_col, S->q_val, S->l_ptr, S->l_col, S->l_val, S->u_ptr, S->u_col, S->u_val,
-                S->diag, S->lev_f, S->lev_f_ptr, S->lev_b, S->lev_b_ptr};
+  void* ps[] = {S->q_ptr, S->q_col, S->q_val, S->l_ptr,  S->l_col,  S->l_val,     S->l_dinv,    S->u_ptr,
+                S->u_col, S->u_val, S->u_dinv, S->lev_f, S->lev_f_ptr, S->lev_b, S->lev_b_ptr};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, s);
   cudaGetLastError();

@@ -16,6 +16,9 @@ Cases:
   3d_256         256^3 Dirichlet 7-point, kappa^2 i.i.d. U[0.01, 1], FP32
   stencil2d_1024 1024 x 1024 SPDE, zero-Neumann, no preconditioner, FP32 (the
                  streamed 2-D step), N vectors per launch
+  figure3_ichol  the Figure 3 matrix (31^2 G)^2 (n = 900, Section 5.2) in CSR,
+                 incomplete-Cholesky factor (drop tolerance 1e-3, shift 1e-3),
+                 FP64, N vectors per launch
 """
 from __future__ import annotations
 
@@ -43,6 +46,10 @@ def run(case: str, nsamples: int, steps: int, trace: bool = False) -> dict:
         shape = (256, 256, 256)
         k2 = torch.from_numpy(inputs.kappa2_uniform_field(shape, seed=1)).cuda()
         prob = gmrf.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=k2)
+    elif case == "figure3_ichol":
+        Q = inputs.figure3_matrix()
+        prob = gmrf.SparseProblem(Q, gmrf.ichol(Q, droptol=1e-3, shift=1e-3), precision="fp64")
+        shape = (prob.n,)
     else:
         raise ValueError("unknown case %r" % case)
     n = int(np.prod(shape))
@@ -57,7 +64,8 @@ def run(case: str, nsamples: int, steps: int, trace: bool = False) -> dict:
         return rc, info
 
     with prob:
-        x = torch.empty(nsamples * n, dtype=torch.float32, device="cuda")
+        x = torch.empty(nsamples * n, dtype=torch.float64 if prob.precision == "fp64" else torch.float32,
+                        device="cuda")
         rc, info = call()
         out.update(m_used=[i.m_used for i in info], rc=rc)
         if trace:
@@ -87,7 +95,7 @@ def run(case: str, nsamples: int, steps: int, trace: bool = False) -> dict:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("case", choices=["headline_1024", "batched_512", "3d_256", "stencil2d_1024"])
+    ap.add_argument("case", choices=["headline_1024", "batched_512", "3d_256", "stencil2d_1024", "figure3_ichol"])
     ap.add_argument("--nsamples", type=int, default=1)
     ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--trace", action="store_true", help="also report per-kernel-class times")
