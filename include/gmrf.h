@@ -442,8 +442,9 @@ int gmrf_create_sparse(const gmrf_sparse_desc* desc, void* stream, gmrf_problem*
  *       droptol <  0 (IC(0)):  A'_ij == 0      (no fill outside Q's pattern)
  *       droptol >= 0 (ICT):    |w_i| < droptol * sum_{i >= j} |A'_ij|
  * (the paper gives no dropping rule; this one does not depend on the scale
- * of Q).  droptol = 0 gives the exact Cholesky factor, a very large droptol
- * the diagonal sqrt(diag A').  Q: CSR as in gmrf_sparse_desc.
+ * of Q); entries that are exactly zero are not stored.  droptol = 0 gives
+ * the exact Cholesky factor, a very large droptol the diagonal
+ * sqrt(diag A').  Q: CSR as in gmrf_sparse_desc.
  * Output F in CSR: f_rowptr[n+1], and per row its columns ascending with the
  * diagonal last, in f_colind / f_val.
  *   Size query: with f_colind == NULL or f_val == NULL only *f_nnz (and

@@ -211,7 +211,8 @@ bool ichol_columns(const SortedRows& r, int64_t n, double droptol, double shift,
     for (int32_t i : touched) {
       if (i == j) continue;
       const double wi = w[(size_t)i];
-      const bool keep = ic0 ? (in_a[(size_t)i] == j) : !(std::fabs(wi) < thr);
+      // exact zeros (a cancelled update, an explicit zero of Q) are not stored
+      const bool keep = wi != 0.0 && (ic0 ? (in_a[(size_t)i] == j) : !(std::fabs(wi) < thr));
       if (keep) cj.emplace_back(i, wi / d);
     }
     if (!cj.empty()) {

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from oracle import exact, sparse as osp, stencil
+from oracle import exact, lanczos as olz, sparse as osp, stencil
 from paper_1312_1476_gb300 import inputs
 
 
@@ -144,3 +144,18 @@ def test_triangular_helpers_invert_the_factor():
     v = np.random.default_rng(8).standard_normal((3, Q.shape[0]))
     np.testing.assert_allclose((F @ osp.apply_lower_inv(F, v).T).T, v, atol=1e-10)
     np.testing.assert_allclose((F.T @ osp.apply_upper_inv(F, v).T).T, v, atol=1e-10)
+
+
+@pytest.mark.parametrize("droptol,shift", [(None, 0.01), (1e-3, 1e-3)])
+def test_krylov_route_matches_dense_map_figure3(droptol, shift):
+    # an independent route to the same x: Algorithm 1 (FP64, full reorthogonalisation)
+    # on A = F^{-1} Q F^{-T}, then F^{-T}, against the dense eigendecomposition map
+    Q = osp.csr(*inputs.figure3_matrix())
+    F = osp.ichol(Q, droptol=droptol, shift=shift)
+    A = osp.preconditioned_matrix(Q, F)
+    z = inputs.gaussian_vectors(1, Q.shape[0], seed=6, dtype=np.float64)[0]
+    u, m, _, _ = olz.adaptive_sample(lambda v: A @ v, z, 1e-12, 600, reorth=True)
+    x = osp.apply_upper_inv(F, u)[0]
+    xe = osp.sample_precond_dense(Q, F, z)[0]
+    assert np.linalg.norm(x - xe) <= 1e-10 * np.linalg.norm(xe)
+    assert m < 200

@@ -114,3 +114,31 @@ def test_invalid_inputs():
     va4 = va.copy()
     va4[d] = 0.0
     assert _call(rp, ci, va4)[0] == gmrf.ERR_INVALID
+
+
+def test_explicit_zeros_and_unsorted_rows():
+    # explicit zeros are outside Q's pattern for IC(0) on both sides, and the
+    # column order within a row does not matter
+    rp, ci, va = inputs.random_sparse_spd(8, 7, seed=5, squared=True)
+    Q = osp.csr(rp, ci, va).tolil()
+    n = Q.shape[0]
+    rng = np.random.default_rng(1)
+    for _ in range(20):  # symmetric explicit zeros at positions outside the pattern
+        i, j = rng.integers(0, n, 2)
+        if i != j and Q[i, j] == 0:
+            Q[i, j] = 1.0
+            Q[j, i] = 1.0
+    Qz = Q.tocsr()
+    Qz.data[Qz.data == 1.0] = 0.0  # stored, but zero
+    rows = []
+    for i in range(n):  # reverse the column order of every row
+        s, e = Qz.indptr[i], Qz.indptr[i + 1]
+        rows.append((Qz.indices[s:e][::-1], Qz.data[s:e][::-1]))
+    ci2 = np.concatenate([r[0] for r in rows]).astype(np.int32)
+    va2 = np.concatenate([r[1] for r in rows])
+    Fl = osp.csr(*gmrf.ichol((Qz.indptr.astype(np.int64), ci2, va2), droptol=-1.0, shift=0.1))
+    Fo = osp.ichol(Qz, droptol=None, shift=0.1)
+    _compare(Fl, Fo)
+    for dt in (0.0, 1e-3):
+        _compare(osp.csr(*gmrf.ichol((Qz.indptr.astype(np.int64), ci2, va2), droptol=dt, shift=0.1)),
+                 osp.ichol(Qz, droptol=dt, shift=0.1))
