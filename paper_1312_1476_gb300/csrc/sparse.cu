@@ -250,8 +250,8 @@ struct SpArgs {
   int gs;  // lanes per row in the triangular solves: a power of two <= 32
 };
 
-// One level-scheduled substitution in place: x_i := (x_i - sum_e val_e x_col_e) / d_i
-// for the rows of each level in turn.  A group of gs lanes (aligned within a
+// One level-scheduled substitution in place: x_i := (x_i - sum_e val_e x_col_e) * (1 / d_i)
+// for the rows of each level in turn (the reciprocal pivots are stored).  A group of gs lanes (aligned within a
 // warp) takes one row, its lanes striding over the row's entries, and the
 // group sums by shuffles; the block's groups take the level's rows in rounds.
 // The round loop depends only on the level, so every lane of a warp reaches
