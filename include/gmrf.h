@@ -307,13 +307,15 @@ int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t 
 int gmrf_trace(int32_t op, int32_t kclass, double* total_ms, int64_t* launches, int64_t* timed);
 
 /* Allocation-free y = M^{-1/2} v (the operation of gmrf_apply with which = 2).
- * The paper has no counterpart: this exists for callers that cannot allocate
- * device memory during the call -- code that is inside CUDA stream capture
- * (cudaMalloc is not allowed there), code that hands all device memory to its
- * own pool or allocator and forbids allocations behind its back, and
- * latency-critical loops that cannot afford an allocation.  gmrf_apply may
- * grow the problem's transform workspace with cudaMalloc on first use; this
- * entry point calls no cudaMalloc, cudaFree or allocating library routine.
+ * The paper has no counterpart.  It exists for callers that must not allocate
+ * device memory while they call into this library: applications that hand
+ * all device memory to their own pool or allocator up front and forbid
+ * allocations behind its back (an allocation outside the pool can fail, or
+ * push a tight memory budget over its limit), and latency-critical loops that
+ * cannot afford the synchronisation and latency of an allocation.
+ * gmrf_apply may grow the problem's transform workspace with cudaMalloc on
+ * first use; this entry point calls no cudaMalloc, cudaFree or allocating
+ * library routine.
  *
  * Its transform scratch is one library-wide static device array of
  * GMRF_NOALLOC_SCRATCH_BYTES (32 MiB), held on every GPU that loads the
@@ -322,6 +324,8 @@ int gmrf_trace(int32_t op, int32_t kclass, double* total_ms, int64_t* launches, 
  * GMRF_ERR_INVALID (a 1024 x 1024 FP32 grid fits 7 vectors per call).
  * v and y: device pointers, [nvec][n] of the problem's precision; host
  * pointers return GMRF_ERR_INVALID.  The problem needs a preconditioner.
+ * The device the problem was created on must be the current device
+ * (otherwise GMRF_ERR_INVALID).  The call returns once y is complete.
  *
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, once per device, with that device current); make

@@ -19,10 +19,14 @@ Counter layout used on both sides:
   word (e // 32) % 4; +1 if set, -1 otherwise.
 
 Parity: the raw 32-bit words are compared bit-exactly with the device; the
-Gaussian values (device FP32 libm vs this FP64 transform) to ~1e-6.  No
-published known-answer vectors are in the repository, so the word stream is
-pinned by statistical tests only (tests/test_oracle_philox.py): parity of the
-word stream to the published generator itself is unpinned.
+Gaussian values (device FP32 libm vs this FP64 transform) to ~1e-6.  The word
+stream is pinned bit for bit to an independent implementation of the same
+generator in a library of the image (Triton's tl.philox, run on the CPU by its
+interpreter), and the transforms by statistical tests
+(tests/test_oracle_philox.py).
+
+This module is test infrastructure: only the tests, the smoke check and the
+benchmark's CPU baseline use it.
 """
 from __future__ import annotations
 

@@ -111,6 +111,7 @@ struct gmrf_problem {
   double kappa2_const = 0.0;
   double kbar2 = 0.0;
   double logdet_M = 0.0;  // log det of the tau-free preconditioner (B_bar^p)
+  int device = 0;                  // the device current at create (the problem's memory lives there)
   cudaStream_t stream = nullptr;   // the caller's stream
   cudaStream_t ws = nullptr;       // the library's work stream (graphs are captured on it)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -440,6 +441,11 @@ int gmrf_create(const gmrf_desc* d, void* stream, gmrf_problem** out) {
   p->tau = d->tau;
   p->kappa2_const = d->kappa2_const;
   p->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return GMRF_ERR_CUDA;
+  }
   auto fail = [&](int code) {
     gmrf_destroy(p);
     return code;
@@ -534,6 +540,11 @@ int gmrf_create_sparse(const gmrf_sparse_desc* d, void* stream, gmrf_problem** o
   p->fp64 = d->precision == GMRF_FP64;
   p->tau = d->tau;
   p->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return GMRF_ERR_CUDA;
+  }
   auto fail = [&](int code) {
     gmrf_destroy(p);
     return code;
@@ -1132,7 +1143,9 @@ int gmrf_autotune(gmrf_problem* p, int32_t nvec_max, gmrf_tuning* out) {
 // of GMRF_NOALLOC_SCRATCH_BYTES.  Every GPU that loads the library holds it
 // until the process exits.  In host code the symbol is only a stand-in, so
 // its device address is looked up with cudaGetSymbolAddress once per device,
-// with that device current, on the first call made on it.
+// on the first call for a problem of that device; the entry point checks
+// first that this device is the current one, so the lookup runs with it
+// current.
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GMRF_NOALLOC_SCRATCH_BYTES];
@@ -1141,12 +1154,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};
 
-int noalloc_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return GMRF_ERR_CUDA;
-  }
+// dev must be the current device.
+int noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return GMRF_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void* ptr = nullptr;
@@ -1168,8 +1178,14 @@ extern "C" int gmrf_apply_inv_sqrt_noalloc(gmrf_problem* p, int64_t nvec, const 
   if (p->precond == GMRF_PREC_NONE) return GMRF_ERR_INVALID;
   if (!is_device_ptr(v) || !is_device_ptr(y)) return GMRF_ERR_INVALID;
   if (precond_apply_scratch_bytes(p->pre, (int)nvec) > (size_t)GMRF_NOALLOC_SCRATCH_BYTES) return GMRF_ERR_INVALID;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRF_ERR_CUDA;
+  }
+  if (cur != p->device) return GMRF_ERR_INVALID;  // the problem's device must be current
   void* scratch = nullptr;
-  CKR(noalloc_scratch(&scratch));
+  CKR(noalloc_scratch(p->device, &scratch));
   cudaStream_t s = p->ws;
   CKR(enter(p));
   // the spectrum is fully written by the forward row pass before it is read:

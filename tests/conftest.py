@@ -11,6 +11,10 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: test that takes more than a few seconds")
+    # the library is compiled in-tree (nvcc cross-compiles without a GPU); test
+    # modules that import the binding at collection need it to exist
+    from paper_1312_1476_gb300 import _build
+    _build.build()
 
 
 def pytest_collection_modifyitems(config, items):

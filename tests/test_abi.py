@@ -93,3 +93,4 @@ def test_invalid_descriptors_rejected_on_host(g):
     assert lib.gmrf_submit_sample(None, None, None, None, None) == g.ERR_INVALID
     assert lib.gmrf_poll(None, 1, None, None) == g.ERR_INVALID and lib.gmrf_wait(None, 1, None) == g.ERR_INVALID
     assert g.strerror(g.ERR_NOT_SPD).startswith("operator")
+    assert g.strerror(g.ERR_TIMEOUT) == "device wait timed out"

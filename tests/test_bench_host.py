@@ -74,3 +74,11 @@ def test_traffic_figures_are_keyed_to_the_kernel_sources(tmp_path, monkeypatch):
     assert bench.traffic_from_profile("pre_col") == rec["bytes_per_launch"]["pre_col"]
     monkeypatch.setattr(bench, "kernel_sources_sha1", lambda: "0" * 40)
     assert bench.traffic_from_profile("pre_col") is None
+
+
+def test_stencil_step_bytes_count_the_field_once_per_launch():
+    # 16 vectors of 256^3 in one launch: (16 + 4/16) n bytes per vector-step
+    n = 256 ** 3
+    assert bench.stencil_step_bytes(n, 16, 1) == 16 * (16 + 4 / 16) * n
+    # one vector per launch: 20 n, the single-vector rule
+    assert bench.stencil_step_bytes(n, 7, 7) == 20 * n * 7

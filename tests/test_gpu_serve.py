@@ -29,7 +29,7 @@ def test_alone_equals_mix(tune):
         assert srv.tuning and all(t["block_width"] >= 1 for t in srv.tuning.values())
     mixed, metrics = srv.serve(reqs, realtime=False)
     assert metrics["requests"] == len(reqs)
-    assert all(r.status in (0, -3) for r in mixed)
+    assert all(r.status == 0 for r in mixed), [(r.rid, r.kind, r.shape, r.status) for r in mixed if r.status]
     kinds = {r.kind for r in reqs}
     assert kinds == {"sample", "logdet", "solve"}
     targets = sorted({0, 5, 11} | {min(i for i, r in enumerate(reqs) if r.kind == k) for k in kinds})

@@ -1,10 +1,10 @@
 """GPU test of gmrf_apply_inv_sqrt_noalloc, the allocation-free variant of
-gmrf_apply(which = 2) for callers that cannot allocate device memory during
-the call (for instance inside CUDA stream capture, or under an external
-memory pool).  Its output must equal the allocating entry point's, on two
-calls in a row that share the library's static scratch array.  This file is
-collected last so that a run stopping at the first failure has already run
-every other test."""
+gmrf_apply(which = 2) for callers that must not allocate device memory during
+the call (an application that routes all device memory through its own pool,
+or a latency-critical loop).  Its output must equal the allocating entry
+point's, on two calls in a row that share the library's static scratch array.
+This file is collected last so that a run stopping at the first failure has
+already run every other test."""
 import ctypes
 
 import numpy as np
