@@ -274,6 +274,65 @@ int gmrf_submit_solve(gmrf_problem* p, const gmrf_solve_opts* opts, const void* 
 int gmrf_poll(gmrf_problem* p, int64_t ticket, int32_t* done, int32_t* result);
 int gmrf_wait(gmrf_problem* p, int64_t ticket, int32_t* result);
 
+/* ---- Continuous-batching server --------------------------------------------
+ * The samples of Algorithm 1 and the probes of Section 6 are independent
+ * Lanczos runs, so the vectors of many requests can share every launch.  A
+ * server keeps the Lanczos state of `nslots` vectors of one problem resident
+ * on the device (bases V_m, alpha/beta, per-vector state) and runs one CUDA
+ * graph of check_every steps over all slots per gmrf_server_step.  Between
+ * replays it admits waiting vectors into free slots (requests first come,
+ * first served; a request may be admitted a part at a time while other slots
+ * are in mid-iteration), and finishes each vector as soon as it stops: a
+ * sample gets T_m^{-1/2} e_1, x = ||z|| V_m y (then M^{-1/2}) and the
+ * accuracy check of gmrf_sample, a probe its quadrature term.  A request is
+ * complete when its last vector is; a log det then gets the reduction of
+ * gmrf_logdet over its probes.  The paper's method has no server; this is the
+ * serving pattern of this library.
+ *
+ * Results: every result is bitwise the one the synchronous calls return for
+ * the same request: a sample request (kind 0, count vectors, seed, tau) gives
+ * the x and info of gmrf_sample(nsamples = count, seed, z_in = NULL,
+ * v_storage NATIVE) on a problem whose tau is this problem's tau times the
+ * request's tau; a log-det request (kind 1, count probes) gives the logdet,
+ * std_err and info of gmrf_logdet(nprobes = count, seed, colour_dist 0) on
+ * such a problem.  tol, m_max and check_every are the server's.
+ *
+ * While a server exists the problem serves it alone: the problem's other
+ * calls return GMRF_ERR_INVALID until gmrf_server_destroy (gmrf_destroy
+ * destroys an attached server first).  One host thread at a time per server.
+ * Device memory: the Lanczos buffers of nslots vectors at m_max, allocated by
+ * gmrf_server_create (GMRF_ERR_OOM if they do not fit), plus per-call
+ * workspaces of the finishing steps. */
+typedef struct gmrf_server gmrf_server; /* opaque, library-owned */
+typedef struct {
+  int32_t nslots;      /* vectors resident at once, 1 .. 65535 */
+  int32_t m_max;       /* largest subspace size per vector, 1 .. 8192 */
+  double tol;          /* stopping tolerance of every vector (gmrf_sample's rule), > 0 */
+  int32_t check_every; /* steps per gmrf_server_step (<= 0: 16) */
+  int32_t reserved;    /* must be 0 */
+} gmrf_server_opts;
+int gmrf_server_create(gmrf_problem* p, const gmrf_server_opts* opts, gmrf_server** out);
+/* Queues a request (no device work for samples; a log det allocates its
+ * [count + 2] result array).  kind 0: count samples into x_out, device memory
+ * [count][n] of the problem's precision that must stay valid until the request
+ * has completed; kind 1: a log det with count Rademacher probes (x_out
+ * ignored).  tau > 0 scales the precision (see Results).  *req receives the
+ * request id.  GMRF_ERR_INVALID for a bad kind, count < 1, tau <= 0 or a host
+ * x_out. */
+int gmrf_server_submit(gmrf_server* sv, int32_t kind, int32_t count, uint64_t seed, double tau, void* x_out,
+                       int64_t* req);
+/* Admits, runs one replay of check_every steps over all slots, finishes what
+ * stopped, completes requests.  *active (may be NULL) = vectors running or
+ * waiting afterwards (0: idle).  Synchronises the problem's work stream. */
+int gmrf_server_step(gmrf_server* sv, int32_t* active);
+/* *done = 1 once request req has completed; then *result (may be NULL) = its
+ * worst per-vector status, info [count] (host, may be NULL) the per-vector
+ * records, *logdet / *std_err (may be NULL) its log-det estimate (kind 1), and
+ * the request is forgotten.  GMRF_ERR_INVALID for an unknown id. */
+int gmrf_server_poll(gmrf_server* sv, int64_t req, int32_t* done, int32_t* result, gmrf_result_info* info,
+                     double* logdet, double* std_err);
+void gmrf_server_destroy(gmrf_server* sv);
+
 /* Matrix-free operator applies on nvec vectors of the problem's precision
  * (Section 2's "routine that computes the matrix-vector product"), for
  * testing and for callers composing their own solvers:

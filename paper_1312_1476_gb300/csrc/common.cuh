@@ -159,6 +159,8 @@ __device__ __forceinline__ A block_reduce(A v, A* scratch) {
 struct VecState {
   int status;     // VS_RUNNING, VS_DONE or a negative gmrf error code
   int m;          // completed steps = number of alpha values
+  int m_min;      // the stopping rule may end the iteration only once m >= m_min (0: any m)
+  int pad_;
   double znorm;   // ||z||
   double d_prev;  // LDL^T pivot d_{m-1} of T_m
   double u_prev;  // u_{m-1} = (L^{-1} e_1)_{m-1}
@@ -366,7 +368,7 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
       if (v.status == VS_RUNNING) {
         double est = s_pfac / sqrt(th);
         v.err_est = est;
-        if (est <= P.tol) v.status = VS_DONE;
+        if (est <= P.tol && j + 1 >= v.m_min) v.status = VS_DONE;
         else if (j + 1 >= P.m_max) v.status = GMRF_ERR_NOT_CONVERGED;
       }
       st[s] = v;

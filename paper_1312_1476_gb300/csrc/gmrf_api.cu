@@ -20,18 +20,12 @@
 #include <algorithm>
 #include <vector>
 
-#include "internal.h"
-#include "precond.h"
-#include "trace.h"
+#include "host.h"
 
 using namespace gmrf;
+using namespace host;
 
-namespace {
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
+namespace host {
 
 // Workspaces are stream-ordered allocations on the problem's work stream, so
 // growing or freeing them never synchronises the device (other problems keep
@@ -67,67 +61,9 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-#define CK(x)                               \
-  do {                                      \
-    cudaError_t e_ = (x);                   \
-    if (e_ != cudaSuccess) {                \
-      cudaGetLastError();                   \
-      return GMRF_ERR_CUDA;                 \
-    }                                       \
-  } while (0)
-#define CKR(x)                 \
-  do {                         \
-    int r_ = (x);              \
-    if (r_ != GMRF_OK) return r_; \
-  } while (0)
+}  // namespace host
 
-}  // namespace
-
-// The Lanczos loop's CUDA graph: `c` steps captured once and replayed until
-// every vector has converged (the kernels read the step index from device
-// state).  Keyed by everything the captured launches depend on.
-struct StepGraph {
-  cudaGraphExec_t exec = nullptr;
-  GraphTrace tr;
-  int nvec = -1, nslots = 0, m_max = 0, c = 0, kernels_per_step = 1, zchunk = 0, solve = 0;
-  double tol = 0.0;
-  const void *W0 = nullptr, *V = nullptr, *Vb = nullptr, *st = nullptr, *S = nullptr, *partials = nullptr;
-  const void* Xacc = nullptr;
-  double xscale = 0.0;
-  bool timed = false;
-  void reset() {
-    if (exec) cudaGraphExecDestroy(exec);
-    exec = nullptr;
-    tr.release();
-    nvec = -1;
-  }
-};
-
-struct gmrf_problem {
-  Grid g;
-  int precond = GMRF_PREC_NONE;
-  bool fp64 = false;
-  double tau = 1.0;
-  double kappa2_const = 0.0;
-  double kbar2 = 0.0;
-  double logdet_M = 0.0;  // log det of the tau-free preconditioner (B_bar^p)
-  int device = 0;                  // the device current at create (the problem's memory lives there)
-  cudaStream_t stream = nullptr;   // the caller's stream
-  cudaStream_t ws = nullptr;       // the library's work stream (graphs are captured on it)
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  StepGraph graph;
-  DevBuf kappa2;  // float [n] or empty (constant)
-  PrecondTables pre;
-  SparseOp* sp = nullptr;  // general sparse Q (gmrf_create_sparse), else null
-  // Lanczos workspace (grow-only)
-  DevBuf W0, W1, V, st, alpha, beta, alpha_f, beta2_f, partials, counters, y, scratch, nodes, q, out2, stage,
-      stage2, work, Vb, xacc, accn, solvew;
-  VecState* st_host = nullptr;
-  int st_host_cap = 0;
-  int tune_bw = 0;  // vectors per Lanczos launch (0: as many as fit)
-};
-
-namespace {
+namespace host {
 
 size_t esize(const gmrf_problem* p) { return p->fp64 ? 8 : 4; }
 
@@ -139,6 +75,7 @@ bool sparse_f(const gmrf_problem* p) { return p->sp && sparse_has_factor(p->sp);
 // Order the work stream after the caller's stream (entry) and the caller's
 // stream after the work stream (exit).
 int enter(gmrf_problem* p) {
+  if (p->server && !p->in_server) return GMRF_ERR_INVALID;  // the problem serves its server only
   CK(cudaEventRecord(p->ev_in, p->stream));
   CK(cudaStreamWaitEvent(p->ws, p->ev_in, 0));
   return GMRF_OK;
@@ -161,7 +98,7 @@ int ensure_host_states(gmrf_problem* p, int nvec) {
 // bf16_basis: keep a bfloat16 copy of V_m ([nvec][m_max + 1][n]) for the
 // assembly; the FP32 ring then has nslots = 2.
 int ensure_lanczos(gmrf_problem* p, int nvec, int nslots, int m_max, bool need_tm, LanczosBufs& b,
-                   bool bf16_basis = false) {
+                   bool bf16_basis) {
   const size_t n = p->g.n, es = esize(p);
   CKR(ensure(p->W0, (size_t)nvec * n * es, p->ws));
   CKR(ensure(p->W1, (size_t)nvec * n * es, p->ws));
@@ -262,7 +199,7 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   if (G.exec && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c && G.tol == P.tol &&
       G.W0 == b.W[0] && G.V == b.V && G.Vb == b.Vb && G.st == b.st && G.S == S && G.partials == b.partials &&
       G.timed == timed && G.zchunk == p->g.zchunk && G.Xacc == b.Xacc && G.xscale == b.xscale &&
-      G.solve == P.solve)
+      G.solve == P.solve && G.Xacc2 == b.Xacc2 && G.y1 == b.y && G.y2 == b.y2)
     return GMRF_OK;
   G.reset();
   cudaStream_t s = p->ws;
@@ -297,6 +234,9 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   G.Vb = b.Vb;
   G.zchunk = p->g.zchunk;
   G.Xacc = b.Xacc;
+  G.Xacc2 = b.Xacc2;
+  G.y1 = b.y;
+  G.y2 = b.y2;
   G.xscale = b.xscale;
   G.st = b.st;
   G.S = S;
@@ -306,10 +246,9 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   return GMRF_OK;
 }
 
-int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, int check_every,
-                bool solve = false) {
-  cudaStream_t s = p->ws;
-  CK(traced(KC_INIT, s, 1, [&] { return launch_lanczos_init(p->fp64, p->g.n, b, s); }));
+// init = false continues the vectors whose states were set running again
+// (their bases, q and recurrence state are still in place).
+StepParams step_params(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, bool solve) {
   StepParams P{};
   P.m_max = m_max;
   P.nslots = b.nslots;
@@ -317,6 +256,14 @@ int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, in
   P.tol = tol;
   P.bd_tol = p->fp64 ? 1e-13 : 1e-6;
   P.vb = b.Vb;
+  return P;
+}
+
+int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, int check_every,
+                bool solve, bool init) {
+  cudaStream_t s = p->ws;
+  if (init) CK(traced(KC_INIT, s, 1, [&] { return launch_lanczos_init(p->fp64, p->g.n, b, s); }));
+  const StepParams P = step_params(p, b, tol, m_max, solve);
   const int c = std::min(check_every > 0 ? check_every : 16, m_max);
   if (p->precond != GMRF_PREC_NONE) CKR(precond_prepare(p->pre, b.nvec, s));
   CKR(capture_steps(p, b, P, c));
@@ -359,6 +306,138 @@ LanczosBufs sub_batch(const LanczosBufs& b, int off, int cnt, size_t n, size_t e
   return r;
 }
 
+// ---- accuracy check of samples ------------------------------------------
+// Theorem 1 bounds the error of x_m by lambda_min^{-1/2} ||r_m||, with
+// r_m = z - A u_m the residual of the CG iterate u_m = ||z|| V_m T_m^{-1} e_1
+// (A the iterated operator), and in exact arithmetic the recurrence gives
+// ||r_m|| without forming u_m.  In finite precision the recurrence keeps
+// shrinking while the residual of the computed u_m stops where the rounding of
+// the applies of A leaves it.  So after the iteration the library forms u_m
+// (in the same pass over V_m as x_m), computes r = z - A u_m directly (A in
+// FP64 for an FP32 stencil, whose products cancel heavily on a smooth u_m; in
+// the problem's precision otherwise) and one product t = A r, and estimates
+//     est_direct = sqrt(r^T A^{-1} r) / ||x_m||,
+// the square root of the quadratic form taken from the two-node Gauss-Radau
+// rule of the Lanczos step from r with the node fixed at theta_min (Golub and
+// Meurant: an upper estimate for 1/t when the node is at most lambda_min).
+// In exact arithmetic this is at most the Theorem 1 estimate, since
+// r^T A^{-1} r <= ||r||^2 / lambda_min; with rounding it follows where the
+// residual actually sits in the spectrum (rounding noise in the high modes
+// weighs little, as it does in the error of x_m).  A vector is GMRF_OK only
+// if both estimates are <= tol; err_est reports the larger.
+
+// Bytes per vector of the check's buffers: z and u_cg in the problem's
+// precision, plus A u_cg in it, or u_cg and A u_cg in FP64 for an FP32
+// stencil problem.
+size_t check_bytes_per_vec(const gmrf_problem* p) {
+  const size_t n = p->g.n, es = esize(p);
+  const bool fp64_pair = !p->sp && p->precond == GMRF_PREC_NONE && !p->fp64;
+  return 2 * n * es + (fp64_pair ? 2 * n * sizeof(double) : n * es);
+}
+
+// T_m^{-1} e_1 of the nvec vectors of b into p->ycg (stride m_max).
+int check_tm(gmrf_problem* p, const LanczosBufs& b, cudaStream_t s) {
+  CKR(ensure(p->ycg, sizeof(double) * 2 * (size_t)b.nvec * b.m_max, p->ws));
+  double* ycg = (double*)p->ycg.p;
+  CK(traced(KC_TM, s, 1, [&] { return launch_tm_inv(b, ycg + (size_t)b.nvec * b.m_max, ycg, s); }));
+  return GMRF_OK;
+}
+
+// For nvec vectors z, u [nvec][n] (problem precision, device): r = z - A u
+// and t = A r with A the iterated operator (tau-free); writes (r.r, r.t, t.t)
+// to p->rn[3 s .. 3 s + 2] (device).  u is overwritten.
+int check_residuals(gmrf_problem* p, int nvec, const void* z, void* u, cudaStream_t s) {
+  const size_t n = p->g.n, es = esize(p), cnt = (size_t)nvec * n;
+  CKR(ensure(p->chk, (size_t)nvec * (check_bytes_per_vec(p) - 2 * n * es), p->ws));
+  CKR(ensure(p->rn, (sizeof(double) * 3 + sizeof(Dots<double>) * kResidBlocks) * (size_t)nvec, p->ws));
+  double* out = (double*)p->rn.p;
+  void* part = out + 3 * (size_t)nvec;
+  auto apply = [&](bool fp64, const void* in, void* res) -> cudaError_t {
+    if (p->sp) return launch_sparse_ops(*p->sp, sparse_f(p) ? 1 : 0, in, res, nvec, s);  // A, or Q without F
+    if (p->precond != GMRF_PREC_NONE)
+      return launch_precond_operator(p->pre, p->g, p->fp64, p->kappa2.p, p->kappa2_const, in, res, nvec, s);
+    return launch_stencil_apply(p->g, fp64, p->kappa2.p, p->kappa2_const, in, res, nvec, s);
+  };
+  const int kc = p->sp ? KC_PRE_APPLY : (p->precond != GMRF_PREC_NONE ? KC_PRE_APPLY : KC_STENCIL_STEP);
+  const int kl = p->sp ? 1 : (p->precond != GMRF_PREC_NONE ? 5 : 1);
+  if (!p->sp && p->precond == GMRF_PREC_NONE && !p->fp64) {
+    double* u64 = (double*)p->chk.p;
+    double* r64 = u64 + cnt;
+    CK(traced(KC_OTHER, s, 1, [&] { return launch_convert(true, u, u64, cnt, s); }));
+    CK(traced(kc, s, kl, [&] { return apply(true, u64, r64); }));
+    CK(traced(KC_OTHER, s, 1, [&] { return launch_resid_form(false, z, true, r64, cnt, s); }));
+    CK(traced(kc, s, kl, [&] { return apply(true, r64, u64); }));
+    CK(traced(KC_OTHER, s, 2, [&] { return launch_dots3(true, r64, u64, n, nvec, part, out, s); }));
+  } else {
+    void* r = p->chk.p;
+    CK(traced(kc, s, kl, [&] { return apply(p->fp64, u, r); }));
+    CK(traced(KC_OTHER, s, 1, [&] { return launch_resid_form(p->fp64, z, p->fp64, r, cnt, s); }));
+    CK(traced(kc, s, kl, [&] { return apply(p->fp64, r, u); }));
+    CK(traced(KC_OTHER, s, 2, [&] { return launch_dots3(p->fp64, r, u, n, nvec, part, out, s); }));
+  }
+  return GMRF_OK;
+}
+
+// est_direct of a vector from (r.r, r.t, t.t) and its state (INFINITY when
+// it cannot be formed).
+double direct_estimate(const VecState& v, const double* d3) {
+  const double rr = d3[0];
+  const double xnorm = v.znorm * std::sqrt(v.energy);
+  if (!(xnorm > 0.0) || !std::isfinite(rr)) return INFINITY;
+  if (rr <= 0.0) return 0.0;
+  const double a1 = d3[1] / rr;                            // Rayleigh quotient of r
+  const double b2 = std::max(d3[2] / rr - a1 * a1, 0.0);  // beta_1^2 of the step from r
+  const double node = v.theta;
+  double q;  // estimate of r^T A^{-1} r / r^T r
+  if (!(node > 0.0)) return INFINITY;
+  if (a1 > node * (1.0 + 1e-12)) {
+    const double omega = node + b2 / (a1 - node);
+    q = omega / (a1 * omega - b2);
+  } else {
+    q = 1.0 / std::max(std::min(a1, node), 1e-300);
+  }
+  const double est = std::sqrt(rr * q) / xnorm;
+  return std::isfinite(est) ? est : INFINITY;
+}
+
+// After a check: vectors that stopped on the recurrence estimate (status
+// done, err_est > 0) while est_direct > tol are set running again with a
+// minimum step count m + max(2, m / 8) (in mmin and the state), when more
+// steps can help: est_direct within 20 tol in the first round, falling by 30 %
+// per round after it, at most 3 rounds, m below m_max.  A direct estimate far
+// above tol, or one that stopped falling, is the floor of the arithmetic: the
+// vector keeps its result and the check reports it.  est[s] receives the
+// direct estimates.  Returns whether any vector was resumed.
+bool check_resume(VecState* st, const double* d3, double* est, const double* est_prev, int* mmin, int nvec,
+                  double tol, int m_max, int round) {
+  bool any = false;
+  for (int s = 0; s < nvec; ++s) {
+    VecState& v = st[s];
+    est[s] = direct_estimate(v, d3 + 3 * s);
+    if (round >= 3 || v.status != VS_DONE || v.m == 0 || !(v.err_est > 0.0) || v.m >= m_max) continue;
+    const double e = est[s];
+    if (e <= tol) continue;
+    const bool progress = round == 0 ? e <= 20.0 * tol : e <= 0.7 * est_prev[s];
+    if (!progress) continue;
+    v.m_min = std::min(m_max, v.m + std::max(2, v.m / 8));
+    v.status = VS_RUNNING;
+    mmin[s] = v.m_min;
+    any = true;
+  }
+  return any;
+}
+
+// Host side: the direct estimates folded into the states.
+void check_apply(VecState* st, const double* est, int nvec, double tol) {
+  for (int s = 0; s < nvec; ++s) {
+    VecState& v = st[s];
+    if (!(v.status == VS_DONE || v.status == GMRF_ERR_NOT_CONVERGED) || v.m == 0) continue;
+    const double e = est[s];
+    if (!(v.err_est >= e)) v.err_est = e;
+    if (v.status == VS_DONE && !(e <= tol)) v.status = GMRF_ERR_NOT_CONVERGED;
+  }
+}
+
 void fill_info(const VecState* st, int nvec, gmrf_result_info* info) {
   if (!info) return;
   for (int s = 0; s < nvec; ++s) {
@@ -371,7 +450,7 @@ void fill_info(const VecState* st, int nvec, gmrf_result_info* info) {
   }
 }
 
-}  // namespace
+}  // namespace host
 
 extern "C" {
 
@@ -568,11 +647,13 @@ int gmrf_create_sparse(const gmrf_sparse_desc* d, void* stream, gmrf_problem** o
 void gmrf_destroy(gmrf_problem* p) {
   if (!p) return;
   async_shutdown(p);  // submitted calls finish first
+  if (p->server) gmrf_server_destroy(p->server);
   if (p->ws) cudaStreamSynchronize(p->ws);
   p->graph.reset();
   DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,
                     &p->partials, &p->counters, &p->y, &p->scratch, &p->nodes, &p->q, &p->out2, &p->stage,
-                    &p->stage2, &p->work, &p->Vb, &p->xacc, &p->accn, &p->solvew};
+                    &p->stage2, &p->work, &p->Vb, &p->xacc, &p->accn, &p->solvew, &p->ycg, &p->ucg,
+                    &p->xacc2, &p->chk, &p->rn, &p->zre, &p->mmin};
   for (DevBuf* b : bufs) release(*b, p->ws);
   precond_free(p->pre, p->ws);
   sparse_free(p->sp, p->ws);
@@ -602,7 +683,8 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
   const bool z_dev = o->z_in && is_device_ptr(o->z_in);
   const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) : 0) +
                        (sparse_f(p) ? n * es : 0) + (bf16 ? (size_t)(m_max + 1) * n * sizeof(__nv_bfloat16) : 0) +
-                       (two_pass ? 2 * n * sizeof(float) + (p->precond ? n * es : 0) : 0);
+                       (two_pass ? 2 * 2 * n * sizeof(float) + (p->precond ? n * es : 0) : 0) +
+                       check_bytes_per_vec(p);
   int chunk = batch_size(p, o->nsamples, nslots, m_max, true, extra);
   if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
   if (chunk < 1) return GMRF_ERR_OOM;
@@ -613,71 +695,115 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
     const int c = std::min(chunk, o->nsamples - s0);
     LanczosBufs b;
     CKR(ensure_lanczos(p, c, nslots, m_max, true, b, bf16));
-    auto load_z = [&]() -> int {
+    CKR(ensure(p->ucg, (size_t)c * n * es, p->ws));
+    CKR(ensure(p->zre, (size_t)c * n * es, p->ws));
+    CKR(ensure(p->mmin, sizeof(int) * c, p->ws));
+    CK(cudaMemsetAsync(p->mmin.p, 0, sizeof(int) * c, s));
+    b.m_min = (const int*)p->mmin.p;
+    auto load_z = [&](void* dst) -> int {
       if (o->z_in) {
         const char* src = (const char*)o->z_in + (size_t)s0 * n * es;
-        CK(cudaMemcpyAsync(b.W[0], src, (size_t)c * n * es,
-                           z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dst, src, (size_t)c * n * es, z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           s));
       } else {
-        CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, c, (int64_t)n, o->seed, s0, b.W[0], s); }));
+        CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, c, (int64_t)n, o->seed, s0, dst, s); }));
       }
       return GMRF_OK;
     };
-    CKR(load_z());
-    CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
-    CK(traced(KC_TM, s, 3, [&] {
-      return launch_tm_inv_sqrt(b, p->fp64, (TmNodes*)p->nodes.p, (double*)p->scratch.p, (double*)p->y.p, s);
-    }));
-    if (two_pass) {
-      // second pass: the same iteration again (bitwise: same z, same kernels),
-      // adding ||z|| y_j v_j to x after every step instead of keeping V_m
-      const size_t xb = (size_t)c * n * (p->fp64 ? sizeof(double) : 2 * sizeof(float));
-      CKR(ensure(p->xacc, xb, p->ws));
-      CKR(ensure(p->accn, sizeof(int) * c, p->ws));
-      CK(cudaMemsetAsync(p->xacc.p, 0, xb, s));
-      CK(cudaMemsetAsync(p->accn.p, 0, sizeof(int) * c, s));
-      b.Xacc = p->xacc.p;
-      b.acc = (int*)p->accn.p;
-      b.y = (const double*)p->y.p;
-      b.xscale = p->precond == GMRF_PREC_NONE ? 1.0 / std::sqrt(p->tau) : 1.0;
-      CKR(load_z());
-      CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
-    }
     void* xdst = (char*)x_out + (size_t)s0 * n * es;
     if (!x_dev) {
       CKR(ensure(p->stage, (size_t)c * n * es, p->ws));
       xdst = p->stage.p;
     }
-    // x_m = ||z|| V_m y (one pass) or the accumulated sum (two passes)
-    auto assemble = [&](double extra, void* dst) -> cudaError_t {
-      return two_pass ? launch_accumulate_finish(p->fp64, n, b, dst, s)
-                      : launch_assemble(p->fp64, n, b, (double*)p->y.p, m_max, extra, dst, s);
-    };
-    if (sparse_f(p)) {
-      // u = ||z|| V_m y, then x = tau^{-1/2} F^{-T} u (Proposition 1 with M = F F^T)
-      CKR(ensure(p->work, (size_t)c * n * es, p->ws));
-      CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0, p->work.p); }));
-      CK(traced(KC_PRE_APPLY, s, 1, [&] { return launch_sparse_ops(*p->sp, 2, p->work.p, xdst, c, s); }));
-      CK(traced(KC_OTHER, s, 1,
-                [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / std::sqrt(p->tau), s); }));
-    } else if (p->precond == GMRF_PREC_NONE) {
-      CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0 / std::sqrt(p->tau), xdst); }));
-    } else {
-      // u = ||z|| V_m y, then x = M^{-1/2} u = tau^{-1/2} B_bar^{-p/2} u (Proposition 1)
-      CKR(ensure(p->work, (size_t)c * n * es, p->ws));
-      CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0, p->work.p); }));
-      CK(traced(KC_PRE_APPLY, s, 3,
-                [&] { return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, p->work.p, xdst, c, s); }));
-      CK(traced(KC_OTHER, s, 1,
-                [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / std::sqrt(p->tau), s); }));
+    CKR(load_z(p->zre.p));  // z for the accuracy check (kept: W[0] becomes a q buffer)
+    std::vector<double> d3((size_t)3 * c), est((size_t)c), est_prev((size_t)c, 0.0);
+    std::vector<int> mmin((size_t)c, 0);
+    CKR(load_z(b.W[0]));
+    CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
+    for (int round = 0;; ++round) {
+      CK(traced(KC_TM, s, 3, [&] {
+        return launch_tm_inv_sqrt(b, p->fp64, (TmNodes*)p->nodes.p, (double*)p->scratch.p, (double*)p->y.p, s);
+      }));
+      CKR(check_tm(p, b, s));
+      LanczosBufs bx = b;
+      if (two_pass) {
+        // second pass: the same iteration again (bitwise: same z, same kernels,
+        // same step counts), adding ||z|| y_j v_j to x (and the check's u_cg)
+        // after every step instead of keeping V_m
+        const size_t xb = (size_t)c * n * (p->fp64 ? sizeof(double) : 2 * sizeof(float));
+        CKR(ensure(p->xacc, xb, p->ws));
+        CKR(ensure(p->xacc2, xb, p->ws));
+        CKR(ensure(p->accn, sizeof(int) * c, p->ws));
+        CK(cudaMemsetAsync(p->xacc.p, 0, xb, s));
+        CK(cudaMemsetAsync(p->xacc2.p, 0, xb, s));
+        CK(cudaMemsetAsync(p->accn.p, 0, sizeof(int) * c, s));
+        bx.Xacc = p->xacc.p;
+        bx.acc = (int*)p->accn.p;
+        bx.y = (const double*)p->y.p;
+        bx.xscale = p->precond == GMRF_PREC_NONE ? 1.0 / std::sqrt(p->tau) : 1.0;
+        bx.Xacc2 = p->xacc2.p;
+        bx.y2 = (const double*)p->ycg.p;
+        CKR(load_z(b.W[0]));
+        CKR(run_lanczos(p, bx, o->tol, m_max, o->check_every));
+      }
+      // x_m = ||z|| V_m y (one pass) or the accumulated sum (two passes), and
+      // with it the check's u_cg = ||z|| V_m T_m^{-1} e_1
+      auto assemble = [&](double extra, void* dst) -> cudaError_t {
+        if (two_pass) {
+          const cudaError_t e = launch_accumulate_finish(p->fp64, n, bx, p->xacc2.p, p->ucg.p, s);
+          return e != cudaSuccess ? e : launch_accumulate_finish(p->fp64, n, bx, p->xacc.p, dst, s);
+        }
+        return launch_assemble_dual(p->fp64, n, b, (double*)p->y.p, m_max, extra, dst, (const double*)p->ycg.p,
+                                    p->ucg.p, s);
+      };
+      if (sparse_f(p)) {
+        // u = ||z|| V_m y, then x = tau^{-1/2} F^{-T} u (Proposition 1 with M = F F^T)
+        CKR(ensure(p->work, (size_t)c * n * es, p->ws));
+        CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0, p->work.p); }));
+        CK(traced(KC_PRE_APPLY, s, 1, [&] { return launch_sparse_ops(*p->sp, 2, p->work.p, xdst, c, s); }));
+        CK(traced(KC_OTHER, s, 1,
+                  [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / std::sqrt(p->tau), s); }));
+      } else if (p->precond == GMRF_PREC_NONE) {
+        CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0 / std::sqrt(p->tau), xdst); }));
+      } else {
+        // u = ||z|| V_m y, then x = M^{-1/2} u = tau^{-1/2} B_bar^{-p/2} u (Proposition 1)
+        CKR(ensure(p->work, (size_t)c * n * es, p->ws));
+        CK(traced(KC_ASSEMBLE, s, 1, [&] { return assemble(1.0, p->work.p); }));
+        CK(traced(KC_PRE_APPLY, s, 3, [&] {
+          return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, p->work.p, xdst, c, s);
+        }));
+        CK(traced(KC_OTHER, s, 1,
+                  [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / std::sqrt(p->tau), s); }));
+      }
+      // accuracy check: r = z - A u_cg, t = A r
+      CKR(check_residuals(p, c, p->zre.p, p->ucg.p, s));
+      CK(cudaMemcpyAsync(d3.data(), p->rn.p, sizeof(double) * 3 * c, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * c, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      trace_collect();
+      // vectors whose recurrence estimate met tol but whose direct estimate did
+      // not, by a margin more steps can close, continue for more steps
+      if (!check_resume(p->st_host, d3.data(), est.data(), est_prev.data(), mmin.data(), c, o->tol, m_max, round))
+        break;
+      est_prev = est;
+      if (two_pass) {
+        // rerun both passes from z with the new minimum step counts (the
+        // other vectors repeat their steps bitwise)
+        CK(cudaMemcpyAsync(p->mmin.p, mmin.data(), sizeof(int) * c, cudaMemcpyHostToDevice, s));
+        CKR(load_z(b.W[0]));
+        CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
+      } else {
+        // continue the resumed vectors in place (their states now RUNNING)
+        CK(cudaMemcpyAsync(b.st, p->st_host, sizeof(VecState) * c, cudaMemcpyHostToDevice, s));
+        CKR(run_lanczos(p, b, o->tol, m_max, o->check_every, false, false));
+      }
     }
+    check_apply(p->st_host, est.data(), c, o->tol);
     if (!x_dev)
       CK(cudaMemcpyAsync((char*)x_out + (size_t)s0 * n * es, xdst, (size_t)c * n * es, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * c, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    trace_collect();
     std::memcpy(all.data() + s0, p->st_host, sizeof(VecState) * c);
   }
+  CK(cudaStreamSynchronize(s));
   CKR(leave(p));
   fill_info(all.data(), o->nsamples, info);
   return worst_status(all.data(), o->nsamples);
@@ -853,7 +979,7 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
   const bool z_dev = so->z_in && is_device_ptr(so->z_in);
   const bool r_dev = lo->probes_in && is_device_ptr(lo->probes_in);
   const size_t extra = (x_dev ? 0 : n * es) + (p->precond ? precond_extra_bytes(p->pre, es) + n * es : 0) +
-                       (sparse_f(p) ? n * es : 0);
+                       (sparse_f(p) ? n * es : 0) + check_bytes_per_vec(p);
   int chunk = batch_size(p, total, nslots, m_max, true, extra);
   if (p->tune_bw > 0 && chunk > p->tune_bw) chunk = p->tune_bw;
   if (chunk < 1) return GMRF_ERR_OOM;
@@ -869,13 +995,15 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
     LanczosBufs b;
     CKR(ensure_lanczos(p, c, nslots, m_max, true, b));
     // the same z and probes as gmrf_sample and gmrf_logdet (per-vector streams)
-    if (nsc > 0) {
+    auto load_z = [&]() -> int {
       if (so->z_in)
         CK(cudaMemcpyAsync(b.W[0], (const char*)so->z_in + (size_t)t0 * n * es, (size_t)nsc * n * es,
                            z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
       else
         CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, nsc, (int64_t)n, so->seed, t0, b.W[0], s); }));
-    }
+      return GMRF_OK;
+    };
+    if (nsc > 0) CKR(load_z());
     if (nqc > 0) {
       void* dst = (char*)b.W[0] + (size_t)nsc * n * es;
       if (lo->probes_in)
@@ -889,41 +1017,72 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
         CK(traced(KC_RNG, s, 1, [&] { return launch_rng(1, p->fp64, nqc, (int64_t)n, lo->seed, q0, dst, s); }));
     }
     CKR(run_lanczos(p, b, so->tol, m_max, so->check_every));
+    std::vector<double> d3((size_t)3 * std::max(nsc, 1)), est((size_t)std::max(nsc, 1)),
+        est_prev((size_t)std::max(nsc, 1), 0.0);
+    std::vector<int> mmin((size_t)std::max(nsc, 1), 0);
+    void* xdst = (char*)x_out + (size_t)t0 * n * es;
     if (nsc > 0) {
-      const LanczosBufs bs = sub_batch(b, 0, nsc, n, es);
-      CK(traced(KC_TM, s, 3, [&] {
-        return launch_tm_inv_sqrt(bs, p->fp64, (TmNodes*)p->nodes.p, (double*)p->scratch.p, (double*)p->y.p, s);
-      }));
-      void* xdst = (char*)x_out + (size_t)t0 * n * es;
+      CKR(ensure(p->ucg, (size_t)nsc * n * es, p->ws));
+      CKR(ensure(p->zre, (size_t)nsc * n * es, p->ws));
       if (!x_dev) {
         CKR(ensure(p->stage, (size_t)nsc * n * es, p->ws));
         xdst = p->stage.p;
       }
+    }
+    // the samples' z for the accuracy check (as in gmrf_sample)
+    if (nsc > 0) {
+      if (so->z_in)
+        CK(cudaMemcpyAsync(p->zre.p, (const char*)so->z_in + (size_t)t0 * n * es, (size_t)nsc * n * es,
+                           z_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      else
+        CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, nsc, (int64_t)n, so->seed, t0, p->zre.p, s); }));
+    }
+    for (int round = 0; nsc > 0; ++round) {
+      const LanczosBufs bs = sub_batch(b, 0, nsc, n, es);
+      CK(traced(KC_TM, s, 3, [&] {
+        return launch_tm_inv_sqrt(bs, p->fp64, (TmNodes*)p->nodes.p, (double*)p->scratch.p, (double*)p->y.p, s);
+      }));
+      CKR(check_tm(p, bs, s));
+      const double* ycg = (const double*)p->ycg.p;
       if (sparse_f(p)) {
         CKR(ensure(p->work, (size_t)nsc * n * es, p->ws));
-        CK(traced(KC_ASSEMBLE, s, 1,
-                  [&] { return launch_assemble(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
+        CK(traced(KC_ASSEMBLE, s, 1, [&] {
+          return launch_assemble_dual(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0, p->work.p, ycg, p->ucg.p, s);
+        }));
         CK(traced(KC_PRE_APPLY, s, 1, [&] { return launch_sparse_ops(*p->sp, 2, p->work.p, xdst, nsc, s); }));
         CK(traced(KC_OTHER, s, 1,
                   [&] { return launch_scale(p->fp64, xdst, (size_t)nsc * n, 1.0 / std::sqrt(p->tau), s); }));
       } else if (p->precond == GMRF_PREC_NONE) {
         CK(traced(KC_ASSEMBLE, s, 1, [&] {
-          return launch_assemble(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0 / std::sqrt(p->tau), xdst, s);
+          return launch_assemble_dual(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0 / std::sqrt(p->tau), xdst, ycg,
+                                      p->ucg.p, s);
         }));
       } else {
         CKR(ensure(p->work, (size_t)nsc * n * es, p->ws));
-        CK(traced(KC_ASSEMBLE, s, 1,
-                  [&] { return launch_assemble(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0, p->work.p, s); }));
+        CK(traced(KC_ASSEMBLE, s, 1, [&] {
+          return launch_assemble_dual(p->fp64, n, bs, (double*)p->y.p, m_max, 1.0, p->work.p, ycg, p->ucg.p, s);
+        }));
         CK(traced(KC_PRE_APPLY, s, 3, [&] {
           return launch_precond_apply(p->pre, p->g, p->fp64, PRE_INV_SQRT, p->work.p, xdst, nsc, s);
         }));
         CK(traced(KC_OTHER, s, 1,
                   [&] { return launch_scale(p->fp64, xdst, (size_t)nsc * n, 1.0 / std::sqrt(p->tau), s); }));
       }
-      if (!x_dev)
-        CK(cudaMemcpyAsync((char*)x_out + (size_t)t0 * n * es, xdst, (size_t)nsc * n * es, cudaMemcpyDeviceToHost,
-                           s));
+      // accuracy check of the samples, with the same resumption as gmrf_sample
+      CKR(check_residuals(p, nsc, p->zre.p, p->ucg.p, s));
+      CK(cudaMemcpyAsync(d3.data(), p->rn.p, sizeof(double) * 3 * nsc, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * nsc, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      trace_collect();
+      if (!check_resume(p->st_host, d3.data(), est.data(), est_prev.data(), mmin.data(), nsc, so->tol, m_max,
+                        round))
+        break;
+      est_prev = est;
+      CK(cudaMemcpyAsync(b.st, p->st_host, sizeof(VecState) * nsc, cudaMemcpyHostToDevice, s));
+      CKR(run_lanczos(p, b, so->tol, m_max, so->check_every, false, false));
     }
+    if (nsc > 0 && !x_dev)
+      CK(cudaMemcpyAsync((char*)x_out + (size_t)t0 * n * es, xdst, (size_t)nsc * n * es, cudaMemcpyDeviceToHost, s));
     if (nqc > 0) {
       const LanczosBufs bq = sub_batch(b, nsc, nqc, n, es);
       CK(traced(KC_TM, s, 2, [&] { return launch_tm_log(bq, p->fp64, (TmNodes*)p->nodes.p, qall + q0, s); }));
@@ -931,6 +1090,7 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
     CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * c, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     trace_collect();
+    if (nsc > 0) check_apply(p->st_host, est.data(), nsc, so->tol);
     std::memcpy(all.data() + t0, p->st_host, sizeof(VecState) * c);
   }
   const double shift = p->logdet_M + (double)n * std::log(p->tau);

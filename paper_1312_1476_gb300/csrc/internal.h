@@ -44,6 +44,11 @@ struct LanczosBufs {
   int* acc = nullptr;
   const double* y = nullptr;  // [nvec][m_max] from the first pass
   double xscale = 1.0;
+  // optional second accumulation, x2 += ||z|| y2_j v_j into Xacc2 (same layout as Xacc)
+  void* Xacc2 = nullptr;
+  const double* y2 = nullptr;
+  // [nvec] minimum step counts for the stopping rule, read at init (null: 0)
+  const int* m_min = nullptr;
 };
 
 // lanczos_stencil.cu --------------------------------------------------------
@@ -82,11 +87,22 @@ cudaError_t launch_lanczos_init(bool fp64, size_t n, const LanczosBufs& b, cudaS
 // x[s] = scale[s] * V_m y  (scale = ||z|| * extra), y from tm buffers.
 cudaError_t launch_assemble(bool fp64, size_t n, const LanczosBufs& b, const double* y, int y_stride,
                             double extra_scale, void* x, cudaStream_t s);
+// The same x, plus x2[s] = ||z|| V_m y2 from the same pass over V_m.
+cudaError_t launch_assemble_dual(bool fp64, size_t n, const LanczosBufs& b, const double* y, int y_stride,
+                                 double extra_scale, void* x, const double* y2, void* x2, cudaStream_t s);
 // Two-pass sampling: add the newest basis vector of each vector to Xacc
-// (after a step), and x = Xacc (sum + compensation) at the end; the same
-// arithmetic, in the same order, as launch_assemble.
+// (and, with b.Xacc2, to Xacc2) after a step, and x = X (sum + compensation)
+// at the end; the same arithmetic, in the same order, as launch_assemble.
 cudaError_t launch_accumulate(bool fp64, size_t n, const LanczosBufs& b, cudaStream_t s);
-cudaError_t launch_accumulate_finish(bool fp64, size_t n, const LanczosBufs& b, void* x, cudaStream_t s);
+cudaError_t launch_accumulate_finish(bool fp64, size_t n, const LanczosBufs& b, const void* X, void* x,
+                                     cudaStream_t s);
+// r = z - r in place for count elements of float or double.
+cudaError_t launch_resid_form(bool z64, const void* z, bool r64, void* r, size_t count, cudaStream_t s);
+// out[3 s .. 3 s + 2] = (r.r, r.t, t.t) in FP64 sums for nvec vectors [nvec][n]
+// of float or double; part: kResidBlocks * nvec Dots<double> of scratch.
+constexpr int kResidBlocks = 128;
+cudaError_t launch_dots3(bool r64, const void* r, const void* t, size_t n, int nvec, void* part, double* out,
+                         cudaStream_t s);
 cudaError_t launch_convert(bool to_fp64, const void* in, void* out, size_t count, cudaStream_t s);
 cudaError_t launch_scale(bool fp64, void* x, size_t count, double a, cudaStream_t s);
 

@@ -112,7 +112,8 @@ __global__ void k_rng_coloured(T* out, int64_t nvec, int64_t n, uint32_t k0, uin
 
 // ||z|| per vector and state reset.  grid (nblk, nvec).
 template <typename T>
-__global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>* partials, unsigned* counters) {
+__global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>* partials, unsigned* counters,
+                       const int* m_min) {
   __shared__ Dots<T> red[8];
   __shared__ int s_flag;
   const int s = blockIdx.y;
@@ -139,6 +140,7 @@ __global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>*
     v.znorm = sqrt(s3);
     v.vscale = v.znorm > 0.0 ? 1.0 / v.znorm : 0.0;
     v.m = 0;
+    v.m_min = m_min ? m_min[s] : 0;
     if (!isfinite(v.znorm)) v.status = GMRF_ERR_NUMERIC;
     else if (v.znorm == 0.0) v.status = VS_DONE;
     else v.status = VS_RUNNING;
@@ -149,81 +151,128 @@ __global__ void k_init(const T* __restrict__ W, size_t n, VecState* st, Dots<T>*
 // x[s][i] = scale_s * sum_j V[s][j][i] y[s][j], scale_s = ||z_s|| * extra.
 // FP32: y split into float hi + lo, compensated (Neumaier) accumulation.
 // The basis is read in its storage type S (T, or bfloat16 for T = float).
+// DUAL: in the same pass over V_m also x2[s][i] = ||z_s|| sum_j V[s][j][i]
+// y2[s][j] (the CG iterate of the accuracy check), with the same arithmetic;
+// x is computed exactly as without it.
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ double to_f(double v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename T, typename S = T>
+// x_i += vv * y_j in a compensated (sum, error) pair
+__device__ __forceinline__ void acc_comp(float vv, float yh, float yl, float& sum, float& comp) {
+  const float t = __fmaf_rn(vv, yh, __fmul_rn(vv, yl));
+  const float s2 = __fadd_rn(sum, t);
+  comp = __fadd_rn(comp, fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t) : __fadd_rn(__fsub_rn(t, s2), sum));
+  sum = s2;
+}
+
+template <typename T, typename S = T, bool DUAL = false>
 __global__ void k_assemble(const S* __restrict__ V, int nslots, size_t n, const VecState* st, const double* y,
-                           int y_stride, double extra, T* x) {
+                           int y_stride, double extra, T* x, const double* y2, T* x2) {
   extern __shared__ unsigned char smem_raw[];
   const int s = blockIdx.y;
   const VecState v = st[s];
   const int m = v.m;
   T* xo = x + (size_t)s * n;
+  T* xo2 = DUAL ? x2 + (size_t)s * n : nullptr;
   const bool bad = !(v.status == VS_DONE || v.status == GMRF_ERR_NOT_CONVERGED);
   if (bad || m == 0) {
     const T fill = (bad && v.status != VS_DONE) ? (T)NAN : (T)0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
       xo[i] = fill;
+      if (DUAL) xo2[i] = fill;
+    }
     return;
   }
   const double scale = v.znorm * extra;
   const double* ys = y + (size_t)s * y_stride;
+  const double* ys2 = DUAL ? y2 + (size_t)s * y_stride : nullptr;
   const S* Vs = V + (size_t)s * nslots * n;
   if (sizeof(T) == 4) {
     float* yh = (float*)smem_raw;
     float* yl = yh + m;
+    float* y2h = yl + m;
+    float* y2l = y2h + m;
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
       const double yy = ys[j] * scale;
       const float h = (float)yy;
       yh[j] = h;
       yl[j] = (float)(yy - (double)h);
+      if (DUAL) {
+        const double y2v = ys2[j] * v.znorm;
+        const float h2 = (float)y2v;
+        y2h[j] = h2;
+        y2l[j] = (float)(y2v - (double)h2);
+      }
     }
     __syncthreads();
-    // x_i += vv * y_j in a compensated (sum, error) pair; the order of the terms is j = 0 .. m-1
-    auto acc = [&](float vv, int j, float& sum, float& comp) {
-      const float t = __fmaf_rn(vv, yh[j], __fmul_rn(vv, yl[j]));
-      const float s2 = __fadd_rn(sum, t);
-      comp = __fadd_rn(comp, fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t)
-                                                     : __fadd_rn(__fsub_rn(t, s2), sum));
-      sum = s2;
-    };
+    // the order of the terms is j = 0 .. m-1
     if constexpr (std::is_same<S, __nv_bfloat16>::value) {
       // bfloat16 basis: half the bytes per load, so more loads in flight per
       // thread (the same arithmetic and order per element as below)
       for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float sum = 0.f, comp = 0.f;
+        float sum = 0.f, comp = 0.f, sum2 = 0.f, comp2 = 0.f;
 #pragma unroll 8
-        for (int j = 0; j < m; ++j) acc(__bfloat162float(Vs[(size_t)j * n + i]), j, sum, comp);
+        for (int j = 0; j < m; ++j) {
+          const float vv = __bfloat162float(Vs[(size_t)j * n + i]);
+          acc_comp(vv, yh[j], yl[j], sum, comp);
+          if (DUAL) acc_comp(vv, y2h[j], y2l[j], sum2, comp2);
+        }
         xo[i] = (T)__fadd_rn(sum, comp);
+        if (DUAL) xo2[i] = (T)__fadd_rn(sum2, comp2);
       }
       return;
     }
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-      float sum = 0.f, comp = 0.f;
-      for (int j = 0; j < m; ++j) acc((float)to_f(Vs[(size_t)j * n + i]), j, sum, comp);
+      float sum = 0.f, comp = 0.f, sum2 = 0.f, comp2 = 0.f;
+      for (int j = 0; j < m; ++j) {
+        const float vv = (float)to_f(Vs[(size_t)j * n + i]);
+        acc_comp(vv, yh[j], yl[j], sum, comp);
+        if (DUAL) acc_comp(vv, y2h[j], y2l[j], sum2, comp2);
+      }
       xo[i] = (T)__fadd_rn(sum, comp);
+      if (DUAL) xo2[i] = (T)__fadd_rn(sum2, comp2);
     }
   } else {
     double* yd = (double*)smem_raw;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) yd[j] = ys[j] * scale;
+    double* yd2 = yd + m;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      yd[j] = ys[j] * scale;
+      if (DUAL) yd2[j] = ys2[j] * v.znorm;
+    }
     __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-      double sum = 0.0;
-      for (int j = 0; j < m; ++j) sum = fma((double)to_f(Vs[(size_t)j * n + i]), yd[j], sum);
+      double sum = 0.0, sum2 = 0.0;
+      for (int j = 0; j < m; ++j) {
+        const double vv = (double)to_f(Vs[(size_t)j * n + i]);
+        sum = fma(vv, yd[j], sum);
+        if (DUAL) sum2 = fma(vv, yd2[j], sum2);
+      }
       xo[i] = (T)sum;
+      if (DUAL) xo2[i] = (T)sum2;
     }
   }
 }
 
 // Two-pass sampling: x += scale_s y_j v_j for the basis vector v_j the step
 // just formed (j = acc[s] if the step ran for vector s), with the arithmetic
-// of k_assemble per element.  acc[s] advances in the vector's last block,
-// after every block has read it.
+// of k_assemble per element; with X2 also x2 += ||z_s|| y2_j v_j (the dual
+// output of k_assemble).  acc[s] advances in the vector's last block, after
+// every block has read it.
+__device__ __forceinline__ void acc_pair(float vv, double yy, float* xh, float* xl, size_t i) {
+  const float h = (float)yy;
+  const float l = (float)(yy - (double)h);
+  const float t = __fmaf_rn(vv, h, __fmul_rn(vv, l));
+  const float sum = xh[i];
+  const float s2 = __fadd_rn(sum, t);
+  xl[i] = __fadd_rn(xl[i], fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t) : __fadd_rn(__fsub_rn(t, s2), sum));
+  xh[i] = s2;
+}
+
 template <typename T>
 __global__ void k_accumulate(const T* __restrict__ V, int nslots, size_t n, const VecState* st, const double* y,
-                             int m_max, double extra, void* X, int* acc, unsigned* counters) {
+                             int m_max, double extra, void* X, int* acc, unsigned* counters, const double* y2,
+                             void* X2) {
   __shared__ int s_flag;
   const int s = blockIdx.y;
   const VecState v = st[s];
@@ -232,24 +281,24 @@ __global__ void k_accumulate(const T* __restrict__ V, int nslots, size_t n, cons
   if (work) {
     const T* vj = V + ((size_t)s * nslots + (size_t)(a % nslots)) * n;
     const double yy = y[(size_t)s * m_max + a] * (v.znorm * extra);
+    const double yy2 = X2 ? y2[(size_t)s * m_max + a] * v.znorm : 0.0;
     if (sizeof(T) == 4) {
       float* xh = (float*)X + (size_t)s * 2 * n;
       float* xl = xh + n;
-      const float h = (float)yy;
-      const float l = (float)(yy - (double)h);
+      float* x2h = X2 ? (float*)X2 + (size_t)s * 2 * n : nullptr;
+      float* x2l = x2h + n;
       for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float vv = (float)vj[i];
-        const float t = __fmaf_rn(vv, h, __fmul_rn(vv, l));
-        const float sum = xh[i];
-        const float s2 = __fadd_rn(sum, t);
-        xl[i] = __fadd_rn(xl[i], fabsf(sum) >= fabsf(t) ? __fadd_rn(__fsub_rn(sum, s2), t)
-                                                         : __fadd_rn(__fsub_rn(t, s2), sum));
-        xh[i] = s2;
+        acc_pair(vv, yy, xh, xl, i);
+        if (X2) acc_pair(vv, yy2, x2h, x2l, i);
       }
     } else {
       double* xd = (double*)X + (size_t)s * n;
-      for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+      double* xd2 = X2 ? (double*)X2 + (size_t)s * n : nullptr;
+      for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         xd[i] = fma((double)vj[i], yy, xd[i]);
+        if (X2) xd2[i] = fma((double)vj[i], yy2, xd2[i]);
+      }
     }
   }
   if (last_block(counters, s, gridDim.x, &s_flag) && threadIdx.x == 0 && work) acc[s] = a + 1;
@@ -271,6 +320,46 @@ __global__ void k_accumulate_finish(const void* X, size_t n, const VecState* st,
     } else {
       xo[i] = (T)((const double*)X)[(size_t)s * n + i];
     }
+  }
+}
+
+// r = z - r in place (the residual from A u in r), elementwise in the type of r.
+template <typename Z, typename R>
+__global__ void k_resid_form(const Z* __restrict__ z, R* r, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    r[i] = (R)((double)z[i] - (double)r[i]);
+}
+
+// Partial sums of r.r, r.t, t.t in FP64 per vector, grid (nblk, nvec); the
+// block tree and the order of the partials depend only on n.
+template <typename R>
+__global__ void k_dots3_partial(const R* __restrict__ r, const R* __restrict__ t, size_t n, Dots<double>* part) {
+  __shared__ Dots<double> red[8];
+  const int s = blockIdx.y;
+  const R* rs = r + (size_t)s * n;
+  const R* ts = t + (size_t)s * n;
+  Dots<double> d;
+  d.zero();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double a = (double)rs[i], b = (double)ts[i];
+    d.s1 = fma(a, a, d.s1);
+    d.s2 = fma(a, b, d.s2);
+    d.s3 = fma(b, b, d.s3);
+  }
+  d = block_reduce(d, red);
+  if (threadIdx.x == 0) part[(size_t)s * gridDim.x + blockIdx.x] = d;
+}
+__global__ void k_dots3_final(const Dots<double>* part, int nblk, double* out) {
+  __shared__ Dots<double> red[8];
+  const int s = blockIdx.x;
+  Dots<double> d;
+  d.zero();
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) d.merge(part[(size_t)s * nblk + b]);
+  d = block_reduce(d, red);
+  if (threadIdx.x == 0) {
+    out[3 * s] = d.s1;
+    out[3 * s + 1] = d.s2;
+    out[3 * s + 2] = d.s3;
   }
 }
 
@@ -367,36 +456,48 @@ cudaError_t launch_lanczos_init(bool fp64, size_t n, const LanczosBufs& b, cudaS
   if (nblk > 256) nblk = 256;
   dim3 grd(nblk, b.nvec);
   if (fp64)
-    k_init<double><<<grd, 256, 0, s>>>((const double*)b.W[0], n, b.st, (Dots<double>*)b.partials, b.counters);
+    k_init<double><<<grd, 256, 0, s>>>((const double*)b.W[0], n, b.st, (Dots<double>*)b.partials, b.counters,
+                                       b.m_min);
   else
-    k_init<float><<<grd, 256, 0, s>>>((const float*)b.W[0], n, b.st, (Dots<float>*)b.partials, b.counters);
+    k_init<float><<<grd, 256, 0, s>>>((const float*)b.W[0], n, b.st, (Dots<float>*)b.partials, b.counters,
+                                      b.m_min);
+  return cudaGetLastError();
+}
+
+template <typename T, typename S, bool DUAL>
+static void assemble_one(const S* V, int nslots, size_t n, const LanczosBufs& b, const double* y, int y_stride,
+                         double extra, T* x, const double* y2, T* x2, cudaStream_t s) {
+  int nblk = (int)((n + 255) / 256);
+  if (nblk > 2048) nblk = 2048;
+  dim3 grd(nblk, b.nvec);
+  const size_t sm = (size_t)b.m_max * 8 * (DUAL ? 2 : 1);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_assemble<T, S, DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_assemble<T, S, DUAL><<<grd, 256, sm, s>>>(V, nslots, n, b.st, y, y_stride, extra, x, y2, x2);
+}
+
+template <bool DUAL>
+static cudaError_t assemble_dispatch(bool fp64, size_t n, const LanczosBufs& b, const double* y, int y_stride,
+                                     double extra_scale, void* x, const double* y2, void* x2, cudaStream_t s) {
+  if (fp64)
+    assemble_one<double, double, DUAL>((const double*)b.V, b.nslots, n, b, y, y_stride, extra_scale, (double*)x, y2,
+                                       (double*)x2, s);
+  else if (b.Vb)  // bfloat16 basis copy: m_max + 1 slots per vector
+    assemble_one<float, __nv_bfloat16, DUAL>(b.Vb, b.m_max + 1, n, b, y, y_stride, extra_scale, (float*)x, y2,
+                                             (float*)x2, s);
+  else
+    assemble_one<float, float, DUAL>((const float*)b.V, b.nslots, n, b, y, y_stride, extra_scale, (float*)x, y2,
+                                     (float*)x2, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble(bool fp64, size_t n, const LanczosBufs& b, const double* y, int y_stride,
                             double extra_scale, void* x, cudaStream_t s) {
-  int nblk = (int)((n + 255) / 256);
-  if (nblk > 2048) nblk = 2048;
-  dim3 grd(nblk, b.nvec);
-  const size_t sm = (size_t)b.m_max * 8;
-  if (fp64) {
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_assemble<double><<<grd, 256, sm, s>>>((const double*)b.V, b.nslots, n, b.st, y, y_stride, extra_scale,
-                                            (double*)x);
-  } else if (b.Vb) {
-    // bfloat16 basis copy: m_max + 1 slots per vector
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_assemble<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_assemble<float, __nv_bfloat16><<<grd, 256, sm, s>>>(b.Vb, b.m_max + 1, n, b.st, y, y_stride, extra_scale,
-                                                          (float*)x);
-  } else {
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_assemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_assemble<float><<<grd, 256, sm, s>>>((const float*)b.V, b.nslots, n, b.st, y, y_stride, extra_scale,
-                                           (float*)x);
-  }
-  return cudaGetLastError();
+  return assemble_dispatch<false>(fp64, n, b, y, y_stride, extra_scale, x, nullptr, nullptr, s);
+}
+
+cudaError_t launch_assemble_dual(bool fp64, size_t n, const LanczosBufs& b, const double* y, int y_stride,
+                                 double extra_scale, void* x, const double* y2, void* x2, cudaStream_t s) {
+  return assemble_dispatch<true>(fp64, n, b, y, y_stride, extra_scale, x, y2, x2, s);
 }
 
 cudaError_t launch_accumulate(bool fp64, size_t n, const LanczosBufs& b, cudaStream_t s) {
@@ -405,19 +506,38 @@ cudaError_t launch_accumulate(bool fp64, size_t n, const LanczosBufs& b, cudaStr
   dim3 grd(nblk, b.nvec);
   if (fp64)
     k_accumulate<double><<<grd, 256, 0, s>>>((const double*)b.V, b.nslots, n, b.st, b.y, b.m_max, b.xscale, b.Xacc,
-                                             b.acc, b.counters);
+                                             b.acc, b.counters, b.y2, b.Xacc2);
   else
     k_accumulate<float><<<grd, 256, 0, s>>>((const float*)b.V, b.nslots, n, b.st, b.y, b.m_max, b.xscale, b.Xacc,
-                                            b.acc, b.counters);
+                                            b.acc, b.counters, b.y2, b.Xacc2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_accumulate_finish(bool fp64, size_t n, const LanczosBufs& b, void* x, cudaStream_t s) {
+cudaError_t launch_accumulate_finish(bool fp64, size_t n, const LanczosBufs& b, const void* X, void* x,
+                                     cudaStream_t s) {
   int nblk = (int)((n + 255) / 256);
   if (nblk > 2048) nblk = 2048;
   dim3 grd(nblk, b.nvec);
-  if (fp64) k_accumulate_finish<double><<<grd, 256, 0, s>>>(b.Xacc, n, b.st, (double*)x);
-  else k_accumulate_finish<float><<<grd, 256, 0, s>>>(b.Xacc, n, b.st, (float*)x);
+  if (fp64) k_accumulate_finish<double><<<grd, 256, 0, s>>>(X, n, b.st, (double*)x);
+  else k_accumulate_finish<float><<<grd, 256, 0, s>>>(X, n, b.st, (float*)x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_form(bool z64, const void* z, bool r64, void* r, size_t count, cudaStream_t s) {
+  const int grid = grid_for(count, 256);
+  if (z64 && r64) k_resid_form<double, double><<<grid, 256, 0, s>>>((const double*)z, (double*)r, count);
+  else if (!z64 && r64) k_resid_form<float, double><<<grid, 256, 0, s>>>((const float*)z, (double*)r, count);
+  else if (!z64 && !r64) k_resid_form<float, float><<<grid, 256, 0, s>>>((const float*)z, (float*)r, count);
+  else k_resid_form<double, float><<<grid, 256, 0, s>>>((const double*)z, (float*)r, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots3(bool r64, const void* r, const void* t, size_t n, int nvec, void* part, double* out,
+                         cudaStream_t s) {
+  dim3 grd(kResidBlocks, nvec);
+  if (r64) k_dots3_partial<double><<<grd, 256, 0, s>>>((const double*)r, (const double*)t, n, (Dots<double>*)part);
+  else k_dots3_partial<float><<<grd, 256, 0, s>>>((const float*)r, (const float*)t, n, (Dots<double>*)part);
+  k_dots3_final<<<nvec, 256, 0, s>>>((const Dots<double>*)part, kResidBlocks, out);
   return cudaGetLastError();
 }
 

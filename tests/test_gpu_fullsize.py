@@ -61,6 +61,34 @@ def test_headline_1024_mirror_fp32(g):
     assert _rel(x.cpu().numpy(), xe) <= 1e-6
 
 
+def test_literal_1024_circulant_fp32(g):
+    # The configuration's literal preconditioner: the constant-kappa circulant
+    # on the grid's own torus (Section 5.1), whose boundary terms leave the FP32
+    # applies a floor near 1e-6.  Whatever the library returns must be honest:
+    # status OK only with the error within tol, otherwise NOT_CONVERGED with an
+    # error estimate that covers the error.  Oracle: Algorithm 1 on the
+    # preconditioned operator in FP64 (no reorthogonalisation: at about 600
+    # steps it would cost O(m^2 n)), run to the Theorem 1 estimate 1e-9.
+    shape = (1024, 1024)
+    n = 1024 * 1024
+    k2 = inputs.kappa2_gp_field(shape, seed=1)
+    kb = precond.kappa2_bar(k2)
+    z = inputs.gaussian_vectors(1, n, seed=2, dtype=np.float32)
+    with g.Problem(shape, "neumann", "spde_squared", kappa2=_dev(k2), precond="circulant", kappa2_precond=kb) as p:
+        x = torch.empty(n, dtype=torch.float32, device="cuda")
+        rc, info = p.sample(x, nsamples=1, tol=1e-6, m_max=2000, z=_dev(z), raise_on_error=False)
+    Q = stencil.precision_matrix(shape, "neumann", "spde_squared", k2.astype(np.float64), 1.0)
+    xe, m, est, status = olz.precond_sample(Q, shape, "periodic", "spde_squared", kb, 1.0, z[0].astype(np.float64),
+                                            1e-9, 1500, check_every=8)
+    assert status == "ok"
+    err = _rel(x.cpu().numpy(), xe)
+    if info[0].status == g.OK:
+        assert rc == g.OK and err <= 1e-6
+    else:
+        assert rc == g.ERR_NOT_CONVERGED and info[0].status == g.ERR_NOT_CONVERGED
+        assert info[0].err_est >= err
+
+
 def test_headline_1024_solve_fp32(g):
     # The Section 5.1 linear solve on the headline problem: x = Q^{-1} b from
     # the mirror-preconditioned Lanczos/CG iteration at tol 1e-6 (relative

@@ -147,9 +147,12 @@ def test_samples_and_probes_in_one_batch(g, colour_dist, block_width, pre):
         with pytest.raises(g.GmrfError):
             p.sample_logdet(x2, nsamples=5, nprobes=4, tol=1e-6, m_max=m_max, seed=11, probe_seed=12,
                             colour_dist=-1)
-    assert rc == rc1 == rc2 == rch == g.OK
+    # the samples' status is the honest one of gmrf_sample (the unpreconditioned
+    # FP32 operator here can stop short of tol); the probes converge
+    assert rc == rc1 == rch and rc2 == g.OK
+    assert rc1 == g.OK or (pre == "none" and rc1 == g.ERR_NOT_CONVERGED)
     assert torch.equal(x1, x2) and np.array_equal(xh, x1.cpu().numpy().reshape(5, n))
     assert np.array_equal(q1, q2) and ld1 == ld2 == ldh and se1 == se2
-    assert [i.m_used for i in si1] == [i.m_used for i in si2]
+    assert [(i.m_used, i.status, i.err_est) for i in si1] == [(i.m_used, i.status, i.err_est) for i in si2]
     assert [i.m_used for i in li1] == [i.m_used for i in li2]
     assert len(q2) == 4 * (colour_dist + 1) ** 2

@@ -5,6 +5,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from honesty import assert_honest
 from oracle import exact, lanczos as olz, philox, precond, stencil
 from paper_1312_1476_gb300 import inputs
 
@@ -81,9 +82,10 @@ def test_unpreconditioned_fp32_vs_dense(g, shape, bc, op):
     with g.Problem(shape, bc, op, kappa2=_dev(k2), tau=2.0, precision="fp32") as p:
         rc, info, X = _sample(g, p, Z, 1e-6, 4 * n, "fp32")
     Xe = exact.sample_dense(Q, Z.astype(np.float64))
+    # FP32 applies of an ill-conditioned Q (the squared operators) can leave
+    # the attainable accuracy near 1e-6: then the library must say so
     for s in range(2):
-        assert info[s].status == g.OK
-        assert _rel(X[s], Xe[s]) <= 1e-6
+        assert_honest(info[s], _rel(X[s], Xe[s]), 1e-6)
 
 
 @pytest.mark.parametrize("kind", ["circulant", "mirror"])
@@ -103,16 +105,23 @@ def test_preconditioned_vs_prop1_dense(g, kind, precision, bc):
                    precision=precision) as p:
         rc, info, X = _sample(g, p, Z, tol, 256, precision)
     Xe = precond.sample_prop1_dense(Q, shape, okind, "spde_squared", kb, 1.5, Z.astype(np.float64))
-    # FP32: 1e-6 when M carries the problem's own boundary condition (mirror M
-    # on a Neumann grid: R = K - kappa_bar^2 only).  When the boundaries differ
-    # (circulant M, or any M on a Dirichlet grid) R also holds boundary edge
-    # terms that are not small, and on a 16x16 grid, where every cell is near the
-    # boundary, the FP32 rounding floor is 1e-6 to 2e-5 depending on rounding order.
+    # Status OK means the requested tolerance is met (Theorem 1 estimate and
+    # the library's direct-residual estimate both <= tol).  When the
+    # boundaries of M and Q differ (circulant M, or any M on a Dirichlet grid)
+    # the FP32 applies cannot reach 1e-6 on this 16 x 16 grid, where every cell
+    # is near the boundary: the library must then say NOT_CONVERGED, with an
+    # error estimate that covers the error it returns.  With matched
+    # boundaries (mirror M on a Neumann grid) and in FP64 it must converge.
     matched = kind == "mirror" and bc == "neumann"
-    tol_x = 1e-10 if precision == "fp64" else (1e-6 if matched else 3e-5)
+    tol_x = 1e-10 if precision == "fp64" else 1e-6
     for s in range(2):
-        assert info[s].status == g.OK
-        assert _rel(X[s], Xe[s]) <= tol_x
+        err = _rel(X[s], Xe[s])
+        if precision == "fp64" or matched:
+            assert info[s].status == g.OK
+        if info[s].status == g.OK:
+            assert err <= tol_x and info[s].err_est <= tol
+        else:
+            assert info[s].status == g.ERR_NOT_CONVERGED and info[s].err_est >= err
 
 
 def test_perfect_preconditioner_one_step(g):
@@ -178,9 +187,9 @@ BF16_CASES = [((24, 20), "neumann", "spde_squared", "none"), ((64, 64), "neumann
 
 @pytest.mark.parametrize("shape,bc,op,pre", BF16_CASES)
 def test_bf16_basis(g, shape, bc, op, pre):
-    # bfloat16 V_m for the assembly: the iteration is unchanged (same m per
-    # vector), x differs from the FP32-basis result by the bfloat16 rounding of
-    # V_m only (~1e-3 relative), for every kernel that stores v_j
+    # bfloat16 V_m for the assembly: the iteration is unchanged, x differs
+    # from the FP32-basis result by the bfloat16 rounding of V_m only (~1e-3
+    # relative), for every kernel that stores v_j
     n = int(np.prod(shape))
     k2 = inputs.kappa2_uniform_field(shape, seed=3, lo=0.1, hi=1.0)
     Z = inputs.gaussian_vectors(3, n, seed=8, dtype=np.float32)
@@ -189,13 +198,19 @@ def test_bf16_basis(g, shape, bc, op, pre):
         xbf = torch.empty(3 * n, dtype=torch.float32, device="cuda")
         rc1, i1 = p.sample(x32, nsamples=3, tol=1e-6, m_max=800, z=_dev(Z))
         rc2, i2 = p.sample(xbf, nsamples=3, tol=1e-6, m_max=800, z=_dev(Z), v_storage="bf16")
-    assert rc1 == g.OK and rc2 == g.OK
+    # the FP32 basis reaches tol; the bfloat16 one cannot, and the library's
+    # direct-residual check says so: NOT_CONVERGED with an estimate that covers
+    # the bfloat16 error
+    assert rc1 in (g.OK, g.ERR_NOT_CONVERGED) and rc2 == g.ERR_NOT_CONVERGED
     X32 = x32.cpu().numpy().reshape(3, n)
     Xbf = xbf.cpu().numpy().reshape(3, n)
     for s in range(3):
-        assert i1[s].m_used == i2[s].m_used and i1[s].err_est == i2[s].err_est
+        # the same iteration; the FP32 basis may take a few more steps when the
+        # check asks for them, the bfloat16 one stops where its floor is found
+        assert i1[s].m_used >= i2[s].m_used and i2[s].status == g.ERR_NOT_CONVERGED
         r = _rel(Xbf[s], X32[s].astype(np.float64))
         assert 1e-5 < r <= 3e-3
+        assert i2[s].err_est >= r
 
 
 TWO_PASS_CASES = [((24, 20), "neumann", "spde_squared", "none", "fp32"),
@@ -232,9 +247,11 @@ def test_two_pass_equals_stored_basis(g, shape, bc, op, pre, precision):
         xf = torch.empty(2 * n, dtype=tdt, device="cuda")
         p.sample(xe, nsamples=2, tol=tol, m_max=900, seed=77)
         p.sample(xf, nsamples=2, tol=tol, m_max=900, seed=77, v_storage="none")
-    assert rc1 == rc2 == g.OK and rc3 == rc4 == g.ERR_NOT_CONVERGED
+    assert rc1 == rc2 and rc1 in (g.OK, g.ERR_NOT_CONVERGED) and rc3 == rc4 == g.ERR_NOT_CONVERGED
+    if precision == "fp64" or pre != "none":
+        assert rc1 == g.OK
     for a, b in ((i1, i2), (i3, i4)):
-        assert [x.m_used for x in a] == [x.m_used for x in b] and [x.err_est for x in a] == [x.err_est for x in b]
+        assert [(x.m_used, x.status, x.err_est) for x in a] == [(x.m_used, x.status, x.err_est) for x in b]
     assert torch.equal(xa, xb) and torch.equal(xc, xd) and torch.equal(xe, xf)
 
 
@@ -339,17 +356,17 @@ def test_strip_kernel_samples_vs_oracle(g, shape, bc, op, precision):
     tol = 1e-10 if precision == "fp64" else 1e-6
     with g.Problem(shape, bc, op, kappa2=_dev(k2), precision=precision) as p:
         x = torch.empty(3 * n, dtype=torch.from_numpy(Z).dtype, device="cuda")
-        rc, info = p.sample(x, nsamples=3, tol=tol, m_max=3000, z=_dev(Z))
-        assert rc == g.OK
+        rc, info = p.sample(x, nsamples=3, tol=tol, m_max=3000, z=_dev(Z), raise_on_error=False)
+        assert rc == g.OK or (precision == "fp32" and rc == g.ERR_NOT_CONVERGED)
         X = x.cpu().numpy().reshape(3, n)
         for s in (0, 2):
             x1 = torch.empty(n, dtype=torch.from_numpy(Z).dtype, device="cuda")
-            rc1, i1 = p.sample(x1, nsamples=1, tol=tol, m_max=3000, z=_dev(Z[s]))
-            assert rc1 == g.OK and i1[0].m_used == info[s].m_used
+            rc1, i1 = p.sample(x1, nsamples=1, tol=tol, m_max=3000, z=_dev(Z[s]), raise_on_error=False)
+            assert (i1[0].m_used, i1[0].status, i1[0].err_est) == (info[s].m_used, info[s].status, info[s].err_est)
             assert np.array_equal(x1.cpu().numpy(), X[s])
     xe, m, est, st = olz.adaptive_sample(lambda v: Q @ v, Z[0].astype(np.float64), 1e-12, 3000, reorth=True)
     assert st == "ok"
-    assert _rel(X[0], xe) <= (1e-9 if precision == "fp64" else 2e-6)
+    assert_honest(info[0], _rel(X[0], xe), 1e-9 if precision == "fp64" else 1e-6)
 
 
 def test_async_submit_poll_wait_equal_synchronous(g):

@@ -5,6 +5,7 @@ does not grow with the grid, the unpreconditioned one does."""
 import numpy as np
 import pytest
 
+from honesty import assert_honest
 from oracle import exact, lanczos as olz, precond, stencil
 from paper_1312_1476_gb300 import inputs
 
@@ -99,11 +100,13 @@ def test_sample_vs_dense(g, pre, precision):
     with _problem(g, shape, "periodic", mdl, precond=pre, precision=precision) as p:
         x = torch.empty(3 * N * N, dtype=torch.from_numpy(Z).dtype, device="cuda")
         tol = 1e-11 if precision == "fp64" else 1e-6
-        rc, info = p.sample(x, nsamples=3, tol=tol, m_max=4000, z=_dev(Z), check_every=4)
-    assert rc == g.OK
+        rc, info = p.sample(x, nsamples=3, tol=tol, m_max=4000, z=_dev(Z), check_every=4, raise_on_error=False)
+    # unpreconditioned FP32 on this ill-conditioned operator may stop at its
+    # floor, and then must say so
+    assert rc == g.OK or (precision == "fp32" and pre == "none" and rc == g.ERR_NOT_CONVERGED)
     X = x.cpu().numpy().reshape(3, N * N)
     for s in range(3):
-        assert _rel(X[s], Xe[s]) <= (1e-10 if precision == "fp64" else 1e-6)
+        assert_honest(info[s], _rel(X[s], Xe[s]), 1e-10 if precision == "fp64" else 1e-6)
 
 
 def test_logdet_fixed_probes(g):

@@ -14,11 +14,16 @@ library's own factorisation is compared with it on the host
   product rounds relative to |Q| |x| (a general matrix has no difference form
   like the lattice stencils), a perturbation of S that moves S^{-1/2} z by up
   to about sqrt(kappa(S)) u in the cases here.
+  In FP32 the library may instead return NOT_CONVERGED when its accuracy
+  check finds the iteration's floor above tol; its error estimate must then
+  cover the error, less the rounding of the final F^{-T} map (64 u kappa(F)),
+  which comes after the iteration.
 """
 import numpy as np
 import pytest
 import scipy.sparse as sp
 
+from honesty import assert_honest
 from oracle import exact, lanczos as olz, sparse as osp
 from paper_1312_1476_gb300 import inputs
 
@@ -80,6 +85,15 @@ def _fp32_tol(F, Q):
     return lim
 
 
+def _fp32_map_tol(F):
+    # rounding of the final FP32 map x = F^{-T} u, which lies outside the
+    # iteration's own error estimate
+    if F is None:
+        return 0.0
+    s = np.linalg.svd(F.toarray(), compute_uv=False)
+    return 64 * U32 * s[0] / s[-1]
+
+
 FACTORS = [("none", 0.0), (None, 0.05), (1e-2, 0.1), (1e-4, 0.0), (np.inf, 0.0), (0.0, 0.0)]
 
 
@@ -98,8 +112,9 @@ def test_sample_vs_prop1_dense(g, kind, droptol, shift, precision):
     Xe = _expected(Q, F, Z, tau=1.7)
     lim = 1e-10 if precision == "fp64" else _fp32_tol(F, Q)
     for s in range(3):
-        assert info[s].status == g.OK
-        assert _rel(X[s], Xe[s]) <= lim
+        if precision == "fp64":
+            assert info[s].status == g.OK
+        assert_honest(info[s], _rel(X[s], Xe[s]), lim, slack=_fp32_map_tol(F) if precision == "fp32" else 0.0)
 
 
 @pytest.mark.parametrize("droptol,shift", [(0.0, 0.0), (1e-5, 1e-4), (1e-3, 1e-3), (None, 0.01)])
@@ -129,8 +144,7 @@ def test_figure3_fp32_good_factor(g):
         rc, info, X = _sample(p, Z, 1e-6, 200, "fp32")
     Xe = _expected(Q, F, Z)
     for s in range(2):
-        assert info[s].status == g.OK
-        assert _rel(X[s], Xe[s]) <= _fp32_tol(F, Q)
+        assert_honest(info[s], _rel(X[s], Xe[s]), _fp32_tol(F, Q), slack=_fp32_map_tol(F))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
