@@ -73,6 +73,11 @@ class GmrfSolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class GmrfServerOpts(ctypes.Structure):
+    _fields_ = [("nslots", ctypes.c_int32), ("m_max", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class GmrfTuning(ctypes.Structure):
     _fields_ = [("block_width", ctypes.c_int32), ("zchunk", ctypes.c_int32), ("vec_steps_per_s", ctypes.c_double),
                 ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -114,6 +119,14 @@ def _load():
         "gmrf_create_sparse": (ctypes.c_int, [ctypes.POINTER(GmrfSparseDesc), P, ctypes.POINTER(P)]),
         "gmrf_ichol": (ctypes.c_int, [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                       P, P, P, ctypes.POINTER(ctypes.c_int64)]),
+        "gmrf_server_create": (ctypes.c_int, [P, ctypes.POINTER(GmrfServerOpts), ctypes.POINTER(P)]),
+        "gmrf_server_submit": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double, P,
+                                              ctypes.POINTER(ctypes.c_int64)]),
+        "gmrf_server_step": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "gmrf_server_poll": (ctypes.c_int, [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(GmrfResultInfo),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "gmrf_server_destroy": (None, [P]),
         "gmrf_destroy": (None, [P]),
         "gmrf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -219,6 +232,8 @@ class Problem:
         return np.float64 if self.precision == "fp64" else np.float32
 
     def close(self):
+        for sv in list(getattr(self, "_servers", [])):
+            sv.close()                  # a server is destroyed before its problem
         if self._h:
             _lib.gmrf_destroy(self._h)  # runs what was submitted first
             self._h = ctypes.c_void_p()
@@ -373,6 +388,90 @@ class Problem:
         rc = _lib.gmrf_apply(self._h, int(which), int(nvec), _ptr(v), _ptr(y))
         if rc != OK:
             raise GmrfError(rc, "gmrf_apply")
+
+
+class Server:
+    """Continuous batching over one problem (gmrf_server_*): a table of
+    ``nslots`` resident vector slots that the requests' samples and probes
+    share; see include/gmrf.h.  While it exists the problem serves it alone."""
+
+    def __init__(self, prob, nslots, m_max=300, tol=1e-6, check_every=16):
+        self.prob = prob
+        self._h = ctypes.c_void_p()
+        o = GmrfServerOpts(int(nslots), int(m_max), float(tol), int(check_every), 0)
+        rc = _lib.gmrf_server_create(prob._h, ctypes.byref(o), ctypes.byref(self._h))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_server_create")
+        self._keep = {}  # request id -> output buffer (kept alive until polled)
+        if not hasattr(prob, "_servers"):
+            prob._servers = []
+        prob._servers.append(self)
+
+    def submit_sample(self, out, count, seed, tau=1.0):
+        """count samples (the streams of Problem.sample(seed=seed)) into the
+        device buffer ``out`` [count][n]; returns the request id."""
+        r = ctypes.c_int64()
+        rc = _lib.gmrf_server_submit(self._h, 0, int(count), int(seed) & (2 ** 64 - 1), float(tau), _ptr(out),
+                                     ctypes.byref(r))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_server_submit")
+        self._keep[r.value] = (out, int(count))
+        return r.value
+
+    def submit_logdet(self, nprobes, seed, tau=1.0):
+        """A log det with nprobes Rademacher probes (Problem.logdet's streams)."""
+        r = ctypes.c_int64()
+        rc = _lib.gmrf_server_submit(self._h, 1, int(nprobes), int(seed) & (2 ** 64 - 1), float(tau), None,
+                                     ctypes.byref(r))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_server_submit")
+        self._keep[r.value] = (None, int(nprobes))
+        return r.value
+
+    def step(self):
+        """One round: admit, run check_every steps, finish; returns the number
+        of vectors running or waiting."""
+        a = ctypes.c_int32()
+        rc = _lib.gmrf_server_step(self._h, ctypes.byref(a))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_server_step")
+        return a.value
+
+    def poll(self, req):
+        """None while request req runs; then (result code, list of SampleInfo,
+        logdet, std_err) and the request is forgotten."""
+        done, res = ctypes.c_int32(), ctypes.c_int32()
+        count = self._keep[req][1]
+        info = (GmrfResultInfo * count)()
+        ld, se = ctypes.c_double(), ctypes.c_double()
+        rc = _lib.gmrf_server_poll(self._h, int(req), ctypes.byref(done), ctypes.byref(res), info, ctypes.byref(ld),
+                                   ctypes.byref(se))
+        if rc != OK:
+            raise GmrfError(rc, "gmrf_server_poll")
+        if not done.value:
+            return None
+        del self._keep[req]
+        return res.value, [SampleInfo(i.m_used, i.status, i.err_est) for i in info], ld.value, se.value
+
+    def close(self):
+        if self._h:
+            _lib.gmrf_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._keep = {}
+        if self in getattr(self.prob, "_servers", []):
+            self.prob._servers.remove(self)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Ticket:
