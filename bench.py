@@ -555,7 +555,7 @@ def measure_variants(args, gmrf, torch, flush, peak):
         out["3d_256"]["cpu_oracle"] = cpu_oracle_rate("3d_128", out["3d_256"]["m_mean"])
     out["table1"] = measure_table1(gmrf, torch)
     out["figure3_ichol"] = measure_figure3(gmrf, torch, timed, cpu=not getattr(args, "no_cpu_baseline", False))
-    out["serving"] = measure_serving()
+    out["serving"] = measure_serving(nreq=getattr(args, "serving_requests", 1000))
     return out
 
 
@@ -704,47 +704,55 @@ def measure_table1(gmrf, torch):
                                      "note": "the paper's prior is unspecified; counts are context"}}
 
 
-def measure_serving(nreq=32):
-    """Poisson request stream of the serving mix (2-D SPDE 128^2..1024^2 with
-    the mirror preconditioner, 3-D 7-point 64^3..128^3, tau ~ U[0.5, 5], 1-8
-    samples or a log det with 16-64 probes, tol 1e-6), served with continuous
-    admission at 0.5x and 1x the measured saturation rate (block width and
-    3-D z chunk from the library's autotuner per grid shape), against one
-    request and one sample at a time in FP64 on the same stream."""
+def measure_serving(nreq=1000, baseline_nreq=24):
+    """Config 5: a Poisson request stream of the serving mix (2-D SPDE
+    128^2..1024^2 with the mirror preconditioner, 3-D 7-point 64^3..128^3,
+    kappa^2 field and tau ~ U[0.5, 5] per request, 1-64 samples or a log det
+    with 16-64 probes, tol 1e-6), served with continuous batching (the
+    library's slot server: requests' vectors share launches and enter slots as
+    they free up) at 0.25x, 0.5x, 1x and 2x the measured saturation rate, with
+    nreq requests per rate; the same stream without packing (one library call
+    per request, up to 16 in flight) at 1x and 2x; and the one-request,
+    one-sample-at-a-time FP64 baseline at 0.25x on a bounded prefix of the
+    stream (baseline_nreq requests: it saturates far below these rates)."""
     from paper_1312_1476_gb300 import serve
 
-    def stream(rate):
-        return serve.make_mix(nreq, rate=rate, seed=4, max_samples=8)
+    def stream(rate, count):
+        return serve.make_mix(count, rate=rate, seed=4)
 
-    res = {}
-    srv = serve.Server(max_inflight=16)
-    burst = stream(1e6)
-    for r in burst:
-        r.arrival = 0.0
-    srv.prepare(burst)
-    srv.serve(burst[:4], realtime=False)
-    _, sat = srv.serve(burst, realtime=False)
-    sat_rate = nreq / sat["wall_s"]
-    res["saturation"] = dict(sat, rate_req_per_s=sat_rate)
-    for frac in (0.5, 1.0):
-        reqs = stream(frac * sat_rate)
-        srv.prepare(reqs)
-        _, met = srv.serve(reqs, realtime=True)
-        res["rate_%.1fx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
-    base = serve.Server(max_inflight=1, precision="fp64", block_width=1)
-    reqs = stream(0.5 * sat_rate)
+    res = {"requests_per_rate": nreq}
+    srv = serve.Server(mode="batched")
+    try:
+        burst = stream(1e6, nreq)
+        for r in burst:
+            r.arrival = 0.0
+        srv.prepare(burst)
+        srv.serve(burst[:6], realtime=False)  # engines and graphs of the first grids
+        _, sat = srv.serve(burst, realtime=False)
+        sat_rate = nreq / sat["wall_s"]
+        res["saturation"] = dict(sat, rate_req_per_s=sat_rate)
+        for frac in (0.25, 0.5, 1.0, 2.0):
+            reqs = stream(frac * sat_rate, nreq)
+            srv.prepare(reqs)
+            _, met = srv.serve(reqs, realtime=True)
+            res["packed_rate_%gx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
+    finally:
+        srv.close()
+    off = serve.Server(mode="direct", max_inflight=16)
+    for frac in (1.0, 2.0):
+        reqs = stream(frac * sat_rate, nreq)
+        off.prepare(reqs)
+        _, met = off.serve(reqs, realtime=True)
+        res["unpacked_rate_%gx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
+    base = serve.Server(mode="direct", max_inflight=1, precision="fp64", block_width=1)
+    reqs = stream(0.25 * sat_rate, baseline_nreq)
     base.prepare(reqs, tune=False)
-    base.serve(reqs[:2], realtime=False)
     _, met = base.serve(reqs, realtime=True)
-    res["fp64_one_at_a_time_rate_0.5x"] = dict(met, rate_req_per_s=0.5 * sat_rate)
-    # the same stream with a fifth of the requests turned into linear solves
-    # (Section 5.1's mean solve, 1-8 seeded right-hand sides), at 0.5x
-    reqs = serve.make_mix(nreq, rate=0.5 * sat_rate, seed=4, max_samples=8, p_logdet=0.25, p_solve=0.2)
-    srv.prepare(reqs)
-    _, met = srv.serve(reqs, realtime=True)
-    res["with_solves_rate_0.5x"] = dict(met, rate_req_per_s=0.5 * sat_rate)
-    res["workload"] = ("%d requests per run; samples and log dets of 2-D SPDE (mirror M) and 3-D 7-point GMRFs of "
-                       "mixed sizes (with_solves: 20%% of them linear solves); latency = completion - arrival" % nreq)
+    res["fp64_one_at_a_time_rate_0.25x"] = dict(met, rate_req_per_s=0.25 * sat_rate)
+    res["workload"] = ("config 5 mix: samples (1-64) and log dets (16-64 probes) of 2-D SPDE (mirror M, 128^2-1024^2) "
+                       "and 3-D 7-point (64^3-128^3) GMRFs, kappa^2 and tau per request, tol 1e-6; latency = "
+                       "completion - arrival; packed = continuous batching in the library's slot server, unpacked "
+                       "= one library call per request")
     return res
 
 
@@ -790,7 +798,16 @@ def main():
     ap.add_argument("--check-every", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="headline workload only")
+    ap.add_argument("--serving-requests", type=int, default=1000, help="requests per rate of the serving sweep")
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving sweep (config 5)")
     args = ap.parse_args()
+    if args.serving_only:
+        import torch
+        from paper_1312_1476_gb300 import _build
+        _build.build()
+        torch.cuda.init()
+        print(json.dumps({"serving": measure_serving(nreq=args.serving_requests)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -1,22 +1,33 @@
-"""Request serving with continuous admission on one GPU.
+"""Request serving with continuous batching on one GPU.
 
 Requests ask for samples x ~= Q^{-1/2} z (Algorithm 1; Proposition 1 for the
-preconditioned 2-D operator) or for log det Q (Section 6) of a lattice GMRF
-drawn per request: a 2-D SPDE-type field (Q = tau (K - Lap)^2, zero-Neumann,
-mirror-preconditioned) or a 3-D 7-point field (Q = tau (K + L), Dirichlet).
+preconditioned 2-D operator), for log det Q (Section 6) or for linear solves
+x = Q^{-1} b (Section 5.1) of a lattice GMRF drawn per request: a 2-D
+SPDE-type field (Q = tau (K - Lap)^2, zero-Neumann, mirror-preconditioned) or a
+3-D 7-point field (Q = tau (K + L), Dirichlet).
 
-Scheduling: a request is admitted when its estimated device memory (Lanczos
-basis, scalars, workspaces) fits in the remaining budget; admitted requests
-run concurrently, each on its own problem and CUDA stream, so their kernels
-overlap on the device.  A request's samples are computed in chunks small
-enough to stay inside the memory it was admitted with, and its Lanczos state
-stays on the device for the whole call.  When a request finishes, its memory
-returns to the budget and waiting requests are admitted at once (arrivals are
-served while earlier requests are still running).
+Batched mode (the default).  Samples and log dets of one grid and one
+coefficient field share an engine: one problem (tau = 1) with the library's
+continuous-batching server (gmrf_server_*), a table of vector slots whose
+Lanczos state (bases, alpha/beta) stays resident on the device.  The vectors of
+every request of that engine share each launch of the step kernels; a
+request's vectors enter free slots as soon as slots free up, also while other
+vectors are in mid-iteration, and the request's tau is applied when its
+vectors finish.  Each engine is driven by its own host thread on its own CUDA
+stream, so the engines' kernels overlap on the device.  Engines are created
+when their first request arrives, sized by the memory budget (slots x basis
+bytes), and an idle engine is released when a new one needs its memory.
+Linear solves (which the server does not run) go through the direct mode.
+
+Direct mode: every request is one call of the library on its own problem and
+stream, admitted when its memory fits the budget (max_inflight at once); with
+max_inflight = 1, block_width = 1 and FP64 this is the one-request,
+one-sample-at-a-time baseline.
 
 Every result depends only on its own request (problem, seed, tolerance): the
-library's reductions have a fixed order per vector, so a request returns the
-same bits alone and in any mix (tests/test_gpu_serve.py).
+library's reductions have a fixed order per vector and the server's results
+are bitwise those of the synchronous calls, so a request returns the same bits
+alone and in any mix (tests/test_gpu_serve.py).
 """
 from __future__ import annotations
 
@@ -102,13 +113,92 @@ class FieldPool:
             return self.cache[key]
 
 
+class Engine:
+    """One grid and field: a problem with tau = 1 and its library server
+    (gmrf_server_*), driven by its own host thread and CUDA stream."""
+
+    def __init__(self, owner, key, k2, nslots, m_max):
+        torch, g = owner.torch, owner.g
+        self.owner, self.key, self.nslots, self.m_max = owner, key, nslots, m_max
+        shape = key[0]
+        self.n = int(np.prod(shape))
+        self.stream = torch.cuda.Stream()
+        self.prob = owner._problem(shape, k2, 1.0, self.stream)
+        self.server = g.Server(self.prob, nslots=nslots, m_max=m_max, tol=owner.tol, check_every=owner.check_every)
+        self.lock = threading.Lock()
+        self.wake = threading.Event()
+        self.active = {}       # library request id -> (Request, x)
+        self.last_used = time.perf_counter()
+        self.stop = False
+        self.error = None
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def busy(self):
+        with self.lock:
+            return bool(self.active)
+
+    def submit(self, req):
+        torch = self.owner.torch
+        dt = torch.float64 if self.owner.precision == "fp64" else torch.float32
+        with self.lock:
+            if req.kind == "sample":
+                x = torch.empty(req.count * self.n, dtype=dt, device="cuda")
+                rid = self.server.submit_sample(x, req.count, req.seed, req.tau)
+            else:
+                x = None
+                rid = self.server.submit_logdet(req.count, req.seed, req.tau)
+            self.active[rid] = (req, x)
+            self.last_used = time.perf_counter()
+        self.wake.set()
+
+    def _loop(self):
+        torch = self.owner.torch
+        with torch.cuda.stream(self.stream):
+            while not self.stop:
+                self.wake.wait(timeout=0.05)
+                with self.lock:
+                    if not self.active:
+                        self.wake.clear()
+                        continue
+                    try:
+                        left = self.server.step()
+                        finished = []
+                        for rid, (req, x) in list(self.active.items()):
+                            r = self.server.poll(rid)
+                            if r is not None:
+                                finished.append((rid, req, x, r))
+                                del self.active[rid]
+                        if left == 0 and not self.active:
+                            self.wake.clear()
+                        self.last_used = time.perf_counter()
+                    except Exception as e:  # surfaced by the dispatcher
+                        self.error = e
+                        self.stop = True
+                        finished = []
+                for rid, req, x, (rc, infos, ld, se) in finished:
+                    self.owner._complete(req, rc, infos, x, ld, se)
+
+    def close(self):
+        self.stop = True
+        self.wake.set()
+        self.thread.join()
+        self.server.close()
+        self.prob.close()
+
+
 class Server:
-    """Continuous-admission server over the C-ABI library."""
+    """Serving over the C-ABI library: batched engines (continuous batching of
+    samples and log dets into shared launches) or direct per-request calls."""
 
-    M_MAX_2D = 300
-    M_MAX_3D = 300
+    # Lanczos steps a vector may take: the mirror-preconditioned 2-D mix needs
+    # 20-80 at tol 1e-6 and the 3-D mix 30-60 (plus the accuracy check's extra
+    # steps), so 128 bounds both and keeps the resident bases small
+    M_MAX_2D = 128
+    M_MAX_3D = 128
 
-    def __init__(self, mem_budget=None, max_inflight=16, precision="fp32", chunk_bytes=8 << 30, block_width=None):
+    def __init__(self, mem_budget=None, max_inflight=16, precision="fp32", chunk_bytes=8 << 30, block_width=None,
+                 mode="batched", nslots_max=64, check_every=16, tol=1e-6):
         import torch
         from . import gmrf
         self.torch = torch
@@ -119,23 +209,33 @@ class Server:
         self.precision = precision
         self.chunk_bytes = chunk_bytes
         self.fields = FieldPool(torch)
-        self.tuning = {}   # grid shape -> block width / z chunk from the library's autotuner
+        self.tuning = {}   # grid shape -> block width / z chunk from the library's autotuner (direct mode)
         self.block_width = block_width  # fixed vectors per launch (e.g. 1: one sample at a time)
+        self.mode = mode
+        self.nslots_max = nslots_max
+        self.check_every = check_every
+        self.tol = tol
         self.used = 0
         self.cv = threading.Condition()
+        self.engines = {}  # (shape, field id) -> Engine
 
-    def _m_max(self, req):
-        return self.M_MAX_2D if len(req.shape) == 2 else self.M_MAX_3D
+    def _m_max(self, req_or_shape):
+        shape = req_or_shape.shape if hasattr(req_or_shape, "shape") else req_or_shape
+        return self.M_MAX_2D if len(shape) == 2 else self.M_MAX_3D
 
+    # ---- memory model
     def vec_bytes(self, req):
         """Device bytes one vector of this request needs inside the library."""
-        n = int(np.prod(req.shape))
+        return self._slot_bytes(req.shape, 2 if req.kind == "logdet" and self.mode == "direct" else None)
+
+    def _slot_bytes(self, shape, slots=None):
+        n = int(np.prod(shape))
         es = 8 if self.precision == "fp64" else 4
-        m = self._m_max(req)
-        slots = 2 if req.kind == "logdet" else m + 1
-        b = (slots + 4) * n * es + 2 * m * 384 * 8 + 64 * m
-        if len(req.shape) == 2:
-            b += 3 * n * es + 2 * req.shape[0] * es   # spectrum, g, w workspaces
+        m = self._m_max(shape)
+        slots = m + 1 if slots is None else slots
+        b = (slots + 6) * n * es + 2 * m * 384 * 8 + 64 * m
+        if len(shape) == 2:
+            b += 3 * n * es + 2 * shape[0] * es   # spectrum, g, w workspaces
         return b
 
     def chunk(self, req):
@@ -144,8 +244,25 @@ class Server:
         return min(c, self.block_width) if self.block_width else c
 
     def need(self, req):
+        """Budget a request takes in direct mode."""
         return self.chunk(req) * self.vec_bytes(req) + 8 * int(np.prod(req.shape))
 
+    def engine_slots(self, shape):
+        """Slots of an engine: as many as a quarter of the budget holds, 8 .. nslots_max."""
+        per = self._slot_bytes(shape)
+        return int(max(8, min(self.nslots_max, (self.budget // 4) // per)))
+
+    # ---- results
+    def _complete(self, req, rc, infos, x, ld, se):
+        end = time.perf_counter()
+        res = Result(req.rid, req.kind, req.shape, req.count, (end - self._t0 - req.arrival) * 1e3, 0.0,
+                     (end - self._t0) * 1e3, [i.m_used for i in infos], rc, x=x, logdet=ld if req.kind == "logdet"
+                     else None, std_err=se if req.kind == "logdet" else None)
+        with self.cv:
+            self._results[req.rid] = res
+            self.cv.notify_all()
+
+    # ---- direct mode: one library call per request
     def _run(self, req, t0):
         torch, g = self.torch, self.g
         start = time.perf_counter()
@@ -162,27 +279,22 @@ class Server:
         dt = torch.float64 if self.precision == "fp64" else torch.float32
         res = Result(req.rid, req.kind, shape, req.count, 0.0, 0.0, 0.0, [], 0)
         with prob:
-            c = self.chunk(req)
             if req.kind == "sample":
+                # one call: the library chunks the vectors by the tuned block width
                 x = torch.empty(req.count * n, dtype=dt, device="cuda")
-                for s0 in range(0, req.count, c):
-                    cc = min(c, req.count - s0)
-                    rc, info = prob.sample(x[s0 * n:(s0 + cc) * n], nsamples=cc, tol=req.tol, m_max=self._m_max(req),
-                                           seed=(req.seed + s0) & 0x7FFFFFFF, raise_on_error=False)
-                    res.m_used += [i.m_used for i in info]
-                    res.status = min(res.status, rc)
+                rc, info = prob.sample(x, nsamples=req.count, tol=req.tol, m_max=self._m_max(req), seed=req.seed,
+                                       raise_on_error=False)
+                res.m_used = [i.m_used for i in info]
+                res.status = rc
                 res.x = x
             elif req.kind == "solve":
                 # seeded right-hand sides from the library's Philox stream, on the problem's stream
                 b = torch.empty(req.count * n, dtype=dt, device="cuda")
                 g.rng(0, req.count, n, req.seed, b, precision=self.precision, stream=stream.cuda_stream)
                 x = torch.empty_like(b)
-                for s0 in range(0, req.count, c):
-                    cc = min(c, req.count - s0)
-                    rc, info = prob.solve(b[s0 * n:(s0 + cc) * n], x[s0 * n:(s0 + cc) * n], nrhs=cc, tol=req.tol,
-                                          m_max=self._m_max(req), raise_on_error=False)
-                    res.m_used += [i.m_used for i in info]
-                    res.status = min(res.status, rc)
+                rc, info = prob.solve(b, x, nrhs=req.count, tol=req.tol, m_max=self._m_max(req), raise_on_error=False)
+                res.m_used = [i.m_used for i in info]
+                res.status = rc
                 res.x = x
             else:
                 ld, se, q, info, rc = prob.logdet(nprobes=req.count, tol=req.tol, m_max=self._m_max(req),
@@ -207,12 +319,13 @@ class Server:
 
     def prepare(self, requests, tune=True):
         """Generates the coefficient fields of `requests` (their inputs) and
-        the library's per-process state before serving starts; with `tune`,
-        runs the library's autotuner once per grid shape of the stream (block
-        width up to the largest request count of that shape, 3-D z chunk)."""
+        the library's per-process state before serving starts; in direct mode
+        with `tune`, runs the library's autotuner once per grid shape of the
+        stream (block width up to the largest request count of that shape,
+        3-D z chunk)."""
         for r in requests:
             self.fields.get(r.shape, r.field_id)
-        if tune:
+        if tune and self.mode == "direct":
             widest = {}
             for r in requests:
                 widest[r.shape] = max(widest.get(r.shape, 1), r.count)
@@ -225,31 +338,79 @@ class Server:
                     self.tuning[shape] = prob.autotune(widest[shape])
         self.torch.cuda.synchronize()
 
+    # ---- batched mode: engines
+    def _engine_for(self, req):
+        """The engine of the request's grid and field, created (and idle
+        engines released) within the memory budget; None while it does not fit."""
+        key = (req.shape, req.field_id)
+        if key in self.engines:
+            return self.engines[key]
+        ns = self.engine_slots(req.shape)
+        need = ns * self._slot_bytes(req.shape)
+        used = sum(e.nslots * self._slot_bytes(e.key[0]) for e in self.engines.values())
+        if used + need > self.budget:
+            for k, e in sorted(self.engines.items(), key=lambda kv: kv[1].last_used):
+                if used + need <= self.budget:
+                    break
+                if not e.busy():
+                    e.close()
+                    del self.engines[k]
+                    used -= e.nslots * self._slot_bytes(k[0])
+        if used + need > self.budget and self.engines:
+            return None
+        e = Engine(self, key, self.fields.get(req.shape, req.field_id), ns, self._m_max(req.shape))
+        self.engines[key] = e
+        return e
+
+    def close(self):
+        for e in self.engines.values():
+            e.close()
+        self.engines = {}
+
     def serve(self, requests, realtime=True):
         """Serves `requests` (arrival times in seconds from now).  Returns the
         results in request order and a metrics dict."""
         reqs = sorted(requests)
-        pending = []  # min-heap by arrival
-        results = {}
+        self._results = {}
         t0 = time.perf_counter()
+        self._t0 = t0
+        direct = [] if self.mode == "batched" else None
+        waiting = []  # batched requests whose engine does not fit yet
         inflight = [0]
+        futures = {}
 
-        def done(req, need, fut):
+        def done_direct(need):
             with self.cv:
                 self.used -= need
                 inflight[0] -= 1
                 self.cv.notify_all()
 
         with ThreadPoolExecutor(max_workers=self.max_inflight) as ex:
-            futures = {}
             i = 0
-            while i < len(reqs) or pending:
+            pending = []  # direct-mode heap by arrival
+            while True:
                 now = time.perf_counter() - t0
                 while i < len(reqs) and (not realtime or reqs[i].arrival <= now):
-                    heapq.heappush(pending, reqs[i])
+                    r = reqs[i]
                     i += 1
+                    if self.mode == "batched" and r.kind != "solve":
+                        waiting.append(r)
+                    else:
+                        heapq.heappush(pending, r)
+                # batched: hand arrivals to their engines
+                still = []
+                for r in waiting:
+                    e = self._engine_for(r)
+                    if e is None:
+                        still.append(r)
+                    else:
+                        e.submit(r)
+                waiting = still
+                for e in self.engines.values():
+                    if e.error is not None:
+                        raise e.error
                 with self.cv:
-                    # admit in arrival order while memory and slots allow
+                    # direct: admit in arrival order while memory and slots allow
                     while pending:
                         req = pending[0]
                         need = self.need(req)
@@ -259,16 +420,20 @@ class Server:
                         self.used += need
                         inflight[0] += 1
                         fut = ex.submit(self._run, req, t0)
-                        fut.add_done_callback(lambda f, r=req, nd=need: done(r, nd, f))
+                        fut.add_done_callback(lambda f, nd=need: done_direct(nd))
                         futures[req.rid] = fut
+                    for rid, fut in list(futures.items()):
+                        if fut.done():
+                            self._results[rid] = fut.result()
+                            del futures[rid]
+                    if i >= len(reqs) and not pending and not waiting and not futures and \
+                            len(self._results) == len(reqs):
+                        break
                     nxt = reqs[i].arrival - (time.perf_counter() - t0) if i < len(reqs) else None
-                    if pending or nxt is None or nxt > 0:
-                        timeout = 0.05 if nxt is None else max(0.0, min(0.05, nxt))
-                        self.cv.wait(timeout=timeout)
-            for rid, fut in futures.items():
-                results[rid] = fut.result()
+                    timeout = 0.01 if nxt is None else max(0.0, min(0.01, nxt))
+                    self.cv.wait(timeout=timeout)
         wall = time.perf_counter() - t0
-        out = [results[r.rid] for r in requests]
+        out = [self._results[r.rid] for r in requests]
         lat = np.array([r.latency_ms for r in out])
         nsamp = sum(r.count for r in out if r.kind == "sample")
         nld = sum(1 for r in out if r.kind == "logdet")
@@ -276,5 +441,5 @@ class Server:
         metrics = {"requests": len(out), "wall_s": wall, "samples": nsamp, "samples_per_s": nsamp / wall,
                    "logdets": nld, "logdets_per_s": nld / wall, "solves": nsol, "solves_per_s": nsol / wall,
                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                   "statuses": sorted(set(r.status for r in out))}
+                   "statuses": sorted(set(r.status for r in out)), "mode": self.mode}
         return out, metrics
