@@ -162,7 +162,7 @@ struct VecState {
   int m_min;      // the stopping rule may end the iteration only once m >= m_min (0: any m)
   int pad_;
   double znorm;   // ||z||
-  double d_prev;  // LDL^T pivot d_{m-1} of T_m
+  double d_prev;  // 1 / d_{m-1}, the reciprocal of the LDL^T pivot d_{m-1} of T_m
   double u_prev;  // u_{m-1} = (L^{-1} e_1)_{m-1}
   double energy;  // e_1^T T_m^{-1} e_1 = sum_i u_i^2 / d_i
   double theta;   // smallest Ritz value theta_min (upper estimate)
@@ -308,7 +308,10 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
     beta[mo + j] = b;
     alpha_f[mo + j] = (float)a;
     beta2_f[mo + j] = (float)(b * b);
-    // LDL^T of T_m: d_0 = a_0, d_j = a_j - b_{j-1}^2 / d_{j-1}; u_0 = 1, u_j = -(b_{j-1}/d_{j-1}) u_{j-1}
+    // LDL^T of T_m: d_0 = a_0, d_j = a_j - b_{j-1}^2 / d_{j-1}; u_0 = 1, u_j = -(b_{j-1}/d_{j-1}) u_{j-1}.
+    // The state keeps 1 / d_{j-1}, so that the step's FP64 chain holds one
+    // division (1 / d_j) and one for 1 / beta_j: GB300's FP64 divisions and
+    // square roots are slow, and this tail runs between every two steps.
     double d, u;
     if (j == 0) {
       d = a;
@@ -318,9 +321,9 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
       v.bmax = 0.0;
       v.theta = a;
     } else {
-      double bp = v.beta_last;
-      d = a - bp * bp / v.d_prev;
-      u = -(bp / v.d_prev) * v.u_prev;
+      const double r = v.beta_last * v.d_prev;  // b_{j-1} / d_{j-1}
+      d = a - v.beta_last * r;
+      u = -r * v.u_prev;
     }
     v.m = j + 1;
     v.beta_last = b;
@@ -333,10 +336,12 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
     } else if (d <= 0.0 || a <= 0.0) {
       v.status = GMRF_ERR_NOT_SPD;
     } else {
-      v.energy += u * u / d;
-      v.d_prev = d;
+      const double dinv = 1.0 / d;
+      v.energy += u * u * dinv;
+      v.d_prev = dinv;
       v.u_prev = u;
-      double pfac = b * fabs(u / d) / sqrt(v.energy);  // ||r_m|| / ||x_m||
+      const double rres = b * fabs(u) * dinv;          // ||r_m|| / ||z||
+      double pfac = rres * rsqrt(v.energy);             // ||r_m|| / ||x_m||
       if (b <= P.bd_tol * (v.amax + v.bmax)) {
         v.status = VS_DONE;  // invariant Krylov subspace: x_m is exact
         v.err_est = 0.0;
@@ -344,12 +349,11 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
       } else if (P.solve) {
         // linear solve: x_m = ||z|| V_m T_m^{-1} e_1 is the CG iterate, with
         // relative residual ||r_m|| / ||z|| = beta_m |e_m^T T_m^{-1} e_1|
-        const double rres = b * fabs(u / d);
         v.err_est = rres;
         if (rres <= P.tol) v.status = VS_DONE;
         else if (j + 1 >= P.m_max) v.status = GMRF_ERR_NOT_CONVERGED;
       } else {
-        double est_lb = pfac / sqrt(v.theta);  // theta >= theta_min(T_m): a lower bound of est
+        double est_lb = pfac * rsqrt(v.theta);  // theta >= theta_min(T_m): a lower bound of est
         v.err_est = est_lb;
         if (est_lb <= P.tol || j + 1 >= P.m_max) need = 1;
       }
@@ -366,7 +370,7 @@ __device__ static void finish_step(const StepParams& P, int j, int s, const Dots
       VecState v = st[s];
       v.theta = th;
       if (v.status == VS_RUNNING) {
-        double est = s_pfac / sqrt(th);
+        double est = s_pfac * rsqrt(th);
         v.err_est = est;
         if (est <= P.tol && j + 1 >= v.m_min) v.status = VS_DONE;
         else if (j + 1 >= P.m_max) v.status = GMRF_ERR_NOT_CONVERGED;
