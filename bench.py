@@ -70,7 +70,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -260,6 +260,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     prob = gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2, precond=args.precond, precision="fp32",
                         stream=stream.cuda_stream)
+    if args.host_loop:
+        prob.set_tuning(host_loop=True)
     x = torch.empty(n, dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     seed0 = replicas.replica_seed(1000, rank)
@@ -310,6 +312,15 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     value = world * args.steps / (t_max / 1e3)
+    # the host-driven iteration on the same steps, for comparison (not the value)
+    if args.host_loop:
+        loop = {"used": "host-replayed step graphs", "ms_per_step_host_loop": round(dev_ms / args.steps, 4)}
+    else:
+        prob.set_tuning(host_loop=True)
+        host_ms = timed_region(False)[0]
+        prob.set_tuning(host_loop=False)
+        loop = {"used": "device-side WHILE node", "ms_per_step_device_loop": round(dev_ms / args.steps, 4),
+                "ms_per_step_host_loop": round(host_ms / args.steps, 4)}
     # roofline: the same K steps again with CUDA events around every kernel
     gmrf.trace_reset()
     traced_ms, _, _, _ = timed_region(True)
@@ -374,6 +385,7 @@ def run_ours(args):
             "e2e": {"value": round(world * args.steps / (e2e_ms / 1e3), 3), "unit": "samples/s",
                     "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n},
             "gpu_launches": int(launches),
+            "lanczos_loop": loop,
             "clocks": clk,
             "wall_s_timed_region": round(t_wall, 3),
         }
@@ -732,6 +744,7 @@ def measure_serving(nreq=1000, baseline_nreq=24):
     per request, up to 16 in flight) at 1x and 2x; and the one-request,
     one-sample-at-a-time FP64 baseline at 0.25x on a bounded prefix of the
     stream (baseline_nreq requests: it saturates far below these rates)."""
+    import torch
     from paper_1312_1476_gb300 import serve
 
     def stream(rate, count):
@@ -745,22 +758,26 @@ def measure_serving(nreq=1000, baseline_nreq=24):
             r.arrival = 0.0
         srv.prepare(burst)
         srv.serve(burst[:6], realtime=False)  # engines and graphs of the first grids
-        _, sat = srv.serve(burst, realtime=False)
+        sat = srv.serve(burst, realtime=False)[1]  # the results (device outputs) are dropped at once
         sat_rate = nreq / sat["wall_s"]
         res["saturation"] = dict(sat, rate_req_per_s=sat_rate)
         for frac in (0.25, 0.5, 1.0, 2.0):
             reqs = stream(frac * sat_rate, nreq)
             srv.prepare(reqs)
-            _, met = srv.serve(reqs, realtime=True)
+            met = srv.serve(reqs, realtime=True)[1]
             res["packed_rate_%gx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
     finally:
         srv.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()  # outputs cached by torch go back to the device for the library's own allocations
     off = serve.Server(mode="direct", max_inflight=16)
     for frac in (1.0, 2.0):
         reqs = stream(frac * sat_rate, nreq)
         off.prepare(reqs)
-        _, met = off.serve(reqs, realtime=True)
+        met = off.serve(reqs, realtime=True)[1]
         res["unpacked_rate_%gx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
     base = serve.Server(mode="direct", max_inflight=1, precision="fp64", block_width=1)
     reqs = stream(0.25 * sat_rate, baseline_nreq)
     base.prepare(reqs, tune=False)
@@ -808,12 +825,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precond", choices=["circulant", "mirror"], default="mirror")
     ap.add_argument("--check-every", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-replayed step graphs instead of the device-side loop (for per-kernel profilers)")
     ap.add_argument("--no-variants", action="store_true", help="headline workload only")
     ap.add_argument("--serving-requests", type=int, default=1000, help="requests per rate of the serving sweep")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving sweep (config 5)")

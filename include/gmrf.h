@@ -413,7 +413,15 @@ typedef struct {
   int32_t zchunk;
   double vec_steps_per_s; /* gmrf_autotune: measured rate of the chosen configuration */
   int32_t candidates;     /* gmrf_autotune: configurations timed */
-  int32_t reserved;       /* must be 0 for gmrf_set_tuning */
+  int32_t host_loop;      /* 0 (default): with launch timing off, the Lanczos
+                           * steps of a call run as one graph launch whose
+                           * conditional WHILE node repeats a step until no
+                           * vector is running (one host wait per call);
+                           * 1: the host replays graphs of check_every steps
+                           * and reads the vector states between them (the
+                           * mode for per-kernel profilers).  Results are
+                           * bitwise the same.  gmrf_autotune leaves it as
+                           * set; other values are GMRF_ERR_INVALID. */
 } gmrf_tuning;
 
 /* Times short Lanczos runs (8 untimed + 8 timed steps on Rademacher vectors,
@@ -429,7 +437,7 @@ int gmrf_autotune(gmrf_problem* p, int32_t nvec_max, gmrf_tuning* out);
 
 /* Sets the tuning explicitly (e.g. one found by gmrf_autotune on another
  * problem with the same grid).  GMRF_ERR_INVALID for negative fields or a
- * non-zero reserved. */
+ * host_loop other than 0 or 1. */
 int gmrf_set_tuning(gmrf_problem* p, const gmrf_tuning* t);
 
 /* ---- General sparse Q with an incomplete-Cholesky preconditioner ----------

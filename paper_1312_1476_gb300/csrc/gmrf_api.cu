@@ -192,11 +192,127 @@ int launch_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, int
   return GMRF_OK;
 }
 
+// The device-side Lanczos loop: a graph whose WHILE node repeats a body of c
+// steps and a condition kernel until no vector is running, or for at most ceil(m_max/c)
+// + 2 condition evaluations, a bound it never reaches.  A call then needs one
+// launch and one host wait.  Returns GMRF_OK with G.exec == nullptr when the
+// runtime cannot build it (the caller then replays c-step graphs).
+int capture_loop(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, int c) {
+  StepGraph& G = p->graph;
+  const void* S = p->precond ? p->pre.S : nullptr;
+  if (G.exec && G.loop && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c &&
+      G.tol == P.tol &&
+      G.W0 == b.W[0] && G.V == b.V && G.Vb == b.Vb && G.st == b.st && G.S == S && G.partials == b.partials &&
+      !G.timed && G.zchunk == p->g.zchunk && G.Xacc == b.Xacc && G.xscale == b.xscale && G.solve == P.solve &&
+      G.Xacc2 == b.Xacc2 && G.y1 == b.y && G.y2 == b.y2)
+    return GMRF_OK;
+  G.reset();
+  CKR(ensure(p->loopctr, sizeof(int), p->ws));
+  cudaStream_t s = p->ws;
+  cudaGraph_t graph = nullptr;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRF_OK;
+  }
+  auto fail = [&]() {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    G.reset();
+    return GMRF_OK;  // the replayed graphs serve instead
+  };
+  // The condition starts at 0 on every launch; a condition kernel ahead of the
+  // WHILE node sets it (to 1 when some vector is running), and the one at the
+  // end of the body sets it for the next iteration.  So the loop can only run
+  // while the condition kernels run; the host checks the states afterwards.
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault) != cudaSuccess) return fail();
+  cudaMemsetParams mp = {};
+  mp.dst = p->loopctr.p;
+  mp.value = 0;
+  mp.elementSize = sizeof(int);
+  mp.width = 1;
+  mp.height = 1;
+  cudaGraphNode_t reset_node;
+  if (cudaGraphAddMemsetNode(&reset_node, graph, nullptr, 0, &mp) != cudaSuccess) return fail();
+  const int limit = (P.m_max + c - 1) / c + 2;  // condition evaluations: one ahead, one per body
+  void* kargs[5];
+  const VecState* st_arg = b.st;
+  int nvec_arg = b.nvec;
+  int* ctr_arg = (int*)p->loopctr.p;
+  int limit_arg = limit;
+  kargs[0] = &h;
+  kargs[1] = &st_arg;
+  kargs[2] = &nvec_arg;
+  kargs[3] = &ctr_arg;
+  kargs[4] = &limit_arg;
+  cudaKernelNodeParams kp = {};
+  kp.func = const_cast<void*>(loop_cond_kernel());
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(256);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = kargs;
+  cudaGraphNode_t first_cond;
+  if (cudaGraphAddKernelNode(&first_cond, graph, &reset_node, 1, &kp) != cudaSuccess) return fail();
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop_node;
+  if (cudaGraphAddNode(&loop_node, graph, &first_cond, nullptr, 1, &cp) != cudaSuccess) return fail();
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  trace_capture_begin(&G.tr);
+  if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    trace_capture_end();
+    return fail();
+  }
+  int r = launch_steps(p, b, P, c, s);
+  if (r == GMRF_OK && traced(KC_OTHER, s, 1, [&] {
+        return launch_loop_cond(h, b.st, b.nvec, (int*)p->loopctr.p, limit, s);
+      }) != cudaSuccess)
+    r = GMRF_ERR_CUDA;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &captured);
+  trace_capture_end();
+  if (r != GMRF_OK || e != cudaSuccess) return fail();
+  const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    G.exec = nullptr;
+    G.reset();
+    return GMRF_OK;
+  }
+  G.loop = true;
+  G.nvec = b.nvec;
+  G.nslots = b.nslots;
+  G.m_max = P.m_max;
+  G.c = c;
+  G.tol = P.tol;
+  G.solve = P.solve;
+  G.W0 = b.W[0];
+  G.V = b.V;
+  G.Vb = b.Vb;
+  G.zchunk = p->g.zchunk;
+  G.Xacc = b.Xacc;
+  G.Xacc2 = b.Xacc2;
+  G.y1 = b.y;
+  G.y2 = b.y2;
+  G.xscale = b.xscale;
+  G.st = b.st;
+  G.S = S;
+  G.partials = b.partials;
+  G.timed = false;
+  G.kernels_per_step = (p->precond && !p->sp ? 5 : 1) + (b.Xacc ? 1 : 0);
+  return GMRF_OK;
+}
+
 int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, int c) {
   StepGraph& G = p->graph;
   const bool timed = trace_timing_enabled();
   const void* S = p->precond ? p->pre.S : nullptr;
-  if (G.exec && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c && G.tol == P.tol &&
+  if (G.exec && !G.loop && G.nvec == b.nvec && G.nslots == b.nslots && G.m_max == P.m_max && G.c == c &&
+      G.tol == P.tol &&
       G.W0 == b.W[0] && G.V == b.V && G.Vb == b.Vb && G.st == b.st && G.S == S && G.partials == b.partials &&
       G.timed == timed && G.zchunk == p->g.zchunk && G.Xacc == b.Xacc && G.xscale == b.xscale &&
       G.solve == P.solve && G.Xacc2 == b.Xacc2 && G.y1 == b.y && G.y2 == b.y2)
@@ -242,6 +358,7 @@ int capture_steps(gmrf_problem* p, const LanczosBufs& b, const StepParams& P, in
   G.S = S;
   G.partials = b.partials;
   G.timed = timed;
+  G.loop = false;
   G.kernels_per_step = (p->precond && !p->sp ? 5 : 1) + (b.Xacc ? 1 : 0);
   return GMRF_OK;
 }
@@ -266,8 +383,32 @@ int run_lanczos(gmrf_problem* p, const LanczosBufs& b, double tol, int m_max, in
   const StepParams P = step_params(p, b, tol, m_max, solve);
   const int c = std::min(check_every > 0 ? check_every : 16, m_max);
   if (p->precond != GMRF_PREC_NONE) CKR(precond_prepare(p->pre, b.nvec, s));
-  CKR(capture_steps(p, b, P, c));
   StepGraph& G = p->graph;
+  if (!trace_timing_enabled() && !p->host_loop) {
+    // the device-side loop: one launch, one wait.  Its body runs at most 8
+    // steps: each WHILE iteration costs a few microseconds (the condition
+    // kernel and the body's launch), and a shorter body wastes fewer steps
+    // after the last vector stops (1024^2 headline: 4.24 ms per sample with
+    // 8-step bodies, 4.32 with 16, 4.60 with 1, 4.28 host-replayed).
+    CKR(capture_loop(p, b, P, std::min(c, 8)));
+    if (G.exec) {
+      int iters = 0;
+      CK(cudaGraphLaunch(G.exec, s));
+      CK(cudaMemcpyAsync(&iters, p->loopctr.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * b.nvec, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      // launch counts: the condition kernel ahead of the loop, then each
+      // iteration of the body (the counter holds both)
+      trace_begin(KC_OTHER, s, 1);
+      trace_end(KC_OTHER, s);
+      for (int k = 1; k < iters; ++k) trace_replayed(&G.tr, 0);
+      bool running = false;
+      for (int v = 0; v < b.nvec; ++v) running |= (p->st_host[v].status == VS_RUNNING);
+      if (!running) return GMRF_OK;
+      // not expected: the replayed graphs finish whatever is still running
+    }
+  }
+  CKR(capture_steps(p, b, P, c));
   int j = 0;
   while (j < m_max) {
     CK(cudaGraphLaunch(G.exec, s));
@@ -313,9 +454,10 @@ LanczosBufs sub_batch(const LanczosBufs& b, int off, int cnt, size_t n, size_t e
 // ||r_m|| without forming u_m.  In finite precision the recurrence keeps
 // shrinking while the residual of the computed u_m stops where the rounding of
 // the applies of A leaves it.  So after the iteration the library forms u_m
-// (in the same pass over V_m as x_m), computes r = z - A u_m directly (A in
-// FP64 for an FP32 stencil, whose products cancel heavily on a smooth u_m; in
-// the problem's precision otherwise) and one product t = A r, and estimates
+// (in the same pass over V_m as x_m), computes r = z - A u_m directly (for an
+// FP32 stencil in pairs of floats, since its products cancel heavily on a
+// smooth u_m; in the problem's precision otherwise) and one product t = A r in
+// the problem's precision (r no longer cancels), and estimates
 //     est_direct = sqrt(r^T A^{-1} r) / ||x_m||,
 // the square root of the quadratic form taken from the two-node Gauss-Radau
 // rule of the Lanczos step from r with the node fixed at theta_min (Golub and
@@ -326,13 +468,11 @@ LanczosBufs sub_batch(const LanczosBufs& b, int off, int cnt, size_t n, size_t e
 // weighs little, as it does in the error of x_m).  A vector is GMRF_OK only
 // if both estimates are <= tol; err_est reports the larger.
 
-// Bytes per vector of the check's buffers: z and u_cg in the problem's
-// precision, plus A u_cg in it, or u_cg and A u_cg in FP64 for an FP32
-// stencil problem.
+// Bytes per vector of the check's buffers: z, u_cg and r in the problem's
+// precision (t = A r goes into u_cg's buffer).
 size_t check_bytes_per_vec(const gmrf_problem* p) {
   const size_t n = p->g.n, es = esize(p);
-  const bool fp64_pair = !p->sp && p->precond == GMRF_PREC_NONE && !p->fp64;
-  return 2 * n * es + (fp64_pair ? 2 * n * sizeof(double) : n * es);
+  return 3 * n * es;  // z, u and r
 }
 
 // T_m^{-1} e_1 of the nvec vectors of b into p->ycg (stride m_max).
@@ -344,37 +484,79 @@ int check_tm(gmrf_problem* p, const LanczosBufs& b, cudaStream_t s) {
 }
 
 // For nvec vectors z, u [nvec][n] (problem precision, device): r = z - A u
-// and t = A r with A the iterated operator (tau-free); writes (r.r, r.t, t.t)
-// to p->rn[3 s .. 3 s + 2] (device).  u is overwritten.
-int check_residuals(gmrf_problem* p, int nvec, const void* z, void* u, cudaStream_t s) {
+// with A the iterated operator (tau-free); with second = false writes
+// (r.r, r.r, r.r) to p->rn[3 s .. 3 s + 2], with second = true also t = A r
+// into u and (r.r, r.t, t.t) (r kept from the first call).  u is overwritten
+// by the second call.
+int check_residuals(gmrf_problem* p, int nvec, const void* z, void* u, bool second, cudaStream_t s) {
   const size_t n = p->g.n, es = esize(p), cnt = (size_t)nvec * n;
   CKR(ensure(p->chk, (size_t)nvec * (check_bytes_per_vec(p) - 2 * n * es), p->ws));
   CKR(ensure(p->rn, (sizeof(double) * 3 + sizeof(Dots<double>) * kResidBlocks) * (size_t)nvec, p->ws));
   double* out = (double*)p->rn.p;
   void* part = out + 3 * (size_t)nvec;
-  auto apply = [&](bool fp64, const void* in, void* res) -> cudaError_t {
+  auto apply = [&](const void* in, void* res) -> cudaError_t {
     if (p->sp) return launch_sparse_ops(*p->sp, sparse_f(p) ? 1 : 0, in, res, nvec, s);  // A, or Q without F
     if (p->precond != GMRF_PREC_NONE)
       return launch_precond_operator(p->pre, p->g, p->fp64, p->kappa2.p, p->kappa2_const, in, res, nvec, s);
-    return launch_stencil_apply(p->g, fp64, p->kappa2.p, p->kappa2_const, in, res, nvec, s);
+    return launch_stencil_apply(p->g, p->fp64, p->kappa2.p, p->kappa2_const, in, res, nvec, s);
   };
-  const int kc = p->sp ? KC_PRE_APPLY : (p->precond != GMRF_PREC_NONE ? KC_PRE_APPLY : KC_STENCIL_STEP);
   const int kl = p->sp ? 1 : (p->precond != GMRF_PREC_NONE ? 5 : 1);
-  if (!p->sp && p->precond == GMRF_PREC_NONE && !p->fp64) {
-    double* u64 = (double*)p->chk.p;
-    double* r64 = u64 + cnt;
-    CK(traced(KC_OTHER, s, 1, [&] { return launch_convert(true, u, u64, cnt, s); }));
-    CK(traced(kc, s, kl, [&] { return apply(true, u64, r64); }));
-    CK(traced(KC_OTHER, s, 1, [&] { return launch_resid_form(false, z, true, r64, cnt, s); }));
-    CK(traced(kc, s, kl, [&] { return apply(true, r64, u64); }));
-    CK(traced(KC_OTHER, s, 2, [&] { return launch_dots3(true, r64, u64, n, nvec, part, out, s); }));
+  // FP32 lattice without a preconditioner: r = z - Q u formed in pairs of
+  // floats (the stencil's own terms cancel on a smooth u)
+  const bool df_resid = !p->sp && p->precond == GMRF_PREC_NONE && !p->fp64;
+  void* r = p->chk.p;
+  if (!second) {
+    if (df_resid) {
+      CK(traced(KC_PRE_APPLY, s, 2, [&] {
+        return launch_resid_df(p->g, (const float*)p->kappa2.p, p->kappa2_const, (const float*)z, (const float*)u,
+                               (float*)r, nvec, part, out, s);
+      }));
+    } else {
+      CK(traced(KC_PRE_APPLY, s, kl, [&] { return apply(u, r); }));
+      CK(traced(KC_OTHER, s, 1, [&] { return launch_resid_form(p->fp64, z, p->fp64, r, cnt, s); }));
+      CK(traced(KC_OTHER, s, 2, [&] { return launch_dots3(p->fp64, r, r, n, nvec, part, out, s); }));
+    }
   } else {
-    void* r = p->chk.p;
-    CK(traced(kc, s, kl, [&] { return apply(p->fp64, u, r); }));
-    CK(traced(KC_OTHER, s, 1, [&] { return launch_resid_form(p->fp64, z, p->fp64, r, cnt, s); }));
-    CK(traced(kc, s, kl, [&] { return apply(p->fp64, r, u); }));
+    // t = A r into u's buffer (u is not needed after r)
+    CK(traced(KC_PRE_APPLY, s, kl, [&] { return apply(r, u); }));
     CK(traced(KC_OTHER, s, 2, [&] { return launch_dots3(p->fp64, r, u, n, nvec, part, out, s); }));
   }
+  return GMRF_OK;
+}
+
+// Theorem 1's form with the direct residual, theta_min^{-1/2} ||r|| / ||x_m||
+// (an upper estimate of est_direct), INFINITY when it cannot be formed.
+double crude_estimate(const VecState& v, double rr) {
+  const double xnorm = v.znorm * std::sqrt(v.energy);
+  if (!(xnorm > 0.0) || !(v.theta > 0.0) || !std::isfinite(rr)) return INFINITY;
+  const double e = std::sqrt(std::max(rr, 0.0) / v.theta) / xnorm;
+  return std::isfinite(e) ? e : INFINITY;
+}
+
+// The direct estimates of nvec vectors after their assembly: z, u as for
+// check_residuals, states on the device (copied to hst).  est[s] is Theorem
+// 1's form with the direct residual where that is already <= tol, else the
+// Gauss-Radau est_direct (a second product A r, run for the batch only when
+// some vector needs it); each vector's value depends only on that vector.
+int check_vectors(gmrf_problem* p, int nvec, const void* z, void* u, const VecState* st_dev, VecState* hst,
+                  double tol, double* est, cudaStream_t s) {
+  std::vector<double> d3((size_t)3 * nvec);
+  CKR(check_residuals(p, nvec, z, u, false, s));
+  CK(cudaMemcpyAsync(d3.data(), p->rn.p, sizeof(double) * 3 * nvec, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hst, st_dev, sizeof(VecState) * nvec, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  bool second = false;
+  for (int i = 0; i < nvec; ++i) {
+    est[i] = crude_estimate(hst[i], d3[3 * i]);
+    const bool checked = (hst[i].status == VS_DONE || hst[i].status == GMRF_ERR_NOT_CONVERGED) && hst[i].m > 0;
+    if (checked && !(est[i] <= tol)) second = true;
+  }
+  if (!second) return GMRF_OK;
+  CKR(check_residuals(p, nvec, z, u, true, s));
+  CK(cudaMemcpyAsync(d3.data(), p->rn.p, sizeof(double) * 3 * nvec, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < nvec; ++i)
+    if (!(est[i] <= tol)) est[i] = direct_estimate(hst[i], d3.data() + 3 * i);
   return GMRF_OK;
 }
 
@@ -406,14 +588,13 @@ double direct_estimate(const VecState& v, const double* d3) {
 // steps can help: est_direct within 20 tol in the first round, falling by 30 %
 // per round after it, at most 3 rounds, m below m_max.  A direct estimate far
 // above tol, or one that stopped falling, is the floor of the arithmetic: the
-// vector keeps its result and the check reports it.  est[s] receives the
-// direct estimates.  Returns whether any vector was resumed.
-bool check_resume(VecState* st, const double* d3, double* est, const double* est_prev, int* mmin, int nvec,
-                  double tol, int m_max, int round) {
+// vector keeps its result and the check reports it.  Returns whether any
+// vector was resumed.
+bool check_resume(VecState* st, const double* est, const double* est_prev, int* mmin, int nvec, double tol, int m_max,
+                  int round) {
   bool any = false;
   for (int s = 0; s < nvec; ++s) {
     VecState& v = st[s];
-    est[s] = direct_estimate(v, d3 + 3 * s);
     if (round >= 3 || v.status != VS_DONE || v.m == 0 || !(v.err_est > 0.0) || v.m >= m_max) continue;
     const double e = est[s];
     if (e <= tol) continue;
@@ -653,7 +834,7 @@ void gmrf_destroy(gmrf_problem* p) {
   DevBuf* bufs[] = {&p->kappa2, &p->W0, &p->W1, &p->V, &p->st, &p->alpha, &p->beta, &p->alpha_f, &p->beta2_f,
                     &p->partials, &p->counters, &p->y, &p->scratch, &p->nodes, &p->q, &p->out2, &p->stage,
                     &p->stage2, &p->work, &p->Vb, &p->xacc, &p->accn, &p->solvew, &p->ycg, &p->ucg,
-                    &p->xacc2, &p->chk, &p->rn, &p->zre, &p->mmin};
+                    &p->xacc2, &p->chk, &p->rn, &p->zre, &p->mmin, &p->loopctr};
   for (DevBuf* b : bufs) release(*b, p->ws);
   precond_free(p->pre, p->ws);
   sparse_free(p->sp, p->ws);
@@ -716,7 +897,7 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
       xdst = p->stage.p;
     }
     CKR(load_z(p->zre.p));  // z for the accuracy check (kept: W[0] becomes a q buffer)
-    std::vector<double> d3((size_t)3 * c), est((size_t)c), est_prev((size_t)c, 0.0);
+    std::vector<double> est((size_t)c), est_prev((size_t)c, 0.0);
     std::vector<int> mmin((size_t)c, 0);
     CKR(load_z(b.W[0]));
     CKR(run_lanczos(p, b, o->tol, m_max, o->check_every));
@@ -775,16 +956,12 @@ int gmrf_sample(gmrf_problem* p, const gmrf_sample_opts* o, void* x_out, gmrf_re
         CK(traced(KC_OTHER, s, 1,
                   [&] { return launch_scale(p->fp64, xdst, (size_t)c * n, 1.0 / std::sqrt(p->tau), s); }));
       }
-      // accuracy check: r = z - A u_cg, t = A r
-      CKR(check_residuals(p, c, p->zre.p, p->ucg.p, s));
-      CK(cudaMemcpyAsync(d3.data(), p->rn.p, sizeof(double) * 3 * c, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * c, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      // accuracy check: the direct residual r = z - A u_cg
+      CKR(check_vectors(p, c, p->zre.p, p->ucg.p, b.st, p->st_host, o->tol, est.data(), s));
       trace_collect();
       // vectors whose recurrence estimate met tol but whose direct estimate did
       // not, by a margin more steps can close, continue for more steps
-      if (!check_resume(p->st_host, d3.data(), est.data(), est_prev.data(), mmin.data(), c, o->tol, m_max, round))
-        break;
+      if (!check_resume(p->st_host, est.data(), est_prev.data(), mmin.data(), c, o->tol, m_max, round)) break;
       est_prev = est;
       if (two_pass) {
         // rerun both passes from z with the new minimum step counts (the
@@ -1017,8 +1194,7 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
         CK(traced(KC_RNG, s, 1, [&] { return launch_rng(1, p->fp64, nqc, (int64_t)n, lo->seed, q0, dst, s); }));
     }
     CKR(run_lanczos(p, b, so->tol, m_max, so->check_every));
-    std::vector<double> d3((size_t)3 * std::max(nsc, 1)), est((size_t)std::max(nsc, 1)),
-        est_prev((size_t)std::max(nsc, 1), 0.0);
+    std::vector<double> est((size_t)std::max(nsc, 1)), est_prev((size_t)std::max(nsc, 1), 0.0);
     std::vector<int> mmin((size_t)std::max(nsc, 1), 0);
     void* xdst = (char*)x_out + (size_t)t0 * n * es;
     if (nsc > 0) {
@@ -1069,14 +1245,9 @@ int gmrf_sample_logdet(gmrf_problem* p, const gmrf_sample_opts* so, const gmrf_l
                   [&] { return launch_scale(p->fp64, xdst, (size_t)nsc * n, 1.0 / std::sqrt(p->tau), s); }));
       }
       // accuracy check of the samples, with the same resumption as gmrf_sample
-      CKR(check_residuals(p, nsc, p->zre.p, p->ucg.p, s));
-      CK(cudaMemcpyAsync(d3.data(), p->rn.p, sizeof(double) * 3 * nsc, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(p->st_host, b.st, sizeof(VecState) * nsc, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      CKR(check_vectors(p, nsc, p->zre.p, p->ucg.p, b.st, p->st_host, so->tol, est.data(), s));
       trace_collect();
-      if (!check_resume(p->st_host, d3.data(), est.data(), est_prev.data(), mmin.data(), nsc, so->tol, m_max,
-                        round))
-        break;
+      if (!check_resume(p->st_host, est.data(), est_prev.data(), mmin.data(), nsc, so->tol, m_max, round)) break;
       est_prev = est;
       CK(cudaMemcpyAsync(b.st, p->st_host, sizeof(VecState) * nsc, cudaMemcpyHostToDevice, s));
       CKR(run_lanczos(p, b, so->tol, m_max, so->check_every, false, false));
@@ -1188,8 +1359,10 @@ int gmrf_rng(int32_t kind, int32_t precision, int64_t nvec, int64_t n, uint64_t 
 }
 
 int gmrf_set_tuning(gmrf_problem* p, const gmrf_tuning* t) {
-  if (!p || !t || t->block_width < 0 || t->zchunk < 0 || t->reserved != 0) return GMRF_ERR_INVALID;
+  if (!p || !t || t->block_width < 0 || t->zchunk < 0 || (t->host_loop != 0 && t->host_loop != 1))
+    return GMRF_ERR_INVALID;
   p->tune_bw = t->block_width;
+  p->host_loop = t->host_loop != 0;
   p->g.zchunk = tune_zchunk_ok(p) ? t->zchunk : 0;
   p->graph.reset();
   return GMRF_OK;
@@ -1290,7 +1463,7 @@ int gmrf_autotune(gmrf_problem* p, int32_t nvec_max, gmrf_tuning* out) {
   out->zchunk = p->g.zchunk;
   out->vec_steps_per_s = best;
   out->candidates = ncand;
-  out->reserved = 0;
+  out->host_loop = p->host_loop ? 1 : 0;
   return GMRF_OK;
 }
 

@@ -58,6 +58,7 @@ struct StepGraph {
   const void* y2 = nullptr;
   double xscale = 0.0;
   bool timed = false;
+  bool loop = false;   // exec is the device-side loop (a WHILE node over one step), else c steps to replay
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
@@ -88,6 +89,7 @@ struct gmrf_problem {
   // accuracy check of samples: T_m^{-1} e_1 and its workspace, the CG iterate
   // u_cg, the product A u_cg (FP64 pair for FP32 stencils), the residual norms
   DevBuf ycg, ucg, xacc2, chk, rn, zre, mmin;
+  DevBuf loopctr;  // iteration counter of the device-side Lanczos loop
   VecState* st_host = nullptr;
   int st_host_cap = 0;
   // a continuous-batching server attached to the problem (server.cu): while it
@@ -95,6 +97,7 @@ struct gmrf_problem {
   gmrf_server* server = nullptr;
   bool in_server = false;
   int tune_bw = 0;  // vectors per Lanczos launch (0: as many as fit)
+  bool host_loop = false;  // host-replayed step graphs instead of the device-side loop
 };
 
 namespace host {
@@ -116,10 +119,13 @@ StepParams step_params(gmrf_problem* p, const LanczosBufs& b, double tol, int m_
 LanczosBufs sub_batch(const LanczosBufs& b, int off, int cnt, size_t n, size_t es);
 size_t check_bytes_per_vec(const gmrf_problem* p);
 int check_tm(gmrf_problem* p, const LanczosBufs& b, cudaStream_t s);
-int check_residuals(gmrf_problem* p, int nvec, const void* z, void* u, cudaStream_t s);
+int check_residuals(gmrf_problem* p, int nvec, const void* z, void* u, bool second, cudaStream_t s);
 double direct_estimate(const VecState& v, const double* d3);
-bool check_resume(VecState* st, const double* d3, double* est, const double* est_prev, int* mmin, int nvec,
-                  double tol, int m_max, int round);
+double crude_estimate(const VecState& v, double rr);
+int check_vectors(gmrf_problem* p, int nvec, const void* z, void* u, const VecState* st_dev, VecState* hst,
+                  double tol, double* est, cudaStream_t s);
+bool check_resume(VecState* st, const double* est, const double* est_prev, int* mmin, int nvec, double tol, int m_max,
+                  int round);
 void check_apply(VecState* st, const double* est, int nvec, double tol);
 void fill_info(const VecState* st, int nvec, gmrf_result_info* info);
 

@@ -103,7 +103,20 @@ cudaError_t launch_resid_form(bool z64, const void* z, bool r64, void* r, size_t
 constexpr int kResidBlocks = 128;
 cudaError_t launch_dots3(bool r64, const void* r, const void* t, size_t n, int nvec, void* part, double* out,
                          cudaStream_t s);
+// out[3 s .. 3 s + 2] from the kResidBlocks partials of each of nvec vectors.
+cudaError_t launch_dots3_final(const void* part, int nvec, double* out, cudaStream_t s);
+// r = z - Q u for nvec FP32 vectors [nvec][n] of a lattice problem without a
+// preconditioner, Q applied in pair-of-floats arithmetic (resid_df.cu), r
+// rounded to FP32; out[3 s] = r.r (out[3 s + 1], out[3 s + 2] = 0); part:
+// kResidBlocks * nvec Dots<double> of scratch.
+cudaError_t launch_resid_df(const Grid& g, const float* kappa2, double kappa2_const, const float* z, const float* u,
+                            float* r, int nvec, void* part, double* out, cudaStream_t s);
 cudaError_t launch_convert(bool to_fp64, const void* in, void* out, size_t count, cudaStream_t s);
+// The condition kernel of the device-side Lanczos loop: sets h to 1 while some
+// of the nvec vectors is running and ++*ctr < limit, else 0.
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const VecState* st, int nvec, int* ctr, int limit,
+                             cudaStream_t s);
+const void* loop_cond_kernel();  // the kernel itself, for a graph kernel node
 cudaError_t launch_scale(bool fp64, void* x, size_t count, double a, cudaStream_t s);
 
 // tridiag.cu ----------------------------------------------------------------

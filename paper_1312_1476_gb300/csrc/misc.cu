@@ -323,6 +323,23 @@ __global__ void k_accumulate_finish(const void* X, size_t n, const VecState* st,
   }
 }
 
+// Condition of the device-side Lanczos loop (a CUDA graph WHILE node): the
+// body runs again while some vector is still iterating and the iteration count
+// is below `limit` (a bound the loop never needs: every vector stops by m_max).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const VecState* st, int nvec, int* ctr, int limit) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < nvec; s += blockDim.x)
+    if (st[s].status == VS_RUNNING) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int n = *ctr + 1;
+    *ctr = n;
+    cudaGraphSetConditional(h, (any && n < limit) ? 1u : 0u);
+  }
+}
+
 // r = z - r in place (the residual from A u in r), elementwise in the type of r.
 template <typename Z, typename R>
 __global__ void k_resid_form(const Z* __restrict__ z, R* r, size_t count) {
@@ -330,8 +347,10 @@ __global__ void k_resid_form(const Z* __restrict__ z, R* r, size_t count) {
     r[i] = (R)((double)z[i] - (double)r[i]);
 }
 
-// Partial sums of r.r, r.t, t.t in FP64 per vector, grid (nblk, nvec); the
-// block tree and the order of the partials depend only on n.
+// Partial sums of r.r, r.t, t.t per vector, grid (nblk, nvec); the block
+// tree and the order of the partials depend only on n.  FP64 vectors sum in
+// FP64; FP32 vectors sum in Dot2 form (exact products, pair sums) on the FP32
+// pipe, each thread's sums finished in FP64.
 template <typename R>
 __global__ void k_dots3_partial(const R* __restrict__ r, const R* __restrict__ t, size_t n, Dots<double>* part) {
   __shared__ Dots<double> red[8];
@@ -340,15 +359,29 @@ __global__ void k_dots3_partial(const R* __restrict__ r, const R* __restrict__ t
   const R* ts = t + (size_t)s * n;
   Dots<double> d;
   d.zero();
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double a = (double)rs[i], b = (double)ts[i];
-    d.s1 = fma(a, a, d.s1);
-    d.s2 = fma(a, b, d.s2);
-    d.s3 = fma(b, b, d.s3);
+  if constexpr (sizeof(R) == 4) {
+    df rr = {0.f, 0.f}, rt = {0.f, 0.f}, tt = {0.f, 0.f};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      const float a = rs[i], b = ts[i];
+      Dots<float>::dot2(rr, a, a);
+      Dots<float>::dot2(rt, a, b);
+      Dots<float>::dot2(tt, b, b);
+    }
+    d.s1 = df_to_double(rr);
+    d.s2 = df_to_double(rt);
+    d.s3 = df_to_double(tt);
+  } else {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      const double a = (double)rs[i], b = (double)ts[i];
+      d.s1 = fma(a, a, d.s1);
+      d.s2 = fma(a, b, d.s2);
+      d.s3 = fma(b, b, d.s3);
+    }
   }
   d = block_reduce(d, red);
   if (threadIdx.x == 0) part[(size_t)s * gridDim.x + blockIdx.x] = d;
 }
+
 __global__ void k_dots3_final(const Dots<double>* part, int nblk, double* out) {
   __shared__ Dots<double> red[8];
   const int s = blockIdx.x;
@@ -538,6 +571,19 @@ cudaError_t launch_dots3(bool r64, const void* r, const void* t, size_t n, int n
   if (r64) k_dots3_partial<double><<<grd, 256, 0, s>>>((const double*)r, (const double*)t, n, (Dots<double>*)part);
   else k_dots3_partial<float><<<grd, 256, 0, s>>>((const float*)r, (const float*)t, n, (Dots<double>*)part);
   k_dots3_final<<<nvec, 256, 0, s>>>((const Dots<double>*)part, kResidBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots3_final(const void* part, int nvec, double* out, cudaStream_t s) {
+  k_dots3_final<<<nvec, 256, 0, s>>>((const Dots<double>*)part, kResidBlocks, out);
+  return cudaGetLastError();
+}
+
+const void* loop_cond_kernel() { return (const void*)k_loop_cond; }
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const VecState* st, int nvec, int* ctr, int limit,
+                             cudaStream_t s) {
+  k_loop_cond<<<1, 256, 0, s>>>(h, st, nvec, ctr, limit);
   return cudaGetLastError();
 }
 

@@ -152,18 +152,16 @@ int finish_samples(gmrf_server* sv, int a, int k, Req& r) {
   }
   // the accuracy check of gmrf_sample, on z regenerated from the request's stream
   CK(traced(KC_RNG, s, 1, [&] { return launch_rng(0, p->fp64, k, (int64_t)n, r.seed, vec0, p->zre.p, s); }));
-  CKR(check_residuals(p, k, p->zre.p, p->ucg.p, s));
-  std::vector<double> d3((size_t)3 * k);
-  CK(cudaMemcpyAsync(d3.data(), p->rn.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  std::vector<double> ests((size_t)k);
+  CKR(check_vectors(p, k, p->zre.p, p->ucg.p, sv->b.st + a, sv->hst.data() + a, sv->o.tol, ests.data(), s));
   bool resumed = false;
   for (int i = 0; i < k; ++i) {
     Slot& sl = sv->slots[a + i];
     VecState& v = sv->hst[a + i];
-    double est = 0.0, prev = sl.est_prev;
+    double est = ests[i], prev = sl.est_prev;
     int mm = 0;
     // one vector's round of gmrf_sample's rule
-    if (check_resume(&v, d3.data() + 3 * i, &est, &prev, &mm, 1, sv->o.tol, m_max, sl.round)) {
+    if (check_resume(&v, &est, &prev, &mm, 1, sv->o.tol, m_max, sl.round)) {
       sl.round += 1;
       sl.est_prev = est;
       resumed = true;

@@ -231,17 +231,20 @@ __global__ void k_tm_inv(const VecState* st, const double* alpha, const double* 
   const double* b = beta + (size_t)s * m_max;
   double* d = dwork + (size_t)s * m_max;
   double* ys = y + (size_t)s * m_max;
-  double dp = a[0], w = 1.0;
-  d[0] = dp;
-  ys[0] = w / dp;  // z_i = w_i / d_i
+  // d[] keeps the reciprocal pivots 1 / d_i: one FP64 division per row (the
+  // chain is serial, and GB300's FP64 divisions are slow)
+  double dinv = 1.0 / a[0], w = 1.0;
+  d[0] = dinv;
+  ys[0] = w * dinv;  // z_i = w_i / d_i
   for (int i = 1; i < m; ++i) {
-    const double l = b[i - 1] / dp;
-    dp = a[i] - l * b[i - 1];
+    const double l = b[i - 1] * dinv;
+    const double dp = a[i] - l * b[i - 1];
     w = -l * w;
-    d[i] = dp;
-    ys[i] = w / dp;
+    dinv = 1.0 / dp;
+    d[i] = dinv;
+    ys[i] = w * dinv;
   }
-  for (int i = m - 2; i >= 0; --i) ys[i] -= (b[i] / d[i]) * ys[i + 1];  // y_i = z_i - l_{i+1} y_{i+1}
+  for (int i = m - 2; i >= 0; --i) ys[i] -= (b[i] * d[i]) * ys[i + 1];  // y_i = z_i - l_{i+1} y_{i+1}
 }
 
 }  // namespace

@@ -80,7 +80,7 @@ class GmrfServerOpts(ctypes.Structure):
 
 class GmrfTuning(ctypes.Structure):
     _fields_ = [("block_width", ctypes.c_int32), ("zchunk", ctypes.c_int32), ("vec_steps_per_s", ctypes.c_double),
-                ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("candidates", ctypes.c_int32), ("host_loop", ctypes.c_int32)]
 
 
 def _load():
@@ -374,11 +374,12 @@ class Problem:
         if rc != OK:
             raise GmrfError(rc, "gmrf_autotune")
         return {"block_width": t.block_width, "zchunk": t.zchunk, "vec_steps_per_s": t.vec_steps_per_s,
-                "candidates": t.candidates}
+                "candidates": t.candidates, "host_loop": bool(t.host_loop)}
 
-    def set_tuning(self, block_width=0, zchunk=0):
-        """Explicit tuning (0 = library default for either field)."""
-        t = GmrfTuning(int(block_width), int(zchunk), 0.0, 0, 0)
+    def set_tuning(self, block_width=0, zchunk=0, host_loop=False):
+        """Explicit tuning (0 = library default for either field); host_loop
+        True: host-replayed step graphs instead of the device-side loop."""
+        t = GmrfTuning(int(block_width), int(zchunk), 0.0, 0, 1 if host_loop else 0)
         rc = _lib.gmrf_set_tuning(self._h, ctypes.byref(t))
         if rc != OK:
             raise GmrfError(rc, "gmrf_set_tuning")

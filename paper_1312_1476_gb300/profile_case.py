@@ -4,7 +4,8 @@
 
 Each case builds one benchmark configuration on its synthetic inputs, runs
 one sample call capped at M Lanczos steps (so it ends after M steps whatever
-the tolerance) and exits.  The sizes keep a capture small: one or a few
+the tolerance) and exits.  The host drives the steps (replayed step graphs,
+not the device-side loop), so a per-kernel profiler sees plain kernel nodes.  The sizes keep a capture small: one or a few
 vectors, a few GB of device memory at most.  With --trace it then repeats the
 call twice more, timed as a whole and then with CUDA events around every
 launch, and reports each kernel class's time per vector-step (the sum of the
@@ -14,6 +15,8 @@ Cases:
   headline_1024  1024 x 1024 SPDE, zero-Neumann, mirror preconditioner, FP32
   batched_512    512 x 512 SPDE, mirror preconditioner, FP32, N vectors per launch
   3d_256         256^3 Dirichlet 7-point, kappa^2 i.i.d. U[0.01, 1], FP32
+  3d_128         the same recipe at 128^3 (16 vectors of 8 MiB: a multi-vector launch
+                 larger than L2 that a counter capture can replay)
   stencil2d_1024 1024 x 1024 SPDE, zero-Neumann, no preconditioner, FP32 (the
                  streamed 2-D step), N vectors per launch
   figure3_ichol  the Figure 3 matrix (31^2 G)^2 (n = 900, Section 5.2) in CSR,
@@ -42,8 +45,8 @@ def run(case: str, nsamples: int, steps: int, trace: bool = False) -> dict:
         shape = (1024, 1024)
         k2 = torch.from_numpy(inputs.kappa2_gp_field(shape, seed=1, ell=64.0)).cuda()
         prob = gmrf.Problem(shape, "neumann", "spde_squared", kappa2=k2)
-    elif case == "3d_256":
-        shape = (256, 256, 256)
+    elif case in ("3d_256", "3d_128"):
+        shape = (256, 256, 256) if case == "3d_256" else (128, 128, 128)
         k2 = torch.from_numpy(inputs.kappa2_uniform_field(shape, seed=1)).cuda()
         prob = gmrf.Problem(shape, "dirichlet", "shifted_laplacian", kappa2=k2)
     elif case == "figure3_ichol":
@@ -64,6 +67,9 @@ def run(case: str, nsamples: int, steps: int, trace: bool = False) -> dict:
         return rc, info
 
     with prob:
+        # host-replayed step graphs: a per-kernel profiler then sees plain
+        # kernel nodes (the kernels are the same as under the device-side loop)
+        prob.set_tuning(block_width=0, zchunk=0, host_loop=True)
         x = torch.empty(nsamples * n, dtype=torch.float64 if prob.precision == "fp64" else torch.float32,
                         device="cuda")
         rc, info = call()
@@ -95,7 +101,8 @@ def run(case: str, nsamples: int, steps: int, trace: bool = False) -> dict:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("case", choices=["headline_1024", "batched_512", "3d_256", "stencil2d_1024", "figure3_ichol"])
+    ap.add_argument("case", choices=["headline_1024", "batched_512", "3d_256", "3d_128", "stencil2d_1024",
+                                     "figure3_ichol"])
     ap.add_argument("--nsamples", type=int, default=1)
     ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--trace", action="store_true", help="also report per-kernel-class times")

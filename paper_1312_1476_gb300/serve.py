@@ -244,8 +244,13 @@ class Server:
         return min(c, self.block_width) if self.block_width else c
 
     def need(self, req):
-        """Budget a request takes in direct mode."""
-        return self.chunk(req) * self.vec_bytes(req) + 8 * int(np.prod(req.shape))
+        """Budget a request takes in direct mode: the library's state for one
+        chunk of its vectors (the call is held to that many vectors per
+        launch), its output and its coefficient field."""
+        n = int(np.prod(req.shape))
+        es = 8 if self.precision == "fp64" else 4
+        out = req.count * n * es if req.kind in ("sample", "solve") else 0
+        return self.chunk(req) * self.vec_bytes(req) + out + (2 * out if req.kind == "solve" else 0) + 8 * n
 
     def engine_slots(self, shape):
         """Slots of an engine: as many as a quarter of the budget holds, 8 .. nslots_max."""
@@ -271,11 +276,14 @@ class Server:
         k2 = self.fields.get(shape, req.field_id)
         stream = torch.cuda.Stream()
         prob = self._problem(shape, k2, req.tau, stream)
-        if self.block_width:
-            prob.set_tuning(block_width=self.block_width)
-        elif shape in self.tuning:
+        # at most chunk(req) vectors per launch: the library's state then stays
+        # within what need() reserved for this request
+        width = self.chunk(req)
+        if shape in self.tuning and not self.block_width:
             t = self.tuning[shape]
-            prob.set_tuning(block_width=t["block_width"], zchunk=t["zchunk"])
+            prob.set_tuning(block_width=min(width, t["block_width"]), zchunk=t["zchunk"])
+        else:
+            prob.set_tuning(block_width=width)
         dt = torch.float64 if self.precision == "fp64" else torch.float32
         res = Result(req.rid, req.kind, shape, req.count, 0.0, 0.0, 0.0, [], 0)
         with prob:
@@ -441,5 +449,6 @@ class Server:
         metrics = {"requests": len(out), "wall_s": wall, "samples": nsamp, "samples_per_s": nsamp / wall,
                    "logdets": nld, "logdets_per_s": nld / wall, "solves": nsol, "solves_per_s": nsol / wall,
                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                   "statuses": sorted(set(r.status for r in out)), "mode": self.mode}
+                   "statuses": {str(c): sum(1 for r in out if r.status == c) for c in sorted({r.status for r in out})},
+                   "mode": self.mode}
         return out, metrics

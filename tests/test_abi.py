@@ -54,6 +54,8 @@ int main(void) {
          offsetof(gmrf_solve_opts, reserved));
   printf("%zu %zu %zu %zu\n", sizeof(gmrf_sparse_desc), offsetof(gmrf_sparse_desc, f_rowptr),
          offsetof(gmrf_sparse_desc, tau), offsetof(gmrf_sparse_desc, reserved));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(gmrf_tuning), offsetof(gmrf_tuning, vec_steps_per_s),
+         offsetof(gmrf_tuning, host_loop), sizeof(gmrf_server_opts), offsetof(gmrf_server_opts, tol));
   return 0;
 }
 """
@@ -69,7 +71,9 @@ int main(void) {
                         g.GmrfSampleOpts.z_in.offset, g.GmrfResultInfo.err_est.offset,
                         g.GmrfLogdetOpts.probes_in.offset, cs(g.GmrfSolveOpts), g.GmrfSolveOpts.nrhs.offset,
                         g.GmrfSolveOpts.reserved.offset, cs(g.GmrfSparseDesc), g.GmrfSparseDesc.f_rowptr.offset,
-                        g.GmrfSparseDesc.tau.offset, g.GmrfSparseDesc.reserved.offset]
+                        g.GmrfSparseDesc.tau.offset, g.GmrfSparseDesc.reserved.offset,
+                        cs(g.GmrfTuning), g.GmrfTuning.vec_steps_per_s.offset, g.GmrfTuning.host_loop.offset,
+                        cs(g.GmrfServerOpts), g.GmrfServerOpts.tol.offset]
 
 
 def test_invalid_descriptors_rejected_on_host(g):

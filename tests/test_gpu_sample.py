@@ -417,3 +417,54 @@ def test_async_submit_poll_wait_equal_synchronous(g):
         p1.close()
         p2.close()
     assert torch.equal(xl, xa[:n])
+
+
+@pytest.mark.parametrize("shape,bc,op,pre,precision", [
+    ((128, 128), "neumann", "spde_squared", "mirror", "fp32"),
+    ((24, 20, 16), "dirichlet", "shifted_laplacian", "none", "fp32"),
+    ((64, 64), "periodic", "shifted_laplacian", "none", "fp64")])
+def test_device_loop_equals_host_loop(g, shape, bc, op, pre, precision):
+    # the device-side WHILE loop and the host-replayed step graphs run the same
+    # steps: samples, log dets and solves are bitwise equal, with the same
+    # per-vector step counts and statuses, also when m_max stops the iteration
+    n = int(np.prod(shape))
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    k2 = inputs.kappa2_gp_field(shape, seed=3) if len(shape) == 2 and op == "spde_squared" else None
+    kw = dict(kappa2=_dev(k2)) if k2 is not None else dict(kappa2_const=0.3)
+    out = {}
+    for host in (False, True):
+        with g.Problem(shape, bc, op, precond=pre, precision=precision, **kw) as p:
+            p.set_tuning(host_loop=host)
+            r = {}
+            for m_max in (400, 5):
+                x = torch.empty(3 * n, dtype=dt, device="cuda")
+                rc, info = p.sample(x, nsamples=3, tol=tol, m_max=m_max, seed=17, check_every=8,
+                                    raise_on_error=False)
+                r["sample", m_max] = (rc, [(i.m_used, i.status, i.err_est) for i in info], x.cpu())
+            ld, se, q, info, rc = p.logdet(nprobes=6, tol=tol, m_max=400, seed=5, check_every=8,
+                                           raise_on_error=False)
+            r["logdet"] = (rc, [(i.m_used, i.status) for i in info], ld, se)
+            b = torch.from_numpy(inputs.gaussian_vectors(2, n, seed=8)).to(dt).cuda().reshape(-1)
+            x = torch.empty_like(b)
+            rc, info = p.solve(b, x, nrhs=2, tol=tol, m_max=400, raise_on_error=False)
+            r["solve"] = (rc, [(i.m_used, i.status) for i in info], x.cpu())
+            out[host] = r
+    assert out[False]["sample", 5][0] == g.ERR_NOT_CONVERGED
+    assert out[False]["sample", 400][0] == g.OK
+    for k in out[False]:
+        a, b = out[False][k], out[True][k]
+        if k == "logdet":
+            assert a == b, k
+        else:
+            assert a[:-1] == b[:-1], k
+            assert torch.equal(a[-1], b[-1]), k
+
+
+def test_host_loop_flag_validated(g):
+    lib = g.lib()
+    with g.Problem((16, 16), "neumann", "shifted_laplacian", kappa2_const=0.3) as p:
+        t = g.GmrfTuning(0, 0, 0.0, 0, 2)
+        assert lib.gmrf_set_tuning(p._h, ctypes.byref(t)) == g.ERR_INVALID
+        t = g.GmrfTuning(0, 0, 0.0, 0, 1)
+        assert lib.gmrf_set_tuning(p._h, ctypes.byref(t)) == g.OK
