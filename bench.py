@@ -751,7 +751,7 @@ def measure_serving(nreq=1000, baseline_nreq=24):
         return serve.make_mix(count, rate=rate, seed=4)
 
     res = {"requests_per_rate": nreq}
-    srv = serve.Server(mode="batched")
+    srv = serve.Server(mode="batched", keep_outputs=False)
     try:
         burst = stream(1e6, nreq)
         for r in burst:
@@ -770,7 +770,7 @@ def measure_serving(nreq=1000, baseline_nreq=24):
         srv.close()
     torch.cuda.synchronize()
     torch.cuda.empty_cache()  # outputs cached by torch go back to the device for the library's own allocations
-    off = serve.Server(mode="direct", max_inflight=16)
+    off = serve.Server(mode="direct", max_inflight=16, keep_outputs=False)
     for frac in (1.0, 2.0):
         reqs = stream(frac * sat_rate, nreq)
         off.prepare(reqs)
@@ -778,7 +778,7 @@ def measure_serving(nreq=1000, baseline_nreq=24):
         res["unpacked_rate_%gx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-    base = serve.Server(mode="direct", max_inflight=1, precision="fp64", block_width=1)
+    base = serve.Server(mode="direct", max_inflight=1, precision="fp64", block_width=1, keep_outputs=False)
     reqs = stream(0.25 * sat_rate, baseline_nreq)
     base.prepare(reqs, tune=False)
     _, met = base.serve(reqs, realtime=True)

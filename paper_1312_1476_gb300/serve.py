@@ -198,7 +198,7 @@ class Server:
     M_MAX_3D = 128
 
     def __init__(self, mem_budget=None, max_inflight=16, precision="fp32", chunk_bytes=8 << 30, block_width=None,
-                 mode="batched", nslots_max=64, check_every=16, tol=1e-6):
+                 mode="batched", nslots_max=64, check_every=16, tol=1e-6, keep_outputs=True):
         import torch
         from . import gmrf
         self.torch = torch
@@ -215,6 +215,10 @@ class Server:
         self.nslots_max = nslots_max
         self.check_every = check_every
         self.tol = tol
+        # keep_outputs False: a completed request's device output is released
+        # (its result keeps the step counts, statuses and log dets), as when a
+        # server hands each result on and keeps no copy
+        self.keep_outputs = keep_outputs
         self.used = 0
         self.cv = threading.Condition()
         self.engines = {}  # (shape, field id) -> Engine
@@ -261,7 +265,8 @@ class Server:
     def _complete(self, req, rc, infos, x, ld, se):
         end = time.perf_counter()
         res = Result(req.rid, req.kind, req.shape, req.count, (end - self._t0 - req.arrival) * 1e3, 0.0,
-                     (end - self._t0) * 1e3, [i.m_used for i in infos], rc, x=x, logdet=ld if req.kind == "logdet"
+                     (end - self._t0) * 1e3, [i.m_used for i in infos], rc, x=x if self.keep_outputs else None,
+                     logdet=ld if req.kind == "logdet"
                      else None, std_err=se if req.kind == "logdet" else None)
         with self.cv:
             self._results[req.rid] = res
@@ -312,6 +317,8 @@ class Server:
                 res.status = rc
             stream.synchronize()
         end = time.perf_counter()
+        if not self.keep_outputs:
+            res.x = None
         res.start_ms = (start - t0) * 1e3
         res.end_ms = (end - t0) * 1e3
         res.latency_ms = (end - t0 - req.arrival) * 1e3
