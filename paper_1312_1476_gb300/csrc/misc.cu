@@ -3,6 +3,7 @@
 // (Algorithm 1, last step) and small elementwise helpers.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <type_traits>
 #include <math.h>
 
@@ -254,6 +255,137 @@ __global__ void k_assemble(const S* __restrict__ V, int nslots, size_t n, const 
   }
 }
 
+// ---- the FP32 assembly on paired FP32 instructions
+// Blackwell's f32x2 instructions take one issue slot for two lane-wise FP32
+// operations with the same IEEE round-to-nearest result per half.  The
+// assembly with two compensated accumulators per element is issue-bound, so
+// k_assemble_pair runs two adjacent elements per thread on them.
+__device__ __forceinline__ unsigned long long pk2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 x2_add(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 x2_sub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 x2_mul(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 x2_fma(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(d);
+}
+
+// acc_comp on two elements: t = vv (yh + yl) as FMA(vv, yh, vv * yl), then
+// (sum, comp) += t with the exact error of sum + t from TwoSum (Knuth).  The
+// error of a floating-point sum is unique, so this gives bitwise the values
+// of acc_comp's magnitude-ordered form.
+__device__ __forceinline__ void acc_comp2(float2 vv, float2 yh, float2 yl, float2& sum, float2& comp) {
+  const float2 t = x2_fma(vv, yh, x2_mul(vv, yl));
+  const float2 s2 = x2_add(sum, t);
+  const float2 bb = x2_sub(s2, sum);
+  const float2 e = x2_add(x2_sub(sum, x2_sub(s2, bb)), x2_sub(t, bb));
+  comp = x2_add(comp, e);
+  sum = s2;
+}
+
+template <typename S>
+__device__ __forceinline__ float2 load_pair(const S* p);
+template <>
+__device__ __forceinline__ float2 load_pair<float>(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+template <>
+__device__ __forceinline__ float2 load_pair<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+
+// k_assemble for FP32 outputs and an even n: elements (2k, 2k + 1) per
+// thread, coefficients staged as (yh, yh, yl, yl) per j; the same arithmetic,
+// order and results as k_assemble.
+template <typename S, bool DUAL>
+__global__ void k_assemble_pair(const S* __restrict__ V, int nslots, size_t n, const VecState* st, const double* y,
+                                int y_stride, double extra, float* x, const double* y2, float* x2) {
+  extern __shared__ float4 c4[];
+  const int s = blockIdx.y;
+  const VecState v = st[s];
+  const int m = v.m;
+  float* xo = x + (size_t)s * n;
+  float* xo2 = DUAL ? x2 + (size_t)s * n : nullptr;
+  const size_t np = n / 2;
+  const bool bad = !(v.status == VS_DONE || v.status == GMRF_ERR_NOT_CONVERGED);
+  if (bad || m == 0) {
+    const float fill = (bad && v.status != VS_DONE) ? NAN : 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      xo[i] = fill;
+      if (DUAL) xo2[i] = fill;
+    }
+    return;
+  }
+  const double scale = v.znorm * extra;
+  const double* ys = y + (size_t)s * y_stride;
+  const double* ys2 = DUAL ? y2 + (size_t)s * y_stride : nullptr;
+  float4* c2 = c4 + m;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double yy = ys[j] * scale;
+    const float h = (float)yy, l = (float)(yy - (double)h);
+    c4[j] = make_float4(h, h, l, l);
+    if (DUAL) {
+      const double y2v = ys2[j] * v.znorm;
+      const float h2 = (float)y2v, l2 = (float)(y2v - (double)h2);
+      c2[j] = make_float4(h2, h2, l2, l2);
+    }
+  }
+  __syncthreads();
+  const S* Vs = V + (size_t)s * nslots * n;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < np; k += (size_t)gridDim.x * blockDim.x) {
+    float2 sum = make_float2(0.f, 0.f), comp = sum, sum2 = sum, comp2 = sum;
+    const S* p = Vs + 2 * k;
+    int j = 0;
+    // four basis loads in flight; the terms are still added in the order j = 0 .. m-1
+    for (; j + 4 <= m; j += 4) {
+      float2 vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) vv[u] = load_pair<S>(p + (size_t)(j + u) * n);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 c = c4[j + u];
+        acc_comp2(vv[u], make_float2(c.x, c.y), make_float2(c.z, c.w), sum, comp);
+        if (DUAL) {
+          const float4 d = c2[j + u];
+          acc_comp2(vv[u], make_float2(d.x, d.y), make_float2(d.z, d.w), sum2, comp2);
+        }
+      }
+    }
+    for (; j < m; ++j) {
+      const float2 vv = load_pair<S>(p + (size_t)j * n);
+      const float4 c = c4[j];
+      acc_comp2(vv, make_float2(c.x, c.y), make_float2(c.z, c.w), sum, comp);
+      if (DUAL) {
+        const float4 d = c2[j];
+        acc_comp2(vv, make_float2(d.x, d.y), make_float2(d.z, d.w), sum2, comp2);
+      }
+    }
+    reinterpret_cast<float2*>(xo)[k] = x2_add(sum, comp);
+    if (DUAL) reinterpret_cast<float2*>(xo2)[k] = x2_add(sum2, comp2);
+  }
+}
+
 // Two-pass sampling: x += scale_s y_j v_j for the basis vector v_j the step
 // just formed (j = acc[s] if the step ran for vector s), with the arithmetic
 // of k_assemble per element; with X2 also x2 += ||z_s|| y2_j v_j (the dual
@@ -500,6 +632,18 @@ cudaError_t launch_lanczos_init(bool fp64, size_t n, const LanczosBufs& b, cudaS
 template <typename T, typename S, bool DUAL>
 static void assemble_one(const S* V, int nslots, size_t n, const LanczosBufs& b, const double* y, int y_stride,
                          double extra, T* x, const double* y2, T* x2, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    // even n (8-byte aligned pairs in every basis slot) and staged coefficients within 200 KB
+    const size_t smp = (size_t)b.m_max * sizeof(float4) * (DUAL ? 2 : 1);
+    if (n % 2 == 0 && smp <= 200 * 1024 && ((uintptr_t)x & 7) == 0 && (!DUAL || ((uintptr_t)x2 & 7) == 0)) {
+      int nb = (int)((n / 2 + 255) / 256);
+      if (nb > 2048) nb = 2048;
+      if (smp > 48 * 1024)
+        cudaFuncSetAttribute(k_assemble_pair<S, DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+      k_assemble_pair<S, DUAL><<<dim3(nb, b.nvec), 256, smp, s>>>(V, nslots, n, b.st, y, y_stride, extra, x, y2, x2);
+      return;
+    }
+  }
   int nblk = (int)((n + 255) / 256);
   if (nblk > 2048) nblk = 2048;
   dim3 grd(nblk, b.nvec);
