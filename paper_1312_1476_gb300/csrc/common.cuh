@@ -102,6 +102,72 @@ struct Dots<float> {
   }
 };
 
+// ---- paired FP32 arithmetic (Blackwell f32x2): one issue slot for two
+// lane-wise FP32 operations, each with the IEEE round-to-nearest result of
+// the scalar operation.
+__device__ __forceinline__ unsigned long long x2_pk(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 x2_upk(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 x2_add(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x2_pk(a)), "l"(x2_pk(b)));
+  return x2_upk(d);
+}
+__device__ __forceinline__ float2 x2_sub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x2_pk(a)), "l"(x2_pk(b)));
+  return x2_upk(d);
+}
+__device__ __forceinline__ float2 x2_mul(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x2_pk(a)), "l"(x2_pk(b)));
+  return x2_upk(d);
+}
+__device__ __forceinline__ float2 x2_fma(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(x2_pk(a)), "l"(x2_pk(b)), "l"(x2_pk(c)));
+  return x2_upk(d);
+}
+
+// The three sums of Dots<float> in Dot2 form over pairs of elements, on the
+// paired instructions: two accumulators per sum (the pair's halves), merged
+// into a Dots<float> at the end.  Per pair and sum: the product and its
+// exact error (TwoProd by FMA), TwoSum into hi, the errors summed into lo.
+struct Dot2x2 {
+  float2 h1, l1, h2, l2, h3, l3;  // v.q, q.q, v.v
+  __device__ __forceinline__ void zero() { h1 = l1 = h2 = l2 = h3 = l3 = make_float2(0.f, 0.f); }
+  // (h, l) += x * y; xn = -x
+  __device__ __forceinline__ static void acc(float2& h, float2& l, float2 x, float2 xn, float2 y) {
+    const float2 p = x2_mul(x, y);
+    const float2 pen = x2_fma(xn, y, p);  // p - x y = -(rounding error of p), exact
+    const float2 s = x2_add(h, p);
+    const float2 bb = x2_sub(s, h);
+    const float2 e = x2_add(x2_sub(h, x2_sub(s, bb)), x2_sub(p, bb));
+    l = x2_add(l, x2_sub(e, pen));
+    h = s;
+  }
+  __device__ __forceinline__ void add(float2 v, float2 q) {
+    const float2 vn = make_float2(-v.x, -v.y), qn = make_float2(-q.x, -q.y);
+    acc(h1, l1, v, vn, q);
+    acc(h2, l2, q, qn, q);
+    acc(h3, l3, v, vn, v);
+  }
+  __device__ __forceinline__ Dots<float> merged() const {
+    Dots<float> d;
+    d.s1 = df_add({h1.x, l1.x}, {h1.y, l1.y});
+    d.s2 = df_add({h2.x, l2.x}, {h2.y, l2.y});
+    d.s3 = df_add({h3.x, l3.x}, {h3.y, l3.y});
+    return d;
+  }
+};
+
 template <>
 struct Dots<double> {
   double s1, s2, s3;

@@ -255,42 +255,9 @@ __global__ void k_assemble(const S* __restrict__ V, int nslots, size_t n, const 
   }
 }
 
-// ---- the FP32 assembly on paired FP32 instructions
-// Blackwell's f32x2 instructions take one issue slot for two lane-wise FP32
-// operations with the same IEEE round-to-nearest result per half.  The
-// assembly with two compensated accumulators per element is issue-bound, so
-// k_assemble_pair runs two adjacent elements per thread on them.
-__device__ __forceinline__ unsigned long long pk2(float2 a) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
-  return r;
-}
-__device__ __forceinline__ float2 upk2(unsigned long long r) {
-  float2 a;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
-  return a;
-}
-__device__ __forceinline__ float2 x2_add(float2 a, float2 b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-  return upk2(d);
-}
-__device__ __forceinline__ float2 x2_sub(float2 a, float2 b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-  return upk2(d);
-}
-__device__ __forceinline__ float2 x2_mul(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-  return upk2(d);
-}
-__device__ __forceinline__ float2 x2_fma(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
-  return upk2(d);
-}
-
+// ---- the FP32 assembly on paired FP32 instructions (x2_* in common.cuh):
+// with two compensated accumulators per element the assembly is
+// issue-bound, so k_assemble_pair runs two adjacent elements per thread.
 // acc_comp on two elements: t = vv (yh + yl) as FMA(vv, yh, vv * yl), then
 // (sum, comp) += t with the exact error of sum + t from TwoSum (Knuth).  The
 // error of a floating-point sum is unique, so this gives bitwise the values

@@ -273,6 +273,8 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
   };
   Dots<T> d;
   d.zero();
+  Dot2x2 dd;  // FP32: the sums over pairs of cells on paired instructions
+  dd.zero();
   // q on row y (< yb): the lane's VX cells; stores and dot products
   auto q_row = [&](int y) {
     const int sl = ring(y);
@@ -302,10 +304,12 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
         if (VX == 4) vb_store4(pb, (float)v[0], (float)v[1 % VX], (float)v[2 % VX], (float)v[3 % VX]);
         else vb_store2(pb, (float)v[0], (float)v[1 % VX]);
       }
+      if constexpr (sizeof(T) == 4) {
 #pragma unroll
-      for (int e = 0; e < VX; ++e) {
-        if constexpr (sizeof(T) == 4) d.add_dot2(v[e], q[e]);
-        else d.add(v[e], q[e]);
+        for (int e = 0; e < VX; e += 2) dd.add(make_float2(v[e], v[e + 1]), make_float2(q[e], q[e + 1]));
+      } else {
+#pragma unroll
+        for (int e = 0; e < VX; ++e) d.add(v[e], q[e]);
       }
     }
   };
@@ -342,6 +346,7 @@ __global__ void __launch_bounds__(SNT) k_stencil2d_strip(StencilArgs<T> a, int y
   }
   cp_async_wait<0>();
   if (!STEP) return;
+  if constexpr (sizeof(T) == 4) d = dd.merged();
   d = block_reduce(d, red);
   const int nblk = gridDim.x * gridDim.y;
   if (threadIdx.x == 0) a.partials[(size_t)s * nblk + blockIdx.x + gridDim.x * blockIdx.y] = d;

@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(NT, kMinBlocks)
     };
     auto cell = [&](const float* sp, int off) -> float { return fv(sp[off], use_vp ? sp[VOFF + off] : 0.f); };
 
-    Dots<float> d;
-    d.zero();
+    Dot2x2 dd;
+    dd.zero();
     bool abort = false;
     if (P > 0) {
       if (tid == 0)
@@ -250,7 +250,10 @@ __global__ void __launch_bounds__(NT, kMinBlocks)
             if (BC != GMRF_BC_NEUMANN || z < nz - 1) r += c - vup[e];
             if (STEP && j > 0) r -= bprev * vpc[e];
             qo[e] = r;
-            if (STEP) d.add_dot2(c, r);
+          }
+          if (STEP) {
+            dd.add(make_float2(vc[0], vc[1]), make_float2(qo[0], qo[1]));
+            dd.add(make_float2(vc[2], vc[3]), make_float2(qo[2], qo[3]));
           }
           const size_t i = (size_t)gx + (size_t)nx * gy + plane * z;
           *reinterpret_cast<float4*>(Wout + i) = make_float4(qo[0], qo[1], qo[2], qo[3]);
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks)
       return;
     }
     if (STEP) {
-      d = block_reduce(d, red);
+      const Dots<float> d = block_reduce(dd.merged(), red);
       if (tid == 0) a.partials[(size_t)s * it.per_vec + li] = d;
       if (last_block(a.counters, s, it.per_vec, &s_int[3]))
         finish_step<float>(a.P, j, s, a.partials, it.per_vec, a.st, a.alpha, a.beta, a.alpha_f, a.beta2_f, red,
