@@ -234,7 +234,35 @@ __global__ void __launch_bounds__(NT, kMinBlocks)
         } else {
           kk[0] = kk[1] = kk[2] = kk[3] = a.kappa2_const;
         }
-        if (own) {
+        if (own && BC != GMRF_BC_NEUMANN) {
+          // every edge exists: pairs of cells on paired FP32 instructions
+          float qo[4];
+#pragma unroll
+          for (int e = 0; e < 4; e += 2) {
+            const float2 c = make_float2(vc[e], vc[e + 1]);
+            const float2 l = make_float2(e == 0 ? vl : vc[e - 1 < 0 ? 0 : e - 1], vc[e]);
+            const float2 rr = make_float2(vc[e + 1], e == 2 ? vr : vc[e + 2 < 4 ? e + 2 : 3]);
+            float2 t = x2_fma(make_float2(kk[e], kk[e + 1]), c, x2_sub(c, l));
+            t = x2_add(t, x2_sub(c, rr));
+            t = x2_add(t, x2_sub(c, make_float2(vs[e], vs[e + 1])));
+            t = x2_add(t, x2_sub(c, make_float2(vn[e], vn[e + 1])));
+            t = x2_add(t, x2_sub(c, make_float2(vdn[e], vdn[e + 1])));
+            t = x2_add(t, x2_sub(c, make_float2(vup[e], vup[e + 1])));
+            if (STEP && j > 0) t = x2_fma(make_float2(-bprev, -bprev), make_float2(vpc[e], vpc[e + 1]), t);
+            qo[e] = t.x;
+            qo[e + 1] = t.y;
+          }
+          if (STEP) {
+            dd.add(make_float2(vc[0], vc[1]), make_float2(qo[0], qo[1]));
+            dd.add(make_float2(vc[2], vc[3]), make_float2(qo[2], qo[3]));
+          }
+          const size_t i = (size_t)gx + (size_t)nx * gy + plane * z;
+          *reinterpret_cast<float4*>(Wout + i) = make_float4(qo[0], qo[1], qo[2], qo[3]);
+          if (STEP) {
+            *reinterpret_cast<float4*>(Vc + i) = make_float4(vc[0], vc[1], vc[2], vc[3]);
+            if (a.P.vb) vb_store4(vb_at(a.P, s, j, n, i), vc[0], vc[1], vc[2], vc[3]);
+          }
+        } else if (own) {
           float qo[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
