@@ -468,3 +468,45 @@ def test_host_loop_flag_validated(g):
         assert lib.gmrf_set_tuning(p._h, ctypes.byref(t)) == g.ERR_INVALID
         t = g.GmrfTuning(0, 0, 0.0, 0, 1)
         assert lib.gmrf_set_tuning(p._h, ctypes.byref(t)) == g.OK
+
+
+@pytest.mark.parametrize("v_storage", ["native", "bf16"])
+def test_pair_assembly_equals_one_element_assembly(g, v_storage):
+    # FP32 outputs with an even n and 8-byte aligned output run the assembly on
+    # two elements per thread with paired FP32 instructions; an output shifted
+    # by one float takes the one-element kernel.  The error term of the
+    # compensated sums is exact in both, so the samples agree bitwise.
+    shape = (64, 32)
+    n = 64 * 32
+    k2 = inputs.kappa2_gp_field(shape, seed=12, ell=6.0)
+    Z = inputs.gaussian_vectors(3, n, seed=13, dtype=np.float32)
+    with g.Problem(shape, "neumann", "spde_squared", kappa2=_dev(k2), precond="mirror") as p:
+        xa = torch.empty(3 * n, dtype=torch.float32, device="cuda")
+        rca, ia = p.sample(xa, nsamples=3, tol=1e-6, m_max=300, z=_dev(Z), check_every=8, v_storage=v_storage,
+                           raise_on_error=False)
+        buf = torch.empty(3 * n + 1, dtype=torch.float32, device="cuda")
+        xb = buf[1:]  # 4-byte offset: not 8-byte aligned
+        rcb, ib = p.sample(xb, nsamples=3, tol=1e-6, m_max=300, z=_dev(Z), check_every=8, v_storage=v_storage,
+                           raise_on_error=False)
+    assert rca == rcb
+    assert [(i.m_used, i.status, i.err_est) for i in ia] == [(i.m_used, i.status, i.err_est) for i in ib]
+    assert torch.equal(xa, xb)
+
+
+def test_device_loop_single_step_cap(g):
+    # m_max = 1 and 2 stop the device-side loop after its first body, as the host loop does
+    shape = (64, 64)
+    n = 64 * 64
+    out = {}
+    for host in (False, True):
+        with g.Problem(shape, "periodic", "shifted_laplacian", kappa2_const=0.3) as p:
+            p.set_tuning(host_loop=host)
+            for m_max in (1, 2):
+                x = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+                rc, info = p.sample(x, nsamples=2, tol=1e-6, m_max=m_max, seed=3, raise_on_error=False)
+                out[host, m_max] = (rc, [(i.m_used, i.status) for i in info], x.cpu())
+    for m_max in (1, 2):
+        a, b = out[False, m_max], out[True, m_max]
+        assert a[0] == b[0] == g.ERR_NOT_CONVERGED and a[1] == b[1]
+        assert all(m == m_max for m, _ in a[1])
+        assert torch.equal(a[2], b[2])

@@ -95,3 +95,19 @@ def test_engines_fit_the_budget():
         assert used <= 2 * per
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("mode", ["batched", "direct"])
+def test_released_outputs(mode):
+    # keep_outputs=False: completed requests keep their counts, statuses and
+    # log dets and drop their device outputs; the metrics count every status
+    reqs = _mix()[:6]
+    srv = serve.Server(mode=mode, max_inflight=4, keep_outputs=False)
+    try:
+        out, metrics = srv.serve(reqs, realtime=False)
+    finally:
+        srv.close()
+    assert all(r.x is None for r in out)
+    assert all(r.status == 0 and len(r.m_used) == r.count for r in out if r.kind != "logdet")
+    assert all(np.isfinite(r.logdet) for r in out if r.kind == "logdet")
+    assert metrics["statuses"] == {"0": len(reqs)}
