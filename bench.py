@@ -742,8 +742,9 @@ def measure_serving(nreq=1000, baseline_nreq=24):
     they free up) at 0.25x, 0.5x, 1x and 2x the measured saturation rate, with
     nreq requests per rate; the same stream without packing (one library call
     per request, up to 16 in flight) at 1x and 2x; and the one-request,
-    one-sample-at-a-time FP64 baseline at 0.25x on a bounded prefix of the
-    stream (baseline_nreq requests: it saturates far below these rates)."""
+    one-sample-at-a-time FP64 baseline at the same four rates on a bounded
+    prefix of each stream (baseline_nreq requests: it saturates far below
+    these rates)."""
     import torch
     from paper_1312_1476_gb300 import serve
 
@@ -779,10 +780,11 @@ def measure_serving(nreq=1000, baseline_nreq=24):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
     base = serve.Server(mode="direct", max_inflight=1, precision="fp64", block_width=1, keep_outputs=False)
-    reqs = stream(0.25 * sat_rate, baseline_nreq)
-    base.prepare(reqs, tune=False)
-    _, met = base.serve(reqs, realtime=True)
-    res["fp64_one_at_a_time_rate_0.25x"] = dict(met, rate_req_per_s=0.25 * sat_rate)
+    for frac in (0.25, 0.5, 1.0, 2.0):
+        reqs = stream(frac * sat_rate, baseline_nreq)
+        base.prepare(reqs, tune=False)
+        met = base.serve(reqs, realtime=True)[1]
+        res["fp64_one_at_a_time_rate_%gx" % frac] = dict(met, rate_req_per_s=frac * sat_rate)
     res["workload"] = ("config 5 mix: samples (1-64) and log dets (16-64 probes) of 2-D SPDE (mirror M, 128^2-1024^2) "
                        "and 3-D 7-point (64^3-128^3) GMRFs, kappa^2 and tau per request, tol 1e-6; latency = "
                        "completion - arrival; packed = continuous batching in the library's slot server, unpacked "
