@@ -217,14 +217,23 @@ int step_body(gmrf_server* sv, int32_t* active) {
   cudaStream_t s = p->ws;
   const int ns = sv->o.nslots;
   CKR(admit(sv));
-  int running = 0;
+  int running = 0, hw = 0;
   for (int i = 0; i < ns; ++i)
-    if (sv->slots[i].req >= 0) ++running;  // admitted or resumed: the replay runs them
+    if (sv->slots[i].req >= 0) {  // admitted or resumed: the replay runs them
+      ++running;
+      hw = i + 1;
+    }
   if (running) {
-    const StepParams P = step_params(p, sv->b, sv->o.tol, sv->o.m_max, false);
+    // The replay covers the slots up to the highest one in use (admission
+    // fills the lowest free slots), rounded up to 8 so that the step graph is
+    // recaptured only when that prefix grows or shrinks by a block of slots:
+    // idle slots beyond it would cost an early-exit block per kernel each.
+    const int hw8 = std::min(ns, (hw + 7) / 8 * 8);
+    const LanczosBufs bp = sub_batch(sv->b, 0, hw8, p->g.n, esize(p));
+    const StepParams P = step_params(p, bp, sv->o.tol, sv->o.m_max, false);
     const int c = std::min(sv->o.check_every > 0 ? sv->o.check_every : 16, sv->o.m_max);
-    if (p->precond != GMRF_PREC_NONE && !p->sp) CKR(precond_prepare(p->pre, ns, s));
-    CKR(capture_steps(p, sv->b, P, c));
+    if (p->precond != GMRF_PREC_NONE && !p->sp) CKR(precond_prepare(p->pre, hw8, s));
+    CKR(capture_steps(p, bp, P, c));
     CK(cudaGraphLaunch(p->graph.exec, s));
     trace_replayed(&p->graph.tr, c * p->graph.kernels_per_step);
   }

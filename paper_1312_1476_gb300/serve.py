@@ -125,9 +125,11 @@ class Engine:
         self.stream = torch.cuda.Stream()
         self.prob = owner._problem(shape, k2, 1.0, self.stream)
         self.server = g.Server(self.prob, nslots=nslots, m_max=m_max, tol=owner.tol, check_every=owner.check_every)
-        self.lock = threading.Lock()
+        self.lock = threading.Lock()    # guards `incoming` and `active` (the library server is the loop's alone)
         self.wake = threading.Event()
-        self.active = {}       # library request id -> (Request, x)
+        self.incoming = []     # (Request, x) handed over by the dispatcher, submitted by the loop
+        self.active = {}       # library request id -> (Request, x); the loop's alone
+        self.inflight = 0      # requests handed over and not yet completed
         self.last_used = time.perf_counter()
         self.stop = False
         self.error = None
@@ -136,19 +138,18 @@ class Engine:
 
     def busy(self):
         with self.lock:
-            return bool(self.active)
+            return self.inflight > 0
 
     def submit(self, req):
+        """Hands a request to the engine; the engine's loop submits it to the
+        library server between two steps, so the dispatcher never waits for a
+        step in flight."""
         torch = self.owner.torch
         dt = torch.float64 if self.owner.precision == "fp64" else torch.float32
+        x = torch.empty(req.count * self.n, dtype=dt, device="cuda") if req.kind == "sample" else None
         with self.lock:
-            if req.kind == "sample":
-                x = torch.empty(req.count * self.n, dtype=dt, device="cuda")
-                rid = self.server.submit_sample(x, req.count, req.seed, req.tau)
-            else:
-                x = None
-                rid = self.server.submit_logdet(req.count, req.seed, req.tau)
-            self.active[rid] = (req, x)
+            self.incoming.append((req, x))
+            self.inflight += 1
             self.last_used = time.perf_counter()
         self.wake.set()
 
@@ -158,24 +159,32 @@ class Engine:
             while not self.stop:
                 self.wake.wait(timeout=0.05)
                 with self.lock:
-                    if not self.active:
+                    incoming, self.incoming = self.incoming, []
+                    if not incoming and not self.active:
                         self.wake.clear()
                         continue
-                    try:
-                        left = self.server.step()
-                        finished = []
-                        for rid, (req, x) in list(self.active.items()):
-                            r = self.server.poll(rid)
-                            if r is not None:
-                                finished.append((rid, req, x, r))
-                                del self.active[rid]
-                        if left == 0 and not self.active:
+                finished = []
+                try:
+                    for req, x in incoming:
+                        if req.kind == "sample":
+                            rid = self.server.submit_sample(x, req.count, req.seed, req.tau)
+                        else:
+                            rid = self.server.submit_logdet(req.count, req.seed, req.tau)
+                        self.active[rid] = (req, x)
+                    left = self.server.step()
+                    for rid, (req, x) in list(self.active.items()):
+                        r = self.server.poll(rid)
+                        if r is not None:
+                            finished.append((rid, req, x, r))
+                            del self.active[rid]
+                    with self.lock:
+                        self.inflight -= len(finished)
+                        if left == 0 and not self.active and not self.incoming:
                             self.wake.clear()
                         self.last_used = time.perf_counter()
-                    except Exception as e:  # surfaced by the dispatcher
-                        self.error = e
-                        self.stop = True
-                        finished = []
+                except Exception as e:  # surfaced by the dispatcher
+                    self.error = e
+                    self.stop = True
                 for rid, req, x, (rc, infos, ld, se) in finished:
                     self.owner._complete(req, rc, infos, x, ld, se)
 
@@ -222,6 +231,9 @@ class Server:
         self.used = 0
         self.cv = threading.Condition()
         self.engines = {}  # (shape, field id) -> Engine
+        self.engines_created = 0
+        self.engines_released = 0
+        self.plan = {}     # (shape, field id) -> slots, from prepare(): every engine of the stream fits at once
 
     def _m_max(self, req_or_shape):
         shape = req_or_shape.shape if hasattr(req_or_shape, "shape") else req_or_shape
@@ -256,8 +268,11 @@ class Server:
         out = req.count * n * es if req.kind in ("sample", "solve") else 0
         return self.chunk(req) * self.vec_bytes(req) + out + (2 * out if req.kind == "solve" else 0) + 8 * n
 
-    def engine_slots(self, shape):
-        """Slots of an engine: as many as a quarter of the budget holds, 8 .. nslots_max."""
+    def engine_slots(self, shape, key=None):
+        """Slots of an engine: the prepared plan's share for its grid and field,
+        else as many as a quarter of the budget holds, 8 .. nslots_max."""
+        if key is not None and key in self.plan:
+            return self.plan[key]
         per = self._slot_bytes(shape)
         return int(max(8, min(self.nslots_max, (self.budget // 4) // per)))
 
@@ -340,6 +355,40 @@ class Server:
         3-D z chunk)."""
         for r in requests:
             self.fields.get(r.shape, r.field_id)
+        if self.mode == "batched":
+            # One engine per grid and field of the stream, all resident at once,
+            # so that no engine is torn down and rebuilt while the stream runs.
+            # Slots follow demand: the same number of slots per requested vector
+            # for every engine (4 .. nslots_max each), the largest such ratio
+            # whose slot tables fit the budget; an engine whose slots are cheap
+            # (small grids) gets at least what an eighth of an equal share of
+            # the budget holds.
+            demand = {}
+            for r in requests:
+                if r.kind != "solve":
+                    k = (r.shape, r.field_id)
+                    demand[k] = demand.get(k, 0) + r.count
+            keys = sorted(set(demand) - set(self.plan), key=lambda k: (len(k[0]), k))
+            if keys:
+                fixed = sum(self.plan[k] * self._slot_bytes(k[0]) for k in self.plan)
+                floor_bytes = self.budget // (8 * (len(self.plan) + len(keys)))
+
+                def slots(k, ratio):
+                    return int(max(4, min(self.nslots_max, max(floor_bytes // self._slot_bytes(k[0]),
+                                                               ratio * demand[k]))))
+
+                def mem(ratio):
+                    return fixed + sum(slots(k, ratio) * self._slot_bytes(k[0]) for k in keys)
+
+                lo, hi = 0.0, float(self.nslots_max)
+                for _ in range(50):
+                    mid = 0.5 * (lo + hi)
+                    lo, hi = (mid, hi) if mem(mid) <= self.budget else (lo, mid)
+                for k in keys:
+                    self.plan[k] = slots(k, lo)
+                for k in keys:
+                    if k not in self.engines:
+                        self._engine_for(Request(arrival=0.0, rid=-1, kind="sample", shape=k[0], field_id=k[1]))
         if tune and self.mode == "direct":
             widest = {}
             for r in requests:
@@ -360,7 +409,7 @@ class Server:
         key = (req.shape, req.field_id)
         if key in self.engines:
             return self.engines[key]
-        ns = self.engine_slots(req.shape)
+        ns = self.engine_slots(req.shape, key)
         need = ns * self._slot_bytes(req.shape)
         used = sum(e.nslots * self._slot_bytes(e.key[0]) for e in self.engines.values())
         if used + need > self.budget:
@@ -370,11 +419,13 @@ class Server:
                 if not e.busy():
                     e.close()
                     del self.engines[k]
+                    self.engines_released += 1
                     used -= e.nslots * self._slot_bytes(k[0])
         if used + need > self.budget and self.engines:
             return None
         e = Engine(self, key, self.fields.get(req.shape, req.field_id), ns, self._m_max(req.shape))
         self.engines[key] = e
+        self.engines_created += 1
         return e
 
     def close(self):
@@ -387,6 +438,7 @@ class Server:
         results in request order and a metrics dict."""
         reqs = sorted(requests)
         self._results = {}
+        created0, released0 = self.engines_created, self.engines_released
         t0 = time.perf_counter()
         self._t0 = t0
         direct = [] if self.mode == "batched" else None
@@ -458,4 +510,9 @@ class Server:
                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                    "statuses": {str(c): sum(1 for r in out if r.status == c) for c in sorted({r.status for r in out})},
                    "mode": self.mode}
+        if self.mode == "batched":
+            metrics["engines"] = {"created": self.engines_created - created0, "released": self.engines_released -
+                                  released0, "live": len(self.engines),
+                                  "slots": {"%s/%d" % ("x".join(map(str, k[0])), k[1]): e.nslots
+                                            for k, e in self.engines.items()}}
         return out, metrics
