@@ -752,6 +752,10 @@ def measure_serving(nreq=1000, baseline_nreq=24):
         return serve.make_mix(count, rate=rate, seed=4)
 
     res = {"requests_per_rate": nreq}
+    # memory the earlier workloads left in torch's cache goes back to the device,
+    # so the serving budget (a share of free HBM) does not depend on them
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     srv = serve.Server(mode="batched", keep_outputs=False)
     try:
         burst = stream(1e6, nreq)
