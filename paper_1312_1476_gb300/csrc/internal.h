@@ -111,7 +111,6 @@ cudaError_t launch_dots3_final(const void* part, int nvec, double* out, cudaStre
 // kResidBlocks * nvec Dots<double> of scratch.
 cudaError_t launch_resid_df(const Grid& g, const float* kappa2, double kappa2_const, const float* z, const float* u,
                             float* r, int nvec, void* part, double* out, cudaStream_t s);
-cudaError_t launch_convert(bool to_fp64, const void* in, void* out, size_t count, cudaStream_t s);
 // The condition kernel of the device-side Lanczos loop: sets h to 1 while some
 // of the nvec vectors is running and ++*ctr < limit, else 0.
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const VecState* st, int nvec, int* ctr, int limit,

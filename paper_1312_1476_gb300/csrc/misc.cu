@@ -495,12 +495,6 @@ __global__ void k_dots3_final(const Dots<double>* part, int nblk, double* out) {
   }
 }
 
-template <typename A, typename B>
-__global__ void k_convert(const A* in, B* out, size_t count) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = (B)in[i];
-}
-
 template <typename T>
 __global__ void k_scale(T* x, size_t count, T a) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
@@ -695,13 +689,6 @@ const void* loop_cond_kernel() { return (const void*)k_loop_cond; }
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const VecState* st, int nvec, int* ctr, int limit,
                              cudaStream_t s) {
   k_loop_cond<<<1, 256, 0, s>>>(h, st, nvec, ctr, limit);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_convert(bool to_fp64, const void* in, void* out, size_t count, cudaStream_t s) {
-  const int grid = grid_for(count, 256);
-  if (to_fp64) k_convert<float, double><<<grid, 256, 0, s>>>((const float*)in, (double*)out, count);
-  else k_convert<double, float><<<grid, 256, 0, s>>>((const double*)in, (float*)out, count);
   return cudaGetLastError();
 }
 
