@@ -391,7 +391,9 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.precond)
-        if not args.no_variants:
+        if world == 1 and not args.no_variants:
+            # the other workloads are single-GPU measurements: under torchrun the
+            # line carries the replicated headline only
             out["variants"] = measure_variants(args, gmrf, torch, flush, peak)
         print(json.dumps(out), flush=True)
     prob.close()
