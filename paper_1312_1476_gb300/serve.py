@@ -207,7 +207,7 @@ class Server:
     M_MAX_3D = 128
 
     def __init__(self, mem_budget=None, max_inflight=16, precision="fp32", chunk_bytes=8 << 30, block_width=None,
-                 mode="batched", nslots_max=64, check_every=16, tol=1e-6, keep_outputs=True):
+                 mode="batched", nslots_max=64, check_every=8, tol=1e-6, keep_outputs=True):
         import torch
         from . import gmrf
         self.torch = torch
