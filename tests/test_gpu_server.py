@@ -106,3 +106,44 @@ def test_server_rejects_bad_requests(g):
         x = torch.empty(1024, dtype=torch.float32, device="cuda")
         rc, _ = p.sample(x, nsamples=1, tol=1e-6, m_max=200, seed=1)
         assert rc == g.OK
+
+
+@pytest.mark.parametrize("precision,with_factor", [("fp64", True), ("fp64", False), ("fp32", True)])
+def test_server_sparse_equals_synchronous_calls(g, precision, with_factor):
+    # the slot server on a CSR precision with an incomplete-Cholesky factor
+    # (Section 5.2): samples (x = F^{-T} A^{-1/2} z) and log dets bitwise equal
+    # to gmrf_sample / gmrf_logdet on a problem with the request's tau
+    Q = inputs.figure3_matrix()
+    F = g.ichol(Q, droptol=1e-3, shift=1e-3) if with_factor else None
+    n = Q[0].shape[0] - 1 if isinstance(Q, tuple) else Q.shape[0]
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tol = TOL[precision]
+    reqs = [("sample", 3, 21, 1.0), ("logdet", 5, 22, 2.0), ("sample", 2, 23, 0.5)]
+    out = {}
+    with g.SparseProblem(Q, F, tau=1.0, precision=precision) as p:
+        with g.Server(p, nslots=4, m_max=800, tol=tol, check_every=8) as sv:
+            ids = []
+            for kind, cnt, seed, tau in reqs:
+                if kind == "sample":
+                    x = torch.full((cnt * n,), float("nan"), dtype=dt, device="cuda")
+                    ids.append((sv.submit_sample(x, cnt, seed, tau), kind, cnt, seed, tau, x))
+                else:
+                    ids.append((sv.submit_logdet(cnt, seed, tau), kind, cnt, seed, tau, None))
+            for _ in range(10000):
+                if sv.step() == 0:
+                    break
+            for rid, kind, cnt, seed, tau, x in ids:
+                out[rid] = (kind, cnt, seed, tau, x, sv.poll(rid))
+    for rid, (kind, cnt, seed, tau, x, (rc, infos, ld, se)) in out.items():
+        with g.SparseProblem(Q, F, tau=tau, precision=precision) as p1:
+            if kind == "sample":
+                x1 = torch.empty(cnt * n, dtype=dt, device="cuda")
+                rc1, i1 = p1.sample(x1, nsamples=cnt, tol=tol, m_max=800, seed=seed, check_every=8,
+                                    raise_on_error=False)
+                assert torch.equal(x, x1)
+            else:
+                ld1, se1, _, i1, rc1 = p1.logdet(nprobes=cnt, tol=tol, m_max=800, seed=seed, check_every=8,
+                                                 raise_on_error=False)
+                assert ld == ld1 and (se == se1 or (np.isnan(se) and np.isnan(se1)))
+        assert rc == rc1
+        assert [(a.m_used, a.status, a.err_est) for a in infos] == [(b.m_used, b.status, b.err_est) for b in i1]
