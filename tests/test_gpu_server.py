@@ -147,3 +147,40 @@ def test_server_sparse_equals_synchronous_calls(g, precision, with_factor):
                 assert ld == ld1 and (se == se1 or (np.isnan(se) and np.isnan(se1)))
         assert rc == rc1
         assert [(a.m_used, a.status, a.err_est) for a in infos] == [(b.m_used, b.status, b.err_est) for b in i1]
+
+
+def test_server_smmala_operator_equals_synchronous_calls(g):
+    # the sMMALA operator tau((kc^2 + L)^2 + D) preconditioned by its prior (circulant on a torus)
+    shape = (64, 64)
+    n = 64 * 64
+    d = inputs.kappa2_uniform_field(shape, seed=8, lo=0.0, hi=3.0)
+    kw = dict(kappa2=torch.from_numpy(d).cuda(), kappa2_const=0.5, precond="circulant", precision="fp32")
+    reqs = [("sample", 3, 31, 1.0), ("logdet", 6, 32, 2.0), ("sample", 4, 33, 0.8)]
+    out = {}
+    with g.Problem(shape, "periodic", "spde_plus_diag", tau=1.0, **kw) as p:
+        with g.Server(p, nslots=5, m_max=300, tol=1e-6, check_every=8) as sv:
+            ids = []
+            for kind, cnt, seed, tau in reqs:
+                if kind == "sample":
+                    x = torch.full((cnt * n,), float("nan"), dtype=torch.float32, device="cuda")
+                    ids.append((sv.submit_sample(x, cnt, seed, tau), kind, cnt, seed, tau, x))
+                else:
+                    ids.append((sv.submit_logdet(cnt, seed, tau), kind, cnt, seed, tau, None))
+            for _ in range(10000):
+                if sv.step() == 0:
+                    break
+            for rid, kind, cnt, seed, tau, x in ids:
+                out[rid] = (kind, cnt, seed, tau, x, sv.poll(rid))
+    for rid, (kind, cnt, seed, tau, x, (rc, infos, ld, se)) in out.items():
+        with g.Problem(shape, "periodic", "spde_plus_diag", tau=tau, **kw) as p1:
+            if kind == "sample":
+                x1 = torch.empty(cnt * n, dtype=torch.float32, device="cuda")
+                rc1, i1 = p1.sample(x1, nsamples=cnt, tol=1e-6, m_max=300, seed=seed, check_every=8,
+                                    raise_on_error=False)
+                assert torch.equal(x, x1)
+            else:
+                ld1, se1, _, i1, rc1 = p1.logdet(nprobes=cnt, tol=1e-6, m_max=300, seed=seed, check_every=8,
+                                                 raise_on_error=False)
+                assert ld == ld1 and se == se1
+        assert rc == rc1 == g.OK
+        assert [(a.m_used, a.status, a.err_est) for a in infos] == [(b.m_used, b.status, b.err_est) for b in i1]
