@@ -34,6 +34,9 @@ from massive Gaussian random vectors"):
   SC'11) that the device path uses for z and Rademacher probes, restated from
   its published definition, with the Box-Muller transform.
 
-Parity status of every function is listed in its docstring; functions whose
-result is not pinned to something outside the oracle say "parity unpinned".
+Parity status of every function is listed in its docstring; a function whose
+result is not pinned to something outside the oracle would say "parity
+unpinned" (none does: the Philox stream is pinned to an independent
+implementation of the generator, the rest to closed forms, dense linear
+algebra and brute force; see the tests/test_oracle_*.py files).
 """
